@@ -1,0 +1,421 @@
+"""Electron-move throughput of the PbyP crowd move on one GB300 (or N replicas).
+
+Metric: electron moves per second over the crowd (walkers x electrons x generations /
+time), FP32-mixed path (headline `value`) next to the FP64 path, with the energy each
+reaches.  A step is one generation: every electron of every walker proposed once
+(Alg. 1 lines 4-9), pending delayed updates applied, the FP64 recompute at its cadence,
+and the local energy (line 11).  Inputs are device resident when the timed region starts;
+L2 is flushed (a 256 MiB write) between timed steps, outside the per-step CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (test infrastructure) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "electron moves/sec over crowd, FP32-mixed vs FP64 GPU, at stated energy error"
+UNIT = "electron-moves/s"
+KERNEL_SRC = os.path.join(ROOT, "paper_2209_14487_gb300", "csrc", "qmc_move.cu")
+
+
+def bytes_per_move(n, N, s, p_acc, update, k):
+    """Algorithmic bytes of one electron move (stencil, inverse column, positions and
+    distance rows, accepted rows, and the inverse update)."""
+    b = 64 * n * s + n * s + 8 * N * s + p_acc * 5 * n * s
+    if update == "sm":
+        b += p_acc * 2 * n * n * s
+    else:
+        b += 2 * n * k * s + p_acc * (2 * n * s + 3 * n * n * s / k)
+    return b
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.dirname(KERNEL_SRC))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(os.path.dirname(KERNEL_SRC), f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the
+    kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        e = d.get(kernel)
+        if e and e.get("source_sha") == source_sha():
+            return e.get("bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            rows.append(parts)
+        if self.uuid:
+            mine = [r for r in rows if self.uuid in r[0]]
+            rows = mine or rows
+        try:
+            sm = [float(r[1]) for r in rows]
+            smax = max(float(r[2]) for r in rows)
+        except (ValueError, IndexError):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unparsed"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[4 + k].lower() in ("active", "1", "yes")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_crowd(wl, precision, update, k, stream, crowd_id):
+    from paper_2209_14487_gb300 import qmcgb
+    c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
+                                  stream=stream)
+    c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=crowd_id)))
+    c.qmc_recompute()
+    return c
+
+
+def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf):
+    """Per-step CUDA-event timing of qmc_sweep(1) on torch's current stream."""
+    import torch
+    stream = torch.cuda.Stream()  # a real stream: torch's default is the legacy NULL stream
+    torch.cuda.set_stream(stream)
+    c = make_crowd(wl, precision, update, k, stream.cuda_stream, crowd_id)
+    eloc = torch.zeros((warmup + steps, wl.n_walkers), dtype=torch.float64, device="cuda")
+    for g in range(warmup):
+        c.qmc_sweep(1, eloc[g], stats=False)
+    torch.cuda.synchronize()
+    n_rc = wl.n_recompute
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    gens = []
+    launches0 = c.launch_count
+    for s in range(steps):
+        flush_buf.add_(1.0)  # write 256 MiB on this stream: evicts the previous step from L2
+        gens.append(c.generation)
+        ev[s][0].record(stream)
+        c.qmc_sweep(1, eloc[warmup + s], stats=False)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    launches = c.launch_count - launches0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    # steps without the FP64 recompute run exactly one launch of the fused move kernel
+    plain = [m for m, g in zip(ms, gens) if not (n_rc > 0 and (g + 1) % n_rc == 0)]
+    e = eloc[warmup:].double().cpu().numpy()
+    # acceptance ratio of the chain (one more generation, after the timed region)
+    c2 = c.qmc_sweep(2, None, stats=True)
+    p_acc = c2.n_accept / max(1, c2.n_moves)
+    c.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    return {"ms": ms, "plain_ms": plain, "eloc": e, "p_acc": p_acc, "launches": launches}
+
+
+def energy_stats(e: np.ndarray, n_blocks: int = 10):
+    blk = e.mean(axis=1)
+    nb = min(n_blocks, len(blk))
+    b = blk[: len(blk) // nb * nb].reshape(nb, -1).mean(axis=1)
+    return float(b.mean()), float(b.std(ddof=1) / math.sqrt(nb)) if nb > 1 else float("nan")
+
+
+def e2e_run(wl, precision, update, k, steps, crowd_id):
+    """Through the public API from pinned host buffers: create, load table, ions, Jastrow
+    and positions, recompute, then `steps` sweeps each returning E_L to the host."""
+    import torch
+
+    from paper_2209_14487_gb300 import qmcgb
+    table = torch.from_numpy(np.ascontiguousarray(wl.table())).pin_memory()
+    R = torch.from_numpy(np.ascontiguousarray(wl.positions(crowd_id=crowd_id))).pin_memory()
+    e_host = torch.zeros(wl.n_walkers, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = qmcgb.Crowd(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L, wl.n_walkers, wl.tau,
+                    precision=precision, update=update, delay_rank=k,
+                    n_recompute=wl.n_recompute, drift=wl.drift, potential=wl.potential,
+                    seed=wl.seed)
+    if wl.n_ions:
+        c.qmc_load_ions(wl.ions)
+    if wl.j2_uu is not None:
+        c.qmc_load_jastrow(qmcgb.QMC_J2_UU, wl.j2_uu.coefs, wl.j2_uu.rc)
+        c.qmc_load_jastrow(qmcgb.QMC_J2_UD, wl.j2_ud.coefs, wl.j2_ud.rc)
+    if wl.j1 is not None:
+        c.qmc_load_jastrow(qmcgb.QMC_J1, wl.j1.coefs, wl.j1.rc)
+    c.qmc_load_orbitals(table)
+    c.qmc_load_positions(R)
+    c.qmc_recompute()
+    for _ in range(steps):
+        c.qmc_sweep(1, e_host, stats=False)
+    t1 = time.perf_counter()
+    c.close()
+    h2d = table.numel() * 8 + R.numel() * 8 + wl.ions.size * 8
+    moves = wl.n_walkers * wl.n_el * steps
+    return moves / (t1 - t0), h2d / steps, wl.n_walkers * 8
+
+
+def cpu_oracle_rate(wl, target_s=12.0, max_gens=None):
+    """Moves/s of the CPU oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    osys = oracle.OracleSystem(wl)
+    W = wl.n_walkers
+    R = wl.positions()
+    crowd = oracle.OracleCrowd(osys, R)
+    t0 = time.perf_counter()
+    crowd.sweep(1)
+    t1 = time.perf_counter()
+    per_gen = t1 - t0
+    gens = max(1, int(target_s / max(per_gen, 1e-6)))
+    if max_gens:
+        gens = min(gens, max_gens)
+    t0 = time.perf_counter()
+    e, na = crowd.sweep(gens)
+    t1 = time.perf_counter()
+    rate = W * wl.n_el * gens / (t1 - t0)
+    return rate, oracle.num_threads(), f"{gens} generation(s) x {W} walkers x {wl.n_el} electrons"
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pw128")
+    ap.add_argument("--delay-rank", type=int, default=None)
+    ap.add_argument("--update", default=None, choices=[None, "sm", "delayed"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    from paper_2209_14487_gb300 import workloads
+    wl = workloads.WORKLOADS[args.workload]()
+    ws, rank, local = dist_env()
+    update = args.update or "delayed"
+    k = args.delay_rank or 4
+    cfg = {
+        "workload": f"{wl.name}: {wl.n_el} electrons ({wl.n_up}/{wl.n_dn}), {wl.n_orb} orbitals "
+                    f"on {wl.grid}^3, {wl.n_ions} ions, L={wl.L:g}, J1({wl.j1.K if wl.j1 else 0})"
+                    f"+J2({wl.j2_uu.K if wl.j2_uu else 0}), {wl.n_walkers} walkers/GPU, "
+                    f"tau={wl.tau}, FP64 recompute every {wl.n_recompute} generations",
+        "walkers_per_gpu": wl.n_walkers, "electrons": wl.n_el,
+        "step": "one generation (all electrons of all walkers proposed once + E_L)",
+        "l2": "flushed between timed steps (256 MiB write outside the per-step events)",
+    }
+
+    if args.impl == "reference":
+        if ws > 1 and rank != 0:
+            return
+        n_gen = args.steps + args.warmup
+        import oracle
+        oracle.build()
+        osys = oracle.OracleSystem(wl)
+        W = wl.n_walkers
+        crowd = oracle.OracleCrowd(osys, wl.positions())
+        t0 = time.perf_counter()
+        crowd.sweep(1)
+        per_gen = time.perf_counter() - t0
+        # bounded sample: whole run within ~3 minutes; fewer walkers when one generation
+        # of the full crowd is too slow
+        budget = 150.0 / max(1, n_gen)
+        Ws = W if per_gen <= budget else max(1, int(W * budget / per_gen))
+        if Ws < W:
+            crowd = oracle.OracleCrowd(osys, wl.positions()[:Ws])
+        for _ in range(args.warmup):
+            crowd.sweep(1)
+        t0 = time.perf_counter()
+        crowd.sweep(args.steps)
+        dt = time.perf_counter() - t0
+        rate = Ws * wl.n_el * args.steps / dt
+        cores = oracle.num_threads()
+        sample = f"{args.steps} generations x {Ws} of {W} walkers x {wl.n_el} electrons"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2209_14487_gb300 import qmcgb  # noqa: F401
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        uuid = None
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        mixed = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush)
+        fp64 = None
+        if not args.no_fp64:
+            fp64 = time_path(wl, "fp64", "sm", 1, args.steps, args.warmup, rank, flush)
+    torch.cuda.synchronize()
+    barrier(ws)
+
+    moves_step = wl.n_walkers * wl.n_el
+    t_mixed = reduce_max(sum(mixed["ms"]) / 1000.0, ws)
+    value = ws * moves_step * args.steps / t_mixed
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * t_mixed / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": dict(cfg, precision="mixed: fp32 orbitals, Jastrow, "
+                                               "ratios and inverse; fp64 recompute and energy",
+                                               update=f"{update} k={k}",
+                                               parallelism=f"replicas x{ws}")}
+    e_m, s_m = energy_stats(mixed["eloc"])
+    out["energy"] = {"mixed": {"mean": e_m, "sigma": s_m}}
+    if fp64 is not None:
+        t64 = reduce_max(sum(fp64["ms"]) / 1000.0, ws)
+        e_d, s_d = energy_stats(fp64["eloc"])
+        out["fp64"] = {"value": ws * moves_step * args.steps / t64, "unit": UNIT,
+                       "ms_per_step": 1000.0 * t64 / args.steps, "update": "sm"}
+        out["energy"]["fp64"] = {"mean": e_d, "sigma": s_d}
+        out["energy"]["diff_sigma"] = abs(e_m - e_d) / math.hypot(s_m, s_d)
+        out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
+    # roofline of the dominant kernel (the fused move kernel, one launch per plain step)
+    hbm, src = peaks()
+    plain = mixed["plain_ms"] or mixed["ms"]
+    t_launch = statistics.mean(plain) / 1000.0
+    bpm = bytes_per_move(wl.n_orb, wl.n_el, 4, mixed["p_acc"], update, k)
+    achieved = moves_step * bpm / t_launch / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                       "frac": achieved / hbm, "traffic": ncu_traffic("move_kernel<float>"),
+                       "kernel": "move_kernel<float> (fused generation)",
+                       "bytes_per_move": bpm, "acceptance": mixed["p_acc"],
+                       "peak_source": src}
+    out["gpu_launches"] = mixed["launches"]
+    out["clocks"] = clk.summary()
+    if not args.no_e2e:
+        rate, h2d, d2h = e2e_run(wl, "mixed", update, k, args.steps, rank)
+        rate = ws * moves_step * args.steps / reduce_max(moves_step * args.steps / rate, ws)
+        out["e2e"] = {"value": rate, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h,
+                      "note": "create + host loads (table, ions, Jastrow, positions) + recompute "
+                              "+ K sweeps returning E_L to pinned host memory, wall clock"}
+    if rank == 0 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(wl)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample, "cpu": cpu_model()}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

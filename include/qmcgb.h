@@ -1,0 +1,179 @@
+/*
+ * qmcgb.h: C ABI of the GB300 (sm_103a) library for the particle-by-particle (PbyP)
+ * electron move over a crowd of walkers, after Luo, Doak, Kent, "A High-Performance
+ * Design for Hierarchical Parallelism in the QMCPACK Monte Carlo code" (arXiv:2209.14487).
+ *
+ * A crowd (Sec. III: a subset of the walkers operated on as one batch, in lock-step) holds
+ * W walkers of one system.  The calls follow Alg. 1 of the paper:
+ *   line 5-6  propose r'_k                      -> qmc_eval_grad_batch, qmc_propose_move_batch
+ *   line 7-8  ratio Psi(R')/Psi(R), grad_k      -> qmc_propose_move_batch
+ *   line 9    accept / reject (inverse update)  -> qmc_accept_reject_batch
+ *   line 11   local energy                      -> qmc_local_energy_batch
+ *   lines 1-11 fused over generations           -> qmc_sweep
+ *
+ * Wavefunction (the paper gives none; the library's reading):
+ *   Psi(R) = det A_up det A_dn exp(-U),  A_s[l][j] = phi_j(r_l) (tricubic B-spline orbitals
+ *   on a periodic G^3 grid), U = sum_{i<j} u2(r_ij) + sum_{i,I} u1(r_iI) (cubic B-spline
+ *   radial functors, minimum image).  Moves: r' = r + tau grad log Psi + sqrt(tau) chi
+ *   (or no drift), Metropolis(-Hastings) acceptance, counter-based Philox4x32-10 draws.
+ *
+ * Conventions:
+ *  - Every call returns a qmc_status (QMC_OK = 0).  qmc_status_string() names it.
+ *  - Arguments marked "mem" are host pointers (QMC_MEM_HOST) or device pointers
+ *    (QMC_MEM_DEVICE) as the call's `mem` argument says.  Calls with device buffers are
+ *    asynchronous on the crowd's stream; calls with host buffers copy and synchronise.
+ *  - The library owns all device state of a crowd; inputs are copied in; outputs go to
+ *    caller-owned buffers.  Positions are double [W][N][3], electrons 0..n_up-1 are spin
+ *    up, n_up..N-1 spin down.
+ *  - A crowd is not thread safe; distinct crowds may be driven from distinct host
+ *    threads and streams (Sec. III, Alg. 4).
+ *  - Device-side failures (singular matrix, non-finite energy) are recorded in a status
+ *    word that the next synchronising call returns.
+ */
+#ifndef QMCGB_H
+#define QMCGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qmc_status {
+  QMC_OK = 0,
+  QMC_ERR_INVALID_ARG = 1, /* bad pointer, size or enum value                         */
+  QMC_ERR_OOM = 2,         /* device allocation failed                                */
+  QMC_ERR_CUDA = 3,        /* a CUDA runtime call failed                              */
+  QMC_ERR_SINGULAR = 4,    /* zero pivot in the FP64 recompute                         */
+  QMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out                            */
+  QMC_ERR_NAN = 6,         /* non-finite local energy or ratio                         */
+  QMC_ERR_STATE = 7,       /* call out of order (accept without propose, no orbitals)  */
+  QMC_ERR_UNSUPPORTED = 8  /* valid request this build does not serve (size limits)    */
+} qmc_status;
+
+enum { QMC_MEM_HOST = 0, QMC_MEM_DEVICE = 1 };
+enum { QMC_PREC_FP64 = 0, QMC_PREC_MIXED = 1 };
+enum { QMC_UPDATE_SM = 0, QMC_UPDATE_DELAYED = 1 };
+enum { QMC_J1 = 0, QMC_J2_UU = 1, QMC_J2_UD = 2 };
+enum { QMC_DTYPE_F64 = 0, QMC_DTYPE_F32 = 1 };
+
+/* The simulated system (Alg. 1 "R = {r_1 .. r_N}" plus what Psi needs). */
+typedef struct qmc_system_desc {
+  int n_up, n_dn;  /* electrons per spin; this build requires n_up == n_dn >= 1      */
+  int n_orb;       /* orbitals in the table (>= n_up); the first n_up are occupied   */
+  int n_ions;      /* electron-ion Jastrow centres (may be 0)                         */
+  int grid;        /* G: spline grid points per dimension (>= 4)                      */
+  int reserved;
+  double L;        /* periodic cubic cell side (bohr)                                 */
+} qmc_system_desc;
+
+/* How the crowd is driven. */
+typedef struct qmc_run_desc {
+  int n_walkers;    /* W >= 1                                                         */
+  int precision;    /* QMC_PREC_FP64: FP64 everywhere; QMC_PREC_MIXED: FP32 orbitals,  *
+                     * Jastrow, ratios and inverse, FP64 recompute and energy sums     */
+  int update;       /* QMC_UPDATE_SM (rank-1 per accept) or QMC_UPDATE_DELAYED         */
+  int delay_rank;   /* k for QMC_UPDATE_DELAYED, 1..64                                 */
+  int n_recompute;  /* generations between FP64 recomputes of A^-1; 0 = never        */
+  int drift;        /* 1: drift-diffusion proposal with Metropolis-Hastings            */
+  int potential;    /* 1: add the model potential to E_L                              */
+  int reserved;
+  double tau;       /* time step                                                      */
+  uint64_t seed;    /* Philox key: (low 32 bits, walker ^ high 32 bits)               */
+} qmc_run_desc;
+
+/* Per-call statistics of qmc_sweep, accumulated in FP64 over walkers and generations. */
+typedef struct qmc_stats {
+  double e_sum;          /* sum over walkers and generations of E_L                    */
+  double e2_sum;         /* sum of E_L^2                                               */
+  long long n_samples;   /* walkers x generations                                      */
+  long long n_accept;    /* accepted moves                                             */
+  long long n_moves;     /* proposed moves = W x N x generations                       */
+} qmc_stats;
+
+typedef struct qmc_crowd qmc_crowd;
+
+/* Creates a crowd of run->n_walkers walkers of system `sys` on the current CUDA device.
+ * `cuda_stream` is a cudaStream_t (may be NULL: the crowd creates its own stream).
+ * Allocates all device state (O(W N n) for the orbital rows, O(W n^2) for inverses).
+ * Errors: INVALID_ARG (sizes), UNSUPPORTED (n_up != n_dn, grid or n beyond limits), OOM. */
+int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* cuda_stream,
+                     qmc_crowd** out);
+int qmc_crowd_destroy(qmc_crowd* crowd);
+
+/* Electron positions, double [W][N][3] (mem).  Values are wrapped into [0, L).  Marks
+ * the orbital rows and inverses stale: the next move, energy or explicit
+ * qmc_recompute() rebuilds them (Alg. 1 line 3). */
+int qmc_load_positions(qmc_crowd* crowd, const double* R, int mem);
+/* Ion positions, double [n_ions][3] (host). */
+int qmc_load_ions(qmc_crowd* crowd, const double* RI);
+/* Orbital coefficient table [G][G][G][n_orb] (mem), x slowest, orbital fastest, periodic
+ * (node g at x = g L / G), dtype QMC_DTYPE_F64 or F32.  The library adds three ghost
+ * layers, pads the orbital dimension and converts to the crowd's precision. */
+int qmc_load_orbitals(qmc_crowd* crowd, const void* coefs, int dtype, int mem);
+/* Radial functor `kind` with K >= 1 free coefficients c (host) and cutoff rc > 0;
+ * u(r) = sum_m c_{i+m} b_m(r/h - i), h = rc/K, i = floor(r/h), three zero coefficients
+ * follow c_{K-1}; u = 0 for r >= rc.  K = 0 removes the term. */
+int qmc_load_jastrow(qmc_crowd* crowd, int kind, const double* c, int K, double rc);
+
+/* FP64 full recompute: orbital rows from the positions, LU with partial pivoting of
+ * each A_s, A_s^-1, log|det A_s| and sign.  Errors: SINGULAR. */
+int qmc_recompute(qmc_crowd* crowd);
+
+/* grad_k log Psi(R) for electron iel of every walker: grad [W][3] (mem). */
+int qmc_eval_grad_batch(qmc_crowd* crowd, int iel, double* grad, int mem);
+
+/* Proposes electron iel of every walker (Alg. 1 lines 5-8).
+ * rnew [W][3] (mem) gives r'; NULL draws r' = r + tau F + sqrt(tau) chi from the
+ * crowd's counter-based RNG at its current generation.  Outputs (mem, each may be NULL):
+ * ratio [W] = Psi(R')/Psi(R); grad [W][3] = grad_k log Psi(R'); log_ratio [W] =
+ * log|ratio|; rnew_out [W][3] = the proposed, wrapped r'.  The proposal stays pending
+ * for qmc_accept_reject_batch. */
+int qmc_propose_move_batch(qmc_crowd* crowd, int iel, const double* rnew, double* ratio,
+                           double* grad, double* log_ratio, double* rnew_out, int mem);
+
+/* Accepts or rejects the pending proposal of electron iel (Alg. 1 line 9).
+ * accept [W] (mem, nonzero = accept) or NULL for the Metropolis test with the crowd's RNG;
+ * accepted_out [W] (mem, may be NULL) receives the decisions.  Accepting updates the
+ * inverse (Sherman-Morrison, or appends to the delayed window), the orbital rows, the
+ * position and log|det|.  Errors: STATE if no proposal of iel is pending. */
+int qmc_accept_reject_batch(qmc_crowd* crowd, int iel, const uint8_t* accept,
+                            uint8_t* accepted_out, int mem);
+
+/* Local energy of every walker (Alg. 1 line 11): eloc [W] (mem).  Applies pending
+ * delayed updates first. */
+int qmc_local_energy_batch(qmc_crowd* crowd, double* eloc, int mem);
+
+/* n_gen generations in one fused launch per generation: every electron of every walker
+ * proposed once in order, pending updates applied, the FP64 recompute every n_recompute
+ * generations, then E_L.  eloc [n_gen][W] (mem, may be NULL); stats (host, may be NULL:
+ * without it the call does not synchronise). */
+int qmc_sweep(qmc_crowd* crowd, int n_gen, double* eloc, int mem, qmc_stats* stats);
+
+/* Getters (host buffers unless mem says otherwise). */
+int qmc_get_positions(qmc_crowd* crowd, double* R, int mem);
+/* log|Psi| = log|det A_up| + log|det A_dn| - U and sign(Psi), [W] each (host). */
+int qmc_get_logpsi(qmc_crowd* crowd, double* logabs, int* sign);
+/* A_s^-1 of every walker as double [W][n][n], element [w][j][l] = (A_s^-1)[j][l]
+ * (host); applies pending delayed updates first. */
+int qmc_get_inverse(qmc_crowd* crowd, int spin, double* out);
+/* A_s of every walker as double [W][n][n], [w][l][j] = phi_j(r_l) (host). */
+int qmc_get_slater_matrix(qmc_crowd* crowd, int spin, double* out);
+int qmc_get_generation(qmc_crowd* crowd, uint32_t* gen);
+int qmc_set_generation(qmc_crowd* crowd, uint32_t gen);
+/* Number of kernel launches this crowd has issued so far. */
+int qmc_get_launch_count(qmc_crowd* crowd, unsigned long long* count);
+
+/* Checkpoint: positions, generation and RNG seed.  With buf == NULL, *size receives the
+ * byte count; otherwise *size must hold at least that many bytes.  Restoring recomputes
+ * every derived quantity in FP64 from the positions. */
+int qmc_crowd_save(qmc_crowd* crowd, void* buf, size_t* size);
+int qmc_crowd_restore(qmc_crowd* crowd, const void* buf, size_t size);
+
+const char* qmc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCGB_H */

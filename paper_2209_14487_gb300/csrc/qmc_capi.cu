@@ -1,0 +1,730 @@
+// Crowd runtime behind the C ABI of include/qmcgb.h: device state of a crowd of walkers
+// (arXiv:2209.14487, Sec. III "crowd"), its stream, the generation counter of the
+// counter-based RNG and the FP64 recompute cadence.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/qmcgb.h"
+#include "qmc_internal.h"
+
+using qmcgb::Params;
+
+struct qmc_crowd {
+  qmc_system_desc sys;
+  qmc_run_desc run;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int es = 8;  // bytes per element of the crowd's precision
+  Params p{};
+  // device buffers
+  double* d_R = nullptr;
+  void* d_rows = nullptr;
+  void* d_binv = nullptr;
+  double* d_logdet = nullptr;
+  int* d_sign = nullptr;
+  void* d_table = nullptr;
+  void* d_jc = nullptr;
+  double* d_ions = nullptr;
+  int* d_win_m = nullptr;
+  int* d_win_P = nullptr;
+  void* d_win_V = nullptr;
+  void* d_win_S = nullptr;
+  void* d_pend_phi = nullptr;
+  double* d_pend = nullptr;
+  double* d_ws = nullptr;
+  double* d_eloc = nullptr;     // [eloc_cap][W]
+  int eloc_cap = 0;
+  unsigned long long* d_nacc = nullptr;
+  int* d_status = nullptr;
+  double* d_io = nullptr;       // staging for host I/O, 12 W doubles
+  uint8_t* d_io8 = nullptr;     // 2 W bytes
+  // host state
+  int K2 = 0, K1 = 0;
+  double rc2 = 1.0, rc1 = 1.0;
+  std::vector<double> c_uu, c_ud, c_1;
+  bool has_orbitals = false, has_positions = false, stale = true;
+  uint32_t gen = 0;
+  unsigned long long launches = 0;
+};
+
+namespace {
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return QMC_ERR_CUDA;  \
+  } while (0)
+
+bool is_mixed(const qmc_crowd* c) { return c->run.precision == QMC_PREC_MIXED; }
+
+int dmalloc(void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return QMC_ERR_OOM;
+  }
+  return QMC_OK;
+}
+
+void free_all(qmc_crowd* c) {
+  void* ptrs[] = {c->d_R, c->d_rows, c->d_binv, c->d_logdet, c->d_sign, c->d_table,
+                  c->d_jc, c->d_ions, c->d_win_m, c->d_win_P, c->d_win_V, c->d_win_S,
+                  c->d_pend_phi, c->d_pend, c->d_ws, c->d_eloc, c->d_nacc, c->d_status,
+                  c->d_io, c->d_io8};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+void sync_params(qmc_crowd* c) {
+  Params& p = c->p;
+  p.R = c->d_R;
+  p.rows = c->d_rows;
+  p.binv = c->d_binv;
+  p.logdet = c->d_logdet;
+  p.sign = c->d_sign;
+  p.table = c->d_table;
+  p.jc = c->d_jc;
+  p.ions = c->d_ions;
+  p.win_m = c->d_win_m;
+  p.win_P = c->d_win_P;
+  p.win_V = c->d_win_V;
+  p.win_S = c->d_win_S;
+  p.pend_phi = c->d_pend_phi;
+  p.pend = c->d_pend;
+  p.status = c->d_status;
+  p.n_accept = c->d_nacc;
+  p.K2 = c->K2;
+  p.K1 = (c->K1 > 0 && c->sys.n_ions > 0) ? c->K1 : 0;
+  p.rc2 = c->rc2;
+  p.rc1 = c->rc1;
+  p.h2inv = c->K2 > 0 ? c->K2 / c->rc2 : 1.0;
+  p.h1inv = c->K1 > 0 ? c->K1 / c->rc1 : 1.0;
+  p.gen = c->gen;
+  p.iel = 0;
+  p.rnew_in = nullptr;
+  p.ratio_out = p.grad_out = p.logratio_out = p.rnew_out = nullptr;
+  p.accept_in = nullptr;
+  p.accept_out = nullptr;
+  p.eloc_out = nullptr;
+}
+
+int launch_status(qmc_crowd* c, cudaError_t e) {
+  ++c->launches;
+  return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+int move(qmc_crowd* c, int mode) {
+  if (is_mixed(c)) return launch_status(c, qmcgb::launch_move<float>(c->p, mode, c->stream));
+  return launch_status(c, qmcgb::launch_move<double>(c->p, mode, c->stream));
+}
+
+int read_status(qmc_crowd* c) {
+  int st = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) CK(cudaMemset(c->d_status, 0, sizeof(int)));
+  if (st & qmcgb::ST_SINGULAR) return QMC_ERR_SINGULAR;
+  if (st & qmcgb::ST_NAN) return QMC_ERR_NAN;
+  if (st & qmcgb::ST_STATE) return QMC_ERR_STATE;
+  return QMC_OK;
+}
+
+int upload_jastrow(qmc_crowd* c) {
+  const int K2 = c->K2, K1 = c->K1;
+  std::vector<double> h((size_t)2 * (K2 + 3) + K1 + 3, 0.0);
+  for (int m = 0; m < K2; ++m) {
+    h[m] = m < (int)c->c_uu.size() ? c->c_uu[m] : 0.0;
+    h[K2 + 3 + m] = m < (int)c->c_ud.size() ? c->c_ud[m] : 0.0;
+  }
+  for (int m = 0; m < K1; ++m) h[2 * (K2 + 3) + m] = c->c_1[m];
+  if (is_mixed(c)) {
+    std::vector<float> f(h.begin(), h.end());
+    CK(cudaMemcpyAsync(c->d_jc, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    CK(cudaMemcpyAsync(c->d_jc, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  sync_params(c);
+  return QMC_OK;
+}
+
+int rebuild(qmc_crowd* c) {
+  sync_params(c);
+  int st;
+  if (is_mixed(c)) st = launch_status(c, qmcgb::launch_eval_rows<float>(c->p, c->stream));
+  else st = launch_status(c, qmcgb::launch_eval_rows<double>(c->p, c->stream));
+  if (st) return st;
+  if (is_mixed(c)) st = launch_status(c, qmcgb::launch_recompute<float>(c->p, c->d_ws, c->stream));
+  else st = launch_status(c, qmcgb::launch_recompute<double>(c->p, c->d_ws, c->stream));
+  if (st) return st;
+  CK(cudaMemsetAsync(c->d_pend, 0, sizeof(double) * c->run.n_walkers * qmcgb::PEND_STRIDE,
+                     c->stream));
+  c->stale = false;
+  return QMC_OK;
+}
+
+int ensure_ready(qmc_crowd* c) {
+  if (!c->has_orbitals || !c->has_positions) return QMC_ERR_STATE;
+  if (c->stale) {
+    int st = rebuild(c);
+    if (st) return st;
+  }
+  sync_params(c);
+  return QMC_OK;
+}
+
+int check_iel(const qmc_crowd* c, int iel) {
+  return (iel >= 0 && iel < c->p.N) ? QMC_OK : QMC_ERR_INVALID_ARG;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qmc_status_string(int status) {
+  switch (status) {
+    case QMC_OK: return "ok";
+    case QMC_ERR_INVALID_ARG: return "invalid argument";
+    case QMC_ERR_OOM: return "device out of memory";
+    case QMC_ERR_CUDA: return "CUDA runtime error";
+    case QMC_ERR_SINGULAR: return "singular Slater matrix";
+    case QMC_ERR_TIMEOUT: return "bounded device wait ran out";
+    case QMC_ERR_NAN: return "non-finite ratio or local energy";
+    case QMC_ERR_STATE: return "call out of order or missing input";
+    case QMC_ERR_UNSUPPORTED: return "size or option not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* cuda_stream,
+                     qmc_crowd** out) {
+  if (!sys || !run || !out) return QMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (sys->n_up < 1 || sys->n_dn < 0 || sys->n_orb < sys->n_up || sys->n_ions < 0 ||
+      sys->grid < 4 || !(sys->L > 0.0) || run->n_walkers < 1 || !(run->tau > 0.0))
+    return QMC_ERR_INVALID_ARG;
+  if (run->precision != QMC_PREC_FP64 && run->precision != QMC_PREC_MIXED)
+    return QMC_ERR_INVALID_ARG;
+  if (run->update != QMC_UPDATE_SM && run->update != QMC_UPDATE_DELAYED)
+    return QMC_ERR_INVALID_ARG;
+  if (run->update == QMC_UPDATE_DELAYED &&
+      (run->delay_rank < 1 || run->delay_rank > qmcgb::MAX_K))
+    return QMC_ERR_INVALID_ARG;
+  if (run->n_recompute < 0) return QMC_ERR_INVALID_ARG;
+  if (sys->n_dn != sys->n_up) return QMC_ERR_UNSUPPORTED;
+  if (sys->n_up > 1024 || sys->grid > 1024) return QMC_ERR_UNSUPPORTED;
+
+  qmc_crowd* c = new qmc_crowd();
+  c->sys = *sys;
+  c->run = *run;
+  c->es = run->precision == QMC_PREC_MIXED ? 4 : 8;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return QMC_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  Params& p = c->p;
+  const int W = run->n_walkers, n = sys->n_up, N = sys->n_up + sys->n_dn;
+  p.W = W;
+  p.N = N;
+  p.n_up = sys->n_up;
+  p.n = n;
+  p.n_pad = (n + 7) & ~7;
+  p.n_ions = sys->n_ions;
+  p.G = sys->grid;
+  p.GP = sys->grid + 3;
+  p.drift = run->drift ? 1 : 0;
+  p.potential = run->potential ? 1 : 0;
+  p.update = run->update;
+  p.k = run->update == QMC_UPDATE_DELAYED ? run->delay_rank : 1;
+  p.vs = n + 1;
+  p.ks = p.k + 1;
+  p.L = sys->L;
+  p.invL = 1.0 / sys->L;
+  p.tau = run->tau;
+  p.sqrt_tau = std::sqrt(run->tau);
+  p.dgrid = sys->grid / sys->L;
+  p.fx_scale = 4294967296.0 / sys->L;
+  p.fx_unit = sys->L / 4294967296.0;
+  p.seed = run->seed;
+  const int es = c->es;
+
+  // stage the moving spin's inverse in shared memory when the whole CTA fits
+  const int optin = qmcgb::max_smem_optin();
+  p.b_in_smem = 1;
+  size_t smem = qmcgb::move_smem_bytes(p, es);
+  if (optin > 0 && smem > (size_t)optin) {
+    p.b_in_smem = 0;
+    smem = qmcgb::move_smem_bytes(p, es);
+  }
+  if (optin > 0 && smem > (size_t)optin) {
+    delete c;
+    return QMC_ERR_UNSUPPORTED;
+  }
+
+  const size_t GP = (size_t)p.GP;
+  int st = QMC_OK;
+  st |= dmalloc((void**)&c->d_R, sizeof(double) * W * N * 3);
+  st |= dmalloc(&c->d_rows, (size_t)es * W * N * 5 * p.n_pad);
+  st |= dmalloc(&c->d_binv, (size_t)es * W * 2 * n * n);
+  st |= dmalloc((void**)&c->d_logdet, sizeof(double) * W * 2);
+  st |= dmalloc((void**)&c->d_sign, sizeof(int) * W * 2);
+  st |= dmalloc(&c->d_table, (size_t)es * GP * GP * GP * p.n_pad);
+  st |= dmalloc(&c->d_jc, sizeof(double) * (3 * (qmcgb::MAX_KNOTS + 3)));
+  st |= dmalloc((void**)&c->d_ions, sizeof(double) * 3 * (sys->n_ions > 0 ? sys->n_ions : 1));
+  st |= dmalloc((void**)&c->d_win_m, sizeof(int) * W * 2);
+  st |= dmalloc((void**)&c->d_win_P, sizeof(int) * W * 2 * qmcgb::MAX_K);
+  if (p.update == QMC_UPDATE_DELAYED) {
+    st |= dmalloc(&c->d_win_V, (size_t)es * W * 2 * p.k * p.vs);
+    st |= dmalloc(&c->d_win_S, (size_t)es * W * 2 * p.k * p.ks);
+  }
+  st |= dmalloc(&c->d_pend_phi, (size_t)es * W * 5 * p.n_pad);
+  st |= dmalloc((void**)&c->d_pend, sizeof(double) * W * qmcgb::PEND_STRIDE);
+  st |= dmalloc((void**)&c->d_ws, sizeof(double) * W * 2 * 2 * n * n);
+  st |= dmalloc((void**)&c->d_nacc, sizeof(unsigned long long));
+  st |= dmalloc((void**)&c->d_status, sizeof(int));
+  st |= dmalloc((void**)&c->d_io, sizeof(double) * 12 * W);
+  st |= dmalloc((void**)&c->d_io8, 2 * (size_t)W);
+  if (st) {
+    free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return QMC_ERR_OOM;
+  }
+  cudaMemsetAsync(c->d_win_m, 0, sizeof(int) * W * 2, c->stream);
+  cudaMemsetAsync(c->d_pend, 0, sizeof(double) * W * qmcgb::PEND_STRIDE, c->stream);
+  cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), c->stream);
+  cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+  cudaMemsetAsync(c->d_table, 0, (size_t)es * GP * GP * GP * p.n_pad, c->stream);
+  cudaMemsetAsync(c->d_logdet, 0, sizeof(double) * W * 2, c->stream);
+  cudaMemsetAsync(c->d_sign, 0, sizeof(int) * W * 2, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return QMC_ERR_CUDA;
+  }
+  sync_params(c);
+  int js = upload_jastrow(c);
+  if (js) {
+    free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return js;
+  }
+  *out = c;
+  return QMC_OK;
+}
+
+int qmc_crowd_destroy(qmc_crowd* c) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return QMC_OK;
+}
+
+int qmc_load_positions(qmc_crowd* c, const double* R, int mem) {
+  if (!c || !R) return QMC_ERR_INVALID_ARG;
+  const size_t n3 = (size_t)c->p.W * c->p.N * 3;
+  CK(cudaMemcpyAsync(c->d_R, R, n3 * sizeof(double),
+                     mem == QMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  int st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R, n3, c->p.L, c->stream));
+  if (st) return st;
+  if (mem == QMC_MEM_HOST) CK(cudaStreamSynchronize(c->stream));
+  c->has_positions = true;
+  c->stale = true;
+  return QMC_OK;
+}
+
+int qmc_load_ions(qmc_crowd* c, const double* RI) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (c->sys.n_ions == 0) return QMC_OK;
+  if (!RI) return QMC_ERR_INVALID_ARG;
+  std::vector<double> h(RI, RI + 3 * c->sys.n_ions);
+  for (double& x : h) x = x - c->p.L * std::floor(x / c->p.L);
+  CK(cudaMemcpyAsync(c->d_ions, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->stale = true;
+  return QMC_OK;
+}
+
+int qmc_load_orbitals(qmc_crowd* c, const void* coefs, int dtype, int mem) {
+  if (!c || !coefs) return QMC_ERR_INVALID_ARG;
+  if (dtype != QMC_DTYPE_F64 && dtype != QMC_DTYPE_F32) return QMC_ERR_INVALID_ARG;
+  const size_t G = (size_t)c->p.G;
+  const size_t bytes = G * G * G * (size_t)c->sys.n_orb * (dtype == QMC_DTYPE_F32 ? 4 : 8);
+  const void* src = coefs;
+  void* tmp = nullptr;
+  if (mem == QMC_MEM_HOST) {
+    if (dmalloc(&tmp, bytes)) return QMC_ERR_OOM;
+    if (cudaMemcpyAsync(tmp, coefs, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      cudaFree(tmp);
+      return QMC_ERR_CUDA;
+    }
+    src = tmp;
+  }
+  sync_params(c);
+  cudaError_t e;
+  if (is_mixed(c))
+    e = qmcgb::launch_pad_table<float>(c->p, src, dtype == QMC_DTYPE_F32, c->sys.n_orb, c->stream);
+  else
+    e = qmcgb::launch_pad_table<double>(c->p, src, dtype == QMC_DTYPE_F32, c->sys.n_orb, c->stream);
+  ++c->launches;
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess || e2 != cudaSuccess) return QMC_ERR_CUDA;
+  c->has_orbitals = true;
+  c->stale = true;
+  return QMC_OK;
+}
+
+int qmc_load_jastrow(qmc_crowd* c, int kind, const double* coefs, int K, double rc) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (K < 0 || K > qmcgb::MAX_KNOTS || (K > 0 && (!coefs || !(rc > 0.0))))
+    return QMC_ERR_INVALID_ARG;
+  std::vector<double> v(coefs ? coefs : nullptr, coefs ? coefs + K : nullptr);
+  if (kind == QMC_J1) {
+    c->K1 = K;
+    c->rc1 = K > 0 ? rc : 1.0;
+    c->c_1 = v;
+  } else if (kind == QMC_J2_UU || kind == QMC_J2_UD) {
+    // like and unlike pair functors share one knot grid
+    const bool other = kind == QMC_J2_UU ? !c->c_ud.empty() : !c->c_uu.empty();
+    if (K > 0 && other && c->K2 > 0 && (K != c->K2 || rc != c->rc2)) return QMC_ERR_INVALID_ARG;
+    if (kind == QMC_J2_UU) c->c_uu = v;
+    else c->c_ud = v;
+    if (K > 0) {
+      c->K2 = K;
+      c->rc2 = rc;
+    } else if (c->c_uu.empty() && c->c_ud.empty()) {
+      c->K2 = 0;
+    }
+  } else {
+    return QMC_ERR_INVALID_ARG;
+  }
+  c->stale = true;
+  return upload_jastrow(c);
+}
+
+int qmc_recompute(qmc_crowd* c) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (!c->has_orbitals || !c->has_positions) return QMC_ERR_STATE;
+  int st = rebuild(c);
+  if (st) return st;
+  return read_status(c);
+}
+
+int qmc_eval_grad_batch(qmc_crowd* c, int iel, double* grad, int mem) {
+  if (!c || !grad) return QMC_ERR_INVALID_ARG;
+  if (check_iel(c, iel)) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  c->p.iel = iel;
+  c->p.grad_out = mem == QMC_MEM_DEVICE ? grad : c->d_io;
+  st = move(c, qmcgb::MODE_GRAD);
+  if (st) return st;
+  if (mem == QMC_MEM_HOST) {
+    CK(cudaMemcpyAsync(grad, c->d_io, sizeof(double) * 3 * c->p.W, cudaMemcpyDeviceToHost,
+                       c->stream));
+    return read_status(c);
+  }
+  return QMC_OK;
+}
+
+int qmc_propose_move_batch(qmc_crowd* c, int iel, const double* rnew, double* ratio,
+                           double* grad, double* log_ratio, double* rnew_out, int mem) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (check_iel(c, iel)) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  const int W = c->p.W;
+  Params& p = c->p;
+  p.iel = iel;
+  if (mem == QMC_MEM_DEVICE) {
+    p.rnew_in = rnew;
+    p.ratio_out = ratio;
+    p.grad_out = grad;
+    p.logratio_out = log_ratio;
+    p.rnew_out = rnew_out;
+  } else {
+    double* io = c->d_io;
+    if (rnew) {
+      CK(cudaMemcpyAsync(io + 9 * W, rnew, sizeof(double) * 3 * W, cudaMemcpyHostToDevice,
+                         c->stream));
+      p.rnew_in = io + 9 * W;
+    }
+    p.ratio_out = io;
+    p.logratio_out = io + W;
+    p.grad_out = io + 2 * W;
+    p.rnew_out = io + 5 * W;
+  }
+  st = move(c, qmcgb::MODE_PROPOSE);
+  if (st) return st;
+  if (mem == QMC_MEM_HOST) {
+    const double* io = c->d_io;
+    if (ratio) CK(cudaMemcpyAsync(ratio, io, sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream));
+    if (log_ratio)
+      CK(cudaMemcpyAsync(log_ratio, io + W, sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream));
+    if (grad)
+      CK(cudaMemcpyAsync(grad, io + 2 * W, sizeof(double) * 3 * W, cudaMemcpyDeviceToHost, c->stream));
+    if (rnew_out)
+      CK(cudaMemcpyAsync(rnew_out, io + 5 * W, sizeof(double) * 3 * W, cudaMemcpyDeviceToHost,
+                         c->stream));
+    return read_status(c);
+  }
+  return QMC_OK;
+}
+
+int qmc_accept_reject_batch(qmc_crowd* c, int iel, const uint8_t* accept, uint8_t* accepted_out,
+                            int mem) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (check_iel(c, iel)) return QMC_ERR_INVALID_ARG;
+  if (!c->has_orbitals || !c->has_positions || c->stale) return QMC_ERR_STATE;
+  sync_params(c);
+  const int W = c->p.W;
+  Params& p = c->p;
+  p.iel = iel;
+  if (mem == QMC_MEM_DEVICE) {
+    p.accept_in = accept;
+    p.accept_out = accepted_out;
+  } else {
+    if (accept) {
+      CK(cudaMemcpyAsync(c->d_io8, accept, W, cudaMemcpyHostToDevice, c->stream));
+      p.accept_in = c->d_io8;
+    }
+    p.accept_out = c->d_io8 + W;
+  }
+  int st = move(c, qmcgb::MODE_ACCEPT);
+  if (st) return st;
+  if (mem == QMC_MEM_HOST) {
+    if (accepted_out)
+      CK(cudaMemcpyAsync(accepted_out, c->d_io8 + W, W, cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+  }
+  return QMC_OK;
+}
+
+int qmc_local_energy_batch(qmc_crowd* c, double* eloc, int mem) {
+  if (!c || !eloc) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  c->p.eloc_out = mem == QMC_MEM_DEVICE ? eloc : c->d_io;
+  st = move(c, qmcgb::MODE_ELOC);
+  if (st) return st;
+  if (mem == QMC_MEM_HOST) {
+    CK(cudaMemcpyAsync(eloc, c->d_io, sizeof(double) * c->p.W, cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+  }
+  return QMC_OK;
+}
+
+int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) {
+  if (!c || n_gen < 0) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  const int W = c->p.W;
+  const bool need_buf = stats || (eloc && mem == QMC_MEM_HOST);
+  if (need_buf && c->eloc_cap < n_gen) {
+    if (c->d_eloc) cudaFree(c->d_eloc);
+    c->d_eloc = nullptr;
+    c->eloc_cap = 0;
+    if (dmalloc((void**)&c->d_eloc, sizeof(double) * (size_t)n_gen * W)) return QMC_ERR_OOM;
+    c->eloc_cap = n_gen;
+  }
+  if (stats) CK(cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), c->stream));
+  for (int g = 0; g < n_gen; ++g) {
+    sync_params(c);
+    Params& p = c->p;
+    if (eloc && mem == QMC_MEM_DEVICE) p.eloc_out = eloc + (size_t)g * W;
+    else if (need_buf) p.eloc_out = c->d_eloc + (size_t)g * W;
+    else p.eloc_out = nullptr;
+    p.n_accept = stats ? c->d_nacc : nullptr;
+    const bool due = c->run.n_recompute > 0 && ((c->gen + 1) % (uint32_t)c->run.n_recompute) == 0;
+    if (!due) {
+      st = move(c, qmcgb::MODE_SWEEP);
+      if (st) return st;
+    } else {
+      st = move(c, qmcgb::MODE_SWEEP_NOE);
+      if (st) return st;
+      if (is_mixed(c)) st = launch_status(c, qmcgb::launch_recompute<float>(p, c->d_ws, c->stream));
+      else st = launch_status(c, qmcgb::launch_recompute<double>(p, c->d_ws, c->stream));
+      if (st) return st;
+      if (p.eloc_out) {
+        st = move(c, qmcgb::MODE_ELOC);
+        if (st) return st;
+      }
+    }
+    c->gen += 1;
+  }
+  if (eloc && mem == QMC_MEM_HOST)
+    CK(cudaMemcpyAsync(eloc, c->d_eloc, sizeof(double) * (size_t)n_gen * W,
+                       cudaMemcpyDeviceToHost, c->stream));
+  if (stats) {
+    std::vector<double> h((size_t)n_gen * W);
+    CK(cudaMemcpyAsync(h.data(), c->d_eloc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    unsigned long long na = 0;
+    CK(cudaMemcpyAsync(&na, c->d_nacc, sizeof(na), cudaMemcpyDeviceToHost, c->stream));
+    st = read_status(c);
+    double s1 = 0.0, s2 = 0.0;
+    for (double e : h) {
+      s1 += e;
+      s2 += e * e;
+    }
+    stats->e_sum = s1;
+    stats->e2_sum = s2;
+    stats->n_samples = (long long)h.size();
+    stats->n_accept = (long long)na;
+    stats->n_moves = (long long)n_gen * W * c->p.N;
+    return st;
+  }
+  if (eloc && mem == QMC_MEM_HOST) return read_status(c);
+  return QMC_OK;
+}
+
+int qmc_get_positions(qmc_crowd* c, double* R, int mem) {
+  if (!c || !R) return QMC_ERR_INVALID_ARG;
+  const size_t bytes = sizeof(double) * c->p.W * c->p.N * 3;
+  CK(cudaMemcpyAsync(R, c->d_R, bytes,
+                     mem == QMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  if (mem == QMC_MEM_HOST) CK(cudaStreamSynchronize(c->stream));
+  return QMC_OK;
+}
+
+int qmc_get_logpsi(qmc_crowd* c, double* logabs, int* sign) {
+  if (!c || !logabs || !sign) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  const int W = c->p.W;
+  if (is_mixed(c)) st = launch_status(c, qmcgb::launch_jastrow_U<float>(c->p, c->d_io, c->stream));
+  else st = launch_status(c, qmcgb::launch_jastrow_U<double>(c->p, c->d_io, c->stream));
+  if (st) return st;
+  std::vector<double> U(W), ld(2 * W);
+  std::vector<int> sg(2 * W);
+  CK(cudaMemcpyAsync(U.data(), c->d_io, sizeof(double) * W, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(ld.data(), c->d_logdet, sizeof(double) * 2 * W, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(sg.data(), c->d_sign, sizeof(int) * 2 * W, cudaMemcpyDeviceToHost,
+                     c->stream));
+  st = read_status(c);
+  for (int w = 0; w < W; ++w) {
+    logabs[w] = ld[2 * w] + ld[2 * w + 1] - U[w];
+    sign[w] = sg[2 * w] * sg[2 * w + 1];
+  }
+  return st;
+}
+
+int qmc_get_inverse(qmc_crowd* c, int spin, double* out) {
+  if (!c || !out || (spin != 0 && spin != 1)) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  st = move(c, qmcgb::MODE_FLUSH);
+  if (st) return st;
+  const int W = c->p.W, n = c->p.n, es = c->es;
+  std::vector<unsigned char> h((size_t)es * W * 2 * n * n);
+  CK(cudaMemcpyAsync(h.data(), c->d_binv, h.size(), cudaMemcpyDeviceToHost, c->stream));
+  st = read_status(c);
+  for (int w = 0; w < W; ++w)
+    for (int l = 0; l < n; ++l)
+      for (int j = 0; j < n; ++j) {
+        const size_t src = (((size_t)w * 2 + spin) * n + l) * n + j;  // B^T[l][j]
+        const double v = es == 4 ? (double)((const float*)h.data())[src]
+                                 : ((const double*)h.data())[src];
+        out[((size_t)w * n + j) * n + l] = v;
+      }
+  return st;
+}
+
+int qmc_get_slater_matrix(qmc_crowd* c, int spin, double* out) {
+  if (!c || !out || (spin != 0 && spin != 1)) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  const int W = c->p.W, n = c->p.n, N = c->p.N, np = c->p.n_pad, es = c->es;
+  std::vector<unsigned char> h((size_t)es * W * N * 5 * np);
+  CK(cudaMemcpyAsync(h.data(), c->d_rows, h.size(), cudaMemcpyDeviceToHost, c->stream));
+  st = read_status(c);
+  for (int w = 0; w < W; ++w)
+    for (int l = 0; l < n; ++l)
+      for (int j = 0; j < n; ++j) {
+        const size_t src = (((size_t)w * N + spin * c->p.n_up + l) * 5) * np + j;
+        out[((size_t)w * n + l) * n + j] =
+            es == 4 ? (double)((const float*)h.data())[src] : ((const double*)h.data())[src];
+      }
+  return st;
+}
+
+int qmc_get_generation(qmc_crowd* c, uint32_t* gen) {
+  if (!c || !gen) return QMC_ERR_INVALID_ARG;
+  *gen = c->gen;
+  return QMC_OK;
+}
+
+int qmc_set_generation(qmc_crowd* c, uint32_t gen) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  c->gen = gen;
+  return QMC_OK;
+}
+
+int qmc_get_launch_count(qmc_crowd* c, unsigned long long* count) {
+  if (!c || !count) return QMC_ERR_INVALID_ARG;
+  *count = c->launches;
+  return QMC_OK;
+}
+
+namespace {
+struct SaveHeader {
+  uint64_t magic;
+  int32_t W, N;
+  uint32_t gen, pad;
+  uint64_t seed;
+};
+constexpr uint64_t kMagic = 0x31424743514d51ull;  // "QMQCGB1"
+}  // namespace
+
+int qmc_crowd_save(qmc_crowd* c, void* buf, size_t* size) {
+  if (!c || !size) return QMC_ERR_INVALID_ARG;
+  const size_t need = sizeof(SaveHeader) + sizeof(double) * c->p.W * c->p.N * 3;
+  if (!buf) {
+    *size = need;
+    return QMC_OK;
+  }
+  if (*size < need) return QMC_ERR_INVALID_ARG;
+  SaveHeader h{kMagic, c->p.W, c->p.N, c->gen, 0u, c->run.seed};
+  std::memcpy(buf, &h, sizeof(h));
+  int st = qmc_get_positions(c, (double*)((char*)buf + sizeof(h)), QMC_MEM_HOST);
+  *size = need;
+  return st;
+}
+
+int qmc_crowd_restore(qmc_crowd* c, const void* buf, size_t size) {
+  if (!c || !buf || size < sizeof(SaveHeader)) return QMC_ERR_INVALID_ARG;
+  SaveHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kMagic || h.W != c->p.W || h.N != c->p.N ||
+      size < sizeof(h) + sizeof(double) * c->p.W * c->p.N * 3)
+    return QMC_ERR_INVALID_ARG;
+  c->gen = h.gen;
+  c->run.seed = h.seed;
+  c->p.seed = h.seed;
+  int st = qmc_load_positions(c, (const double*)((const char*)buf + sizeof(h)), QMC_MEM_HOST);
+  if (st) return st;
+  if (c->has_orbitals) return qmc_recompute(c);
+  return QMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,308 @@
+// Device helpers of the PbyP move (arXiv:2209.14487, Alg. 1 lines 5-11) for sm_103a.
+#pragma once
+#include <cstdint>
+
+#include "qmc_internal.h"
+
+namespace qmcgb {
+
+// ---------------------------------------------------------------------------------------
+// Precision traits.  FP64: positions and every quantity in double.  Mixed: orbitals,
+// Jastrow, ratios and the inverse in float; electron and ion positions additionally held
+// as 32-bit fixed point (x = q L / 2^32), so the minimum image is an integer subtraction
+// and the spline cell an integer multiply (no FP64 arithmetic in the hot loop).
+// ---------------------------------------------------------------------------------------
+template <typename T> struct IsMixed { static constexpr bool value = false; };
+template <> struct IsMixed<float> { static constexpr bool value = true; };
+
+// ---------------------------------------------------------------------------------------
+// Counter-based RNG: Philox4x32-10 (Salmon et al., SC'11), stateless per (walker, draw).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// 53-bit uniform in (0, 1]: (k + 1/2) 2^-53, k = (a >> 5) 2^26 + (b >> 6).
+__device__ __forceinline__ double uniform53(uint32_t a, uint32_t b) {
+  const unsigned long long k = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+  return __dadd_rn(__ull2double_rn(k), 0.5) * 0x1p-53;
+}
+
+// The draws of one proposal: out = (chi_x, chi_y, chi_z, u_accept).  Key (seed_lo,
+// walker ^ seed_hi); counter (gen, electron, slot, 0); Box-Muller on slots 0 and 1,
+// the acceptance uniform from slot 2.
+__device__ __forceinline__ void move_draws(uint64_t seed, uint32_t walker, uint32_t gen,
+                                           uint32_t iel, double* out) {
+  const uint32_t k0 = (uint32_t)seed, k1 = walker ^ (uint32_t)(seed >> 32);
+  const double two_pi = 6.283185307179586476925286766559;
+  uint32_t c[4] = {gen, iel, 0u, 0u};
+  philox4x32_10(c, k0, k1);
+  double u1 = uniform53(c[0], c[1]), u2 = uniform53(c[2], c[3]);
+  double rad = sqrt(-2.0 * log(u1));
+  out[0] = rad * cos(two_pi * u2);
+  out[1] = rad * sin(two_pi * u2);
+  uint32_t c2[4] = {gen, iel, 1u, 0u};
+  philox4x32_10(c2, k0, k1);
+  double u3 = uniform53(c2[0], c2[1]), u4 = uniform53(c2[2], c2[3]);
+  out[2] = sqrt(-2.0 * log(u3)) * cos(two_pi * u4);
+  uint32_t c3[4] = {gen, iel, 2u, 0u};
+  philox4x32_10(c3, k0, k1);
+  out[3] = uniform53(c3[0], c3[1]);
+}
+
+__device__ __forceinline__ double accept_uniform(uint64_t seed, uint32_t walker, uint32_t gen,
+                                                 uint32_t iel) {
+  uint32_t c[4] = {gen, iel, 2u, 0u};
+  philox4x32_10(c, (uint32_t)seed, walker ^ (uint32_t)(seed >> 32));
+  return uniform53(c[0], c[1]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Uniform cubic B-spline basis: weight q of a cell at t (q = 0..3 value, 4..7 first
+// derivative, 8..11 second derivative, all in cell units).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T basis_one(T t, int q) {
+  const T t2 = t * t, t3 = t2 * t, s = T(1) - t;
+  const T sixth = T(1) / T(6);
+  switch (q) {
+    case 0: return s * s * s * sixth;
+    case 1: return (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+    case 2: return (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
+    case 3: return t3 * sixth;
+    case 4: return T(-0.5) * s * s;
+    case 5: return T(1.5) * t2 - T(2) * t;
+    case 6: return T(-1.5) * t2 + t + T(0.5);
+    case 7: return T(0.5) * t2;
+    case 8: return s;
+    case 9: return T(3) * t - T(2);
+    case 10: return T(-3) * t + T(1);
+    default: return t;
+  }
+}
+
+// All twelve weights of one dimension at t (value, first, second derivative).
+template <typename T>
+__device__ __forceinline__ void basis12(T t, T* w) {
+  const T t2 = t * t, t3 = t2 * t, s = T(1) - t;
+  const T sixth = T(1) / T(6);
+  w[0] = s * s * s * sixth;
+  w[1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+  w[2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
+  w[3] = t3 * sixth;
+  w[4] = T(-0.5) * s * s;
+  w[5] = T(1.5) * t2 - T(2) * t;
+  w[6] = T(-1.5) * t2 + t + T(0.5);
+  w[7] = T(0.5) * t2;
+  w[8] = s;
+  w[9] = T(3) * t - T(2);
+  w[10] = T(-3) * t + T(1);
+  w[11] = t;
+}
+
+// Radial functor u(r) with K free coefficients c[0..K-1] followed by three zeros:
+// i = floor(r h^-1) (at most K-1), u = sum_m c[i+m] b_m(t); zero for r >= rc.
+template <typename T>
+__device__ __forceinline__ void radial(const T* __restrict__ c, int K, T hinv, T rc, T r, T& u,
+                                       T& du, T& d2u) {
+  u = du = d2u = T(0);
+  if (!(r < rc)) return;
+  const T x = r * hinv;
+  int i = (int)floor(x);
+  i = i > K - 1 ? K - 1 : (i < 0 ? 0 : i);
+  const T t = x - T(i);
+  const T t2 = t * t, t3 = t2 * t, s = T(1) - t;
+  const T sixth = T(1) / T(6);
+  const T c0 = c[i], c1 = c[i + 1], c2 = c[i + 2], c3 = c[i + 3];
+  u = (c0 * s * s * s + c1 * (T(3) * t3 - T(6) * t2 + T(4)) +
+       c2 * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + c3 * t3) * sixth;
+  du = (c0 * (T(-0.5) * s * s) + c1 * (T(1.5) * t2 - T(2) * t) +
+        c2 * (T(-1.5) * t2 + t + T(0.5)) + c3 * (T(0.5) * t2)) * hinv;
+  d2u = (c0 * s + c1 * (T(3) * t - T(2)) + c2 * (T(-3) * t + T(1)) + c3 * t) * hinv * hinv;
+}
+
+// ---------------------------------------------------------------------------------------
+// Minimum-image displacements.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void disp_f64(const double* a, const double* b, double L, double invL,
+                                         double* d) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double x = a[k] - b[k];
+    d[k] = x - L * rint(x * invL);
+  }
+}
+
+// Fixed point: the signed 32-bit difference is the minimum image exactly.
+__device__ __forceinline__ void disp_fx(const uint32_t* a, const uint32_t* b, float unit,
+                                        float* d) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = (float)(int32_t)(a[k] - b[k]) * unit;
+}
+
+__device__ __forceinline__ uint32_t to_fixed(double x, double scale) {
+  return (uint32_t)__double2ull_rn(x * scale);
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L, double invL) {
+  double y = x - L * floor(x * invL);
+  return y;
+}
+
+// ---------------------------------------------------------------------------------------
+// Reductions.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums V values over the CTA; thread 0 receives the totals in v.  `red` holds
+// NWARP * V values; the caller syncs before `red` is reused.
+template <int V, typename R>
+__device__ __forceinline__ void block_sum_to0(R* v, R* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < V; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) red[warp * V + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      R acc = red[q];
+      for (int wi = 1; wi < NWARP; ++wi) acc += red[wi * V + q];
+      v[q] = acc;
+    }
+  }
+}
+
+// Eight values summed over a warp by recursive halving (9 shuffles instead of 40): lane L
+// ends with the warp total of value 4*bit4(L) + 2*bit3(L) + bit2(L).
+template <typename R>
+__device__ __forceinline__ R warp_sum8_transposed(const R* v) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  R a[4], b[2];
+  const bool u4 = lane & 16, u3 = lane & 8, u2 = lane & 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const R send = u4 ? v[q] : v[q + 4];
+    const R keep = u4 ? v[q + 4] : v[q];
+    a[q] = keep + __shfl_xor_sync(full, send, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const R send = u3 ? a[q] : a[q + 2];
+    const R keep = u3 ? a[q + 2] : a[q];
+    b[q] = keep + __shfl_xor_sync(full, send, 8);
+  }
+  R c = (u2 ? b[1] : b[0]) + __shfl_xor_sync(full, u2 ? b[0] : b[1], 4);
+  c += __shfl_xor_sync(full, c, 2);
+  c += __shfl_xor_sync(full, c, 1);
+  return c;
+}
+
+// Sums eight values over the CTA and hands every thread all eight totals (one barrier).
+// `red` holds NWARP * 8 values and must not be rewritten before every warp has read it.
+template <typename R>
+__device__ __forceinline__ void block_allreduce8(R* v, R* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const R c = warp_sum8_transposed(v);
+  if ((lane & 3) == 0) red[warp * 8 + (lane >> 2)] = c;
+  __syncthreads();
+  R t = R(0);
+  if (lane < 8) {
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) t += red[w * 8 + lane];
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
+}
+
+// ---------------------------------------------------------------------------------------
+// Tricubic B-spline orbital stencil: for item (j, a) the 16 coefficients of orbital j at
+// x offset a (4 y rows x 4 consecutive z) -- one coalesced read per (y, z) across the
+// orbital lanes of a warp (orbital-fastest table with three ghost layers, so the stencil
+// of cell (cx, cy, cz) starts at padded index (cx, cy, cz) and never wraps).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stencil_load(const T* __restrict__ table, int GP, int n_pad,
+                                             int cx, int cy, int cz, int j, int a, T* cf) {
+  const T* base = table + (((size_t)(cx + a) * GP + cy) * GP + cz) * (size_t)n_pad + j;
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cf[b * 4 + c] = __ldg(base + ((size_t)b * GP + c) * n_pad);
+}
+
+// Partial sums over (y, z) of one item: value, d/dy, d/dz and the y+z second derivatives,
+// with the y and z basis weights w[12 * dim + q].
+template <typename T>
+__device__ __forceinline__ void stencil_reduce(const T* cf, const T* w, T* out4) {
+  T v = 0, gy = 0, gz = 0, l = 0;
+  const T* wy = w + 12;
+  const T* wz = w + 24;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const T x = cf[b * 4 + c];
+      s0 += wz[c] * x;
+      s1 += wz[4 + c] * x;
+      s2 += wz[8 + c] * x;
+    }
+    v += wy[b] * s0;
+    gy += wy[4 + b] * s0;
+    gz += wy[b] * s1;
+    l += wy[8 + b] * s0 + wy[b] * s2;
+  }
+  out4[0] = v;
+  out4[1] = gy;
+  out4[2] = gz;
+  out4[3] = l;
+}
+
+// Combines the four x offsets of orbital j: phi, grad (3) and Laplacian.
+template <typename T>
+__device__ __forceinline__ void stencil_combine(const T* part, int n_pad, int j, const T* w,
+                                                T dinv, T* o5) {
+  T v = 0, gx = 0, gy = 0, gz = 0, l = 0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const T pv = part[(a * 4 + 0) * n_pad + j];
+    const T py = part[(a * 4 + 1) * n_pad + j];
+    const T pz = part[(a * 4 + 2) * n_pad + j];
+    const T pl = part[(a * 4 + 3) * n_pad + j];
+    v += w[a] * pv;
+    gx += w[4 + a] * pv;
+    gy += w[a] * py;
+    gz += w[a] * pz;
+    l += w[8 + a] * pv + w[a] * pl;
+  }
+  o5[0] = v;
+  o5[1] = gx * dinv;
+  o5[2] = gy * dinv;
+  o5[3] = gz * dinv;
+  o5[4] = l * dinv * dinv;
+}
+
+}  // namespace qmcgb

@@ -1,0 +1,92 @@
+// Internal interface between the CUDA translation units of libqmcgb (not part of the ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace qmcgb {
+
+constexpr int NT = 256;            // threads per CTA of the walker kernels
+constexpr int NWARP = NT / 32;
+constexpr int MAX_K = 64;          // largest delay rank
+constexpr int MAX_KNOTS = 64;      // largest radial functor (free coefficients)
+constexpr int PEND_STRIDE = 24;    // doubles of pending-proposal state per walker
+
+// pending-proposal slots (doubles)
+enum {
+  P_R = 0, P_DISP = 3, P_FP = 6, P_RHOD = 9, P_RHO = 10, P_DU = 11, P_LOGGF = 12,
+  P_IEL = 13, P_VALID = 14
+};
+
+enum Mode {
+  MODE_SWEEP = 0,    // one generation: every electron moved once, windows applied, E_L
+  MODE_GRAD = 1,     // grad log Psi of electron iel at the current positions
+  MODE_PROPOSE = 2,  // ratio and grad at r' for electron iel, kept pending
+  MODE_ACCEPT = 3,   // accept / reject the pending proposal of electron iel
+  MODE_ELOC = 4,     // apply windows, E_L
+  MODE_FLUSH = 5,    // apply windows only
+  MODE_SWEEP_NOE = 6 // MODE_SWEEP without E_L (a recompute comes first)
+};
+
+// status bits written by kernels
+enum { ST_SINGULAR = 1, ST_NAN = 2, ST_STATE = 4 };
+
+struct Params {
+  int W, N, n_up, n;        // n = electrons per spin = occupied orbitals
+  int n_pad;                // orbital stride of the table and of the rows
+  int n_ions, G, GP;        // GP = G + 3 (ghost layers)
+  int drift, potential, update, k;
+  int K2, K1;               // free radial coefficients (0 = term absent)
+  int b_in_smem;            // inverse of the moving spin staged in shared memory
+  int skip_eloc;            // sweep without the local energy (a recompute comes first)
+  int vs, ks;               // padded strides of the window's V rows and S^-1 rows
+  uint32_t gen;
+  double L, invL, tau, sqrt_tau, dgrid;   // dgrid = G / L
+  double rc2, rc1, h2inv, h1inv;
+  double fx_scale, fx_unit;               // 2^32 / L and L / 2^32 (fixed-point positions)
+  uint64_t seed;
+  const void* table;        // [GP^3][n_pad] T
+  const void* jc;           // T [K2+3] like, [K2+3] unlike, [K1+3] electron-ion
+  const double* ions;       // [n_ions][3]
+  double* R;                // [W][N][3]
+  void* rows;               // [W][N][5][n_pad] T: phi, dphi/dx, dphi/dy, dphi/dz, lap phi
+  void* binv;               // [W][2][n][n] T: B^T, [k][j] = (A^-1)[j][k]
+  double* logdet;           // [W][2]
+  int* sign;                // [W][2]
+  int* win_m;               // [W][2]
+  int* win_P;               // [W][2][MAX_K]
+  void* win_V;              // [W][2][k][vs] T
+  void* win_S;              // [W][2][k][ks] T  (S^-1)
+  void* pend_phi;           // [W][5][n_pad] T
+  double* pend;             // [W][PEND_STRIDE]
+  int iel;
+  const double* rnew_in;    // [W][3] or null
+  double* ratio_out;
+  double* grad_out;
+  double* logratio_out;
+  double* rnew_out;
+  const uint8_t* accept_in; // [W] or null
+  uint8_t* accept_out;
+  double* eloc_out;         // [W]
+  unsigned long long* n_accept;
+  int* status;
+};
+
+size_t move_smem_bytes(const Params& p, int elem_bytes);
+int max_smem_optin();
+
+template <typename T>
+cudaError_t launch_move(const Params& p, int mode, cudaStream_t s);
+template <typename T>
+cudaError_t launch_eval_rows(const Params& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int n_orb,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s);
+cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s);
+
+}  // namespace qmcgb

@@ -1,0 +1,289 @@
+// Set-up and recompute kernels: orbital rows from positions (Alg. 1 line 3), the FP64
+// full recompute of A^-1 and log|det| by LU with partial pivoting, the ghost-padded
+// orbital table, the Jastrow exponent U for log|Psi|, and position wrapping.
+#include <cmath>
+
+#include "qmc_device.cuh"
+#include "qmc_internal.h"
+
+namespace qmcgb {
+
+// One CTA per (walker, electron): phi, grad phi, lap phi of the occupied orbitals at r_i.
+template <typename T>
+__global__ void __launch_bounds__(NT) eval_rows_kernel(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* part = (T*)smem;  // [16][n_pad]
+  __shared__ T wts[48];
+  __shared__ int cell[3];
+  __shared__ T tt[3];
+  const int w = blockIdx.x / p.N, i = blockIdx.x - w * p.N;
+  const int n = p.n, n_pad = p.n_pad;
+  if (threadIdx.x < 3) {
+    const int d = threadIdx.x;
+    const double x = p.R[((size_t)w * p.N + i) * 3 + d];
+    if constexpr (IsMixed<T>::value) {
+      const uint32_t q = to_fixed(x, p.fx_scale);
+      const unsigned long long prod = (unsigned long long)q * (unsigned long long)p.G;
+      cell[d] = (int)(prod >> 32);
+      tt[d] = (float)(uint32_t)prod * 0x1p-32f;
+    } else {
+      const double s = x * p.dgrid;
+      int g = (int)floor(s);
+      g = g > p.G - 1 ? p.G - 1 : (g < 0 ? 0 : g);
+      cell[d] = g;
+      tt[d] = s - (double)g;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) basis12(tt[threadIdx.x], wts + 12 * threadIdx.x);
+  __syncthreads();
+  const T* table = (const T*)p.table;
+  for (int it = threadIdx.x; it < 4 * n; it += NT) {
+    T cf[16], o4[4];
+    stencil_load(table, p.GP, n_pad, cell[0], cell[1], cell[2], it % n, it / n, cf);
+    stencil_reduce(cf, wts, o4);
+    const int j = it % n, a = it / n;
+    for (int q = 0; q < 4; ++q) part[(a * 4 + q) * n_pad + j] = o4[q];
+  }
+  __syncthreads();
+  T* rw = (T*)p.rows + ((size_t)w * p.N + i) * 5 * n_pad;
+  for (int j = threadIdx.x; j < n; j += NT) {
+    T o5[5];
+    stencil_combine(part, n_pad, j, wts, (T)p.dgrid, o5);
+    for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = o5[q];
+  }
+}
+
+// One CTA per (walker, spin): FP64 LU with partial pivoting (row exchanges) of A_s, then
+// the columns of A_s^-1 by forward/back substitution; writes B^T = (A^-1)^T in the
+// crowd's precision, log|det A_s| and its sign, and empties the delayed window.
+// `ws` is scratch: 2 n^2 doubles per (walker, spin).
+template <typename T>
+__global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* ws) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* piv = (int*)smem;  // [n]
+  __shared__ double red_v[NWARP];
+  __shared__ int red_i[NWARP];
+  __shared__ int s_piv, s_sing, s_sign;
+  __shared__ double s_logabs;
+  const int ws_id = blockIdx.x, w = ws_id / 2, s = ws_id - 2 * w;
+  const int n = p.n, n_pad = p.n_pad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* LU = ws + (size_t)ws_id * 2 * n * n;
+  double* X = LU + (size_t)n * n;
+  const T* rows = (const T*)p.rows + (size_t)w * p.N * 5 * n_pad;
+  for (int e = tid; e < n * n; e += NT) {
+    const int l = e / n, j = e - l * n;
+    LU[e] = (double)rows[((size_t)(s * p.n_up + l)) * 5 * n_pad + j];
+  }
+  if (tid == 0) { s_sing = 0; s_sign = 1; s_logabs = 0.0; }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < n; i += NT) {
+      const double v = fabs(LU[(size_t)i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = red_v[0];
+      int ib = red_i[0];
+      for (int q = 1; q < NWARP; ++q)
+        if (red_v[q] > b || (red_v[q] == b && red_i[q] < ib)) { b = red_v[q]; ib = red_i[q]; }
+      piv[k] = ib;
+      s_piv = ib;
+      if (!(b > 0.0)) s_sing = 1;
+    }
+    __syncthreads();
+    if (s_sing) break;
+    const int pk = s_piv;
+    if (pk != k) {
+      for (int j = tid; j < n; j += NT) {
+        const double t = LU[(size_t)k * n + j];
+        LU[(size_t)k * n + j] = LU[(size_t)pk * n + j];
+        LU[(size_t)pk * n + j] = t;
+      }
+    }
+    __syncthreads();
+    const double akk = LU[(size_t)k * n + k];
+    if (tid == 0) {
+      if (pk != k) s_sign = -s_sign;
+      if (akk < 0.0) s_sign = -s_sign;
+      s_logabs += log(fabs(akk));
+    }
+    for (int i = k + 1 + tid; i < n; i += NT) LU[(size_t)i * n + k] /= akk;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int e = tid; e < m * m; e += NT) {
+      const int i = k + 1 + e / m, j = k + 1 + (e - (e / m) * m);
+      LU[(size_t)i * n + j] -= LU[(size_t)i * n + k] * LU[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  if (s_sing) {
+    if (tid == 0) {
+      atomicOr(p.status, ST_SINGULAR);
+      p.logdet[w * 2 + s] = -INFINITY;
+      p.sign[w * 2 + s] = 0;
+    }
+    return;
+  }
+  for (int col = tid; col < n; col += NT) {
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + col] = (i == col) ? 1.0 : 0.0;
+    for (int k = 0; k < n; ++k) {
+      const int pk = piv[k];
+      if (pk != k) {
+        const double t = X[(size_t)k * n + col];
+        X[(size_t)k * n + col] = X[(size_t)pk * n + col];
+        X[(size_t)pk * n + col] = t;
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      double acc = X[(size_t)i * n + col];
+      for (int j = 0; j < i; ++j) acc -= LU[(size_t)i * n + j] * X[(size_t)j * n + col];
+      X[(size_t)i * n + col] = acc;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double acc = X[(size_t)i * n + col];
+      for (int j = i + 1; j < n; ++j) acc -= LU[(size_t)i * n + j] * X[(size_t)j * n + col];
+      X[(size_t)i * n + col] = acc / LU[(size_t)i * n + i];
+    }
+  }
+  __syncthreads();
+  T* Bg = (T*)p.binv + ((size_t)w * 2 + s) * n * n;
+  for (int e = tid; e < n * n; e += NT) {
+    const int k = e / n, i = e - k * n;  // B^T[k][i] = (A^-1)[i][k]
+    Bg[e] = (T)X[(size_t)i * n + k];
+  }
+  if (tid == 0) {
+    p.logdet[w * 2 + s] = s_logabs;
+    p.sign[w * 2 + s] = s_sign;
+    if (p.win_m) p.win_m[w * 2 + s] = 0;
+  }
+}
+
+// Orbital table [G][G][G][n_orb] (f64 or f32) -> [(G+3)^3][n_pad] in T with one ghost
+// layer before and two after each dimension (padded index x holds node (x-1) mod G), so
+// that a cell's 4^3 stencil is contiguous in z and never wraps.
+template <typename T>
+__global__ void pad_table_kernel(const Params p, const void* src, int src_f32, int n_orb, T* dst) {
+  const size_t GP = (size_t)p.GP, total = GP * GP * GP * (size_t)p.n_pad;
+  const int G = p.G;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % p.n_pad);
+    const size_t cidx = idx / p.n_pad;
+    const int z = (int)(cidx % GP), y = (int)((cidx / GP) % GP), x = (int)(cidx / (GP * GP));
+    if (j >= p.n) {
+      dst[idx] = T(0);
+      continue;
+    }
+    const int gx = (x - 1 + G) % G, gy = (y - 1 + G) % G, gz = (z - 1 + G) % G;
+    const size_t s = (((size_t)gx * G + gy) * G + gz) * (size_t)n_orb + j;
+    dst[idx] = src_f32 ? (T)((const float*)src)[s] : (T)((const double*)src)[s];
+  }
+}
+
+// U(R) per walker in FP64 accumulation (for log|Psi| queries).
+template <typename T>
+__global__ void __launch_bounds__(NT) jastrow_U_kernel(const Params p, double* U) {
+  __shared__ double red[NWARP];
+  const int w = blockIdx.x, N = p.N, NI = p.n_ions;
+  const double* R = p.R + (size_t)w * N * 3;
+  const T* jc = (const T*)p.jc;
+  double acc = 0.0;
+  if (p.K2 > 0) {
+    for (int q = threadIdx.x; q < N * N; q += NT) {
+      const int i = q / N, j = q - i * N;
+      if (j <= i) continue;
+      double d[3];
+      disp_f64(R + 3 * i, R + 3 * j, p.L, p.invL, d);
+      const T r = (T)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const bool same = (i < p.n_up) == (j < p.n_up);
+      T u, du, d2u;
+      radial(jc + (same ? 0 : p.K2 + 3), p.K2, (T)p.h2inv, (T)p.rc2, r, u, du, d2u);
+      acc += (double)u;
+    }
+  }
+  if (p.K1 > 0) {
+    for (int q = threadIdx.x; q < N * NI; q += NT) {
+      const int i = q / NI, I = q - i * NI;
+      double d[3];
+      disp_f64(R + 3 * i, p.ions + 3 * I, p.L, p.invL, d);
+      const T r = (T)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      T u, du, d2u;
+      radial(jc + 2 * (p.K2 + 3), p.K1, (T)p.h1inv, (T)p.rc1, r, u, du, d2u);
+      acc += (double)u;
+    }
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < NWARP; ++q) t += red[q];
+    U[w] = t;
+  }
+}
+
+__global__ void wrap_kernel(double* R, size_t n3, double L) {
+  const double invL = 1.0 / L;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3;
+       e += (size_t)gridDim.x * blockDim.x)
+    R[e] = wrap_coord(R[e], L, invL);
+}
+
+template <typename T>
+cudaError_t launch_eval_rows(const Params& p, cudaStream_t s) {
+  const size_t bytes = (size_t)16 * p.n_pad * sizeof(T);
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(eval_rows_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  eval_rows_kernel<T><<<p.W * p.N, NT, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s) {
+  recompute_kernel<T><<<p.W * 2, NT, (size_t)p.n * sizeof(int), s>>>(p, ws);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int n_orb,
+                             cudaStream_t s) {
+  pad_table_kernel<T><<<1024, 256, 0, s>>>(p, src, src_f32, n_orb, (T*)p.table);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s) {
+  jastrow_U_kernel<T><<<p.W, NT, 0, s>>>(p, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s) {
+  wrap_kernel<<<256, 256, 0, s>>>(R, n3, L);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_eval_rows<double>(const Params&, cudaStream_t);
+template cudaError_t launch_eval_rows<float>(const Params&, cudaStream_t);
+template cudaError_t launch_recompute<double>(const Params&, double*, cudaStream_t);
+template cudaError_t launch_recompute<float>(const Params&, double*, cudaStream_t);
+template cudaError_t launch_pad_table<double>(const Params&, const void*, int, int, cudaStream_t);
+template cudaError_t launch_pad_table<float>(const Params&, const void*, int, int, cudaStream_t);
+template cudaError_t launch_jastrow_U<double>(const Params&, double*, cudaStream_t);
+template cudaError_t launch_jastrow_U<float>(const Params&, double*, cudaStream_t);
+
+}  // namespace qmcgb

@@ -1,0 +1,1055 @@
+// The particle-by-particle move over a crowd of walkers (arXiv:2209.14487, Alg. 1 lines
+// 4-11) as one CTA per walker.  Walkers are independent (Alg. 1 line 2), so a walker's
+// CTA runs its whole electron loop (Alg. 1 line 4, sequential) without any grid-level
+// synchronisation: one launch per generation replaces the per-electron kernel chain of
+// the lock-step driver (Sec. II-C, limitations (a)-(b)).  The fine-grained batched calls
+// (propose / accept / energy) are other instantiations of the same kernel and device
+// functions, so the timed path and the parity-tested path are one code.
+//
+// Precision: T = double is the FP64 path.  T = float is the mixed path: orbitals,
+// Jastrow, ratios, the proposal and the Metropolis test in FP32 on 32-bit fixed-point
+// positions, inverse in FP32; log|det| and the local energy accumulate in FP64 and the
+// inverse is recomputed in FP64 by a separate kernel.  In the mixed path every warp
+// evaluates the (cheap, deterministic) proposal and acceptance itself after each block
+// reduction, so the move needs three barriers plus one per accepted move; the FP64 path,
+// where GB300's FP64 rate makes redundant scalar work expensive, lets thread 0 do it.
+#include <cmath>
+
+#include "qmc_device.cuh"
+#include "qmc_internal.h"
+
+namespace qmcgb {
+
+constexpr int JT = 4;  // Jastrow partner terms cached per thread (N + N_ions <= JT * NT)
+
+// Per-move proposal state (registers of every thread in the mixed path; in the FP64 path
+// thread 0 builds it in shared memory and the others copy it).
+template <typename T>
+struct Prop {
+  T F[3], disp[3], logGf;
+  T t[3];          // offsets in the spline cell
+  int cell[3];
+  uint32_t rq[3];  // mixed: fixed-point proposed position
+  double rp[3];    // FP64: proposed position
+};
+
+template <typename T>
+struct Res {
+  T rhoD, dU, rho, Fp[3];
+};
+
+template <typename T>
+struct Scal {
+  Prop<T> pr;
+  Res<T> rs;
+  double logdet[2];
+  int sign[2];
+  int accept, m;
+  T wts[48];
+};
+
+// Constants of the crowd in the path's precision, converted once per kernel (a double to
+// float conversion runs on the FP64 pipe, 1/64 rate on GB300).
+template <typename T>
+struct Cst {
+  T L, invL, tau, stau, dgrid, h2inv, h1inv, rc2, rc1, halfL, unit, scale;
+};
+
+template <typename T>
+__device__ __forceinline__ Cst<T> make_cst(const Params& p) {
+  Cst<T> k;
+  k.L = (T)p.L;
+  k.invL = (T)p.invL;
+  k.tau = (T)p.tau;
+  k.stau = (T)p.sqrt_tau;
+  k.dgrid = (T)p.dgrid;
+  k.h2inv = (T)p.h2inv;
+  k.h1inv = (T)p.h1inv;
+  k.rc2 = (T)p.rc2;
+  k.rc1 = (T)p.rc1;
+  k.halfL = (T)(0.5 * p.L);
+  k.unit = (T)p.fx_unit;
+  k.scale = (T)p.fx_scale;
+  return k;
+}
+
+struct Lay {
+  size_t scal, B, R, Rq, ion, ionq, jc, phi, part, col, dchi, du, red0, red1;
+  size_t wP, wV, wS, wy, wz, wc, wb, snap, xb, yb, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline int b_stride(const Params& p) { return p.b_in_smem ? p.n + 1 : p.n; }
+
+template <typename T>
+__host__ __device__ inline Lay make_lay(const Params& p) {
+  const size_t es = sizeof(T);
+  Lay L{};
+  size_t o = 0;
+  L.scal = o; o += al16(sizeof(Scal<T>));
+  L.B = o; o += al16(p.b_in_smem ? (size_t)p.n * (p.n + 1) * es : 0);
+  L.R = o; o += al16((size_t)p.N * 3 * 8);
+  L.Rq = o; o += al16((size_t)p.N * 3 * 4);
+  L.ion = o; o += al16((size_t)p.n_ions * 3 * 8);
+  L.ionq = o; o += al16((size_t)p.n_ions * 3 * 4);
+  L.jc = o; o += al16((size_t)(2 * (p.K2 + 3) + p.K1 + 3) * es);
+  L.phi = o; o += al16((size_t)5 * p.n_pad * es);
+  L.part = o; o += al16((size_t)16 * p.n_pad * es);
+  L.col = o; o += al16((size_t)p.n_pad * es);
+  L.dchi = o; o += al16((size_t)p.N * 3 * es);
+  L.du = o; o += al16((size_t)p.N * 8);
+  L.red0 = o; o += al16((size_t)NWARP * 8 * 8);
+  L.red1 = o; o += al16((size_t)NWARP * 8 * 8);
+  L.wP = L.wV = L.wS = L.wy = L.wz = L.wc = L.wb = L.snap = L.xb = L.yb = o;
+  if (p.update == 1) {
+    L.wP = o; o += al16((size_t)MAX_K * 4);
+    L.wV = o; o += al16((size_t)p.k * p.vs * es);
+    L.wS = o; o += al16((size_t)p.k * p.ks * es);
+    L.wy = o; o += al16((size_t)(MAX_K + 1) * es);
+    L.wz = o; o += al16((size_t)(MAX_K + 1) * es);
+    L.wc = o; o += al16((size_t)(MAX_K + 1) * es);
+    L.wb = o; o += al16((size_t)(MAX_K + 1) * es);
+    L.snap = o; o += al16((size_t)p.k * p.n * es);
+    L.xb = o; o += al16((size_t)p.n * p.k * es);
+    L.yb = o; o += al16((size_t)p.n * p.k * es);
+  }
+  L.total = o;
+  return L;
+}
+
+size_t move_smem_bytes(const Params& p, int elem_bytes) {
+  return elem_bytes == 4 ? make_lay<float>(p).total : make_lay<double>(p).total;
+}
+
+template <typename T>
+struct Ctx {
+  const Params& p;
+  Cst<T> k;
+  int w, tid, lane, warp;
+  int bs;   // row stride of B
+  Scal<T>* sc;
+  T* B;     // inverse (transposed) of the moving spin: shared or global
+  T* Bs;    // shared staging buffer (if p.b_in_smem)
+  T* Bg;    // this walker's global inverses [2][n][n]
+  double* R;
+  uint32_t* Rq;
+  double* ion;
+  uint32_t* ionq;
+  T* jc;
+  T* phi;
+  T* part;
+  T* col;
+  T* dchi;
+  double* du;
+  T* red0;
+  T* red1;
+  int* wP;
+  T* wV;
+  T* wS;
+  T* wy;
+  T* wz;
+  T* wc;
+  T* wb;
+  T* snap;
+  T* xb;
+  T* yb;
+  T* rows;  // this walker's global orbital rows [N][5][n_pad]
+  // stencil items of this thread (orbital j, x offset a), at most 4
+  int nit;
+  int itj[4], ita[4];
+};
+
+// ---------------------------------------------------------------------------------------
+// Jastrow term geometry: displacement from electron/point (x, q) to partner t (electron
+// t < N, ion t - N) and its length; the radial functor of the pair.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void partner_disp(const Ctx<T>& c, const double* x, const uint32_t* q,
+                                             int t, T* d, T& r) {
+  const Params& p = c.p;
+  if constexpr (IsMixed<T>::value) {
+    const uint32_t* b = t < p.N ? c.Rq + 3 * t : c.ionq + 3 * (t - p.N);
+    disp_fx(q, b, c.k.unit, d);
+    r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  } else {
+    const double* b = t < p.N ? c.R + 3 * t : c.ion + 3 * (t - p.N);
+    disp_f64(x, b, p.L, p.invL, d);
+    r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void functor(const Ctx<T>& c, int i, int t, const T*& coef, int& K,
+                                        T& hinv, T& rc) {
+  const Params& p = c.p;
+  if (t < p.N) {
+    const bool same = (i < p.n_up) == (t < p.n_up);
+    coef = c.jc + (same ? 0 : p.K2 + 3);
+    K = p.K2;
+    hinv = c.k.h2inv;
+    rc = c.k.rc2;
+  } else {
+    coef = c.jc + 2 * (p.K2 + 3);
+    K = p.K1;
+    hinv = c.k.h1inv;
+    rc = c.k.rc1;
+  }
+}
+
+__device__ __forceinline__ void term_range(const Params& p, int& t0, int& t1) {
+  t0 = p.K2 > 0 ? 0 : p.N;
+  t1 = p.K1 > 0 ? p.N + p.n_ions : p.N;
+}
+
+// ---------------------------------------------------------------------------------------
+// Inverse and delayed window of one spin: staging in and out of shared memory.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ void begin_spin(Ctx<T>& c, int s) {
+  const Params& p = c.p;
+  const int n = p.n;
+  T* Bg = c.Bg + (size_t)s * n * n;
+  if (p.b_in_smem) {
+    for (int r = c.warp; r < n; r += NWARP)
+      for (int j = c.lane; j < n; j += 32) c.Bs[r * c.bs + j] = Bg[(size_t)r * n + j];
+    c.B = c.Bs;
+  } else {
+    c.B = Bg;
+  }
+  if (p.update == 1) {
+    const int ws = c.w * 2 + s;
+    const int m = p.win_m[ws];
+    const T* gV = (const T*)p.win_V + (size_t)ws * p.k * p.vs;
+    const T* gS = (const T*)p.win_S + (size_t)ws * p.k * p.ks;
+    for (int e = c.tid; e < m; e += NT) c.wP[e] = p.win_P[ws * MAX_K + e];
+    for (int e = c.tid; e < m * p.vs; e += NT) c.wV[e] = gV[e];
+    for (int e = c.tid; e < m * p.ks; e += NT) c.wS[e] = gS[e];
+    if (c.tid == 0) c.sc->m = m;
+  } else if (c.tid == 0) {
+    c.sc->m = 0;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void end_spin(Ctx<T>& c, int s, bool store) {
+  const Params& p = c.p;
+  const int n = p.n;
+  __syncthreads();
+  if (!store) return;
+  if (p.b_in_smem) {
+    T* Bg = c.Bg + (size_t)s * n * n;
+    for (int r = c.warp; r < n; r += NWARP)
+      for (int j = c.lane; j < n; j += 32) Bg[(size_t)r * n + j] = c.Bs[r * c.bs + j];
+  }
+  if (p.update == 1) {
+    const int ws = c.w * 2 + s;
+    const int m = c.sc->m;
+    T* gV = (T*)p.win_V + (size_t)ws * p.k * p.vs;
+    T* gS = (T*)p.win_S + (size_t)ws * p.k * p.ks;
+    for (int e = c.tid; e < m; e += NT) p.win_P[ws * MAX_K + e] = c.wP[e];
+    for (int e = c.tid; e < m * p.vs; e += NT) gV[e] = c.wV[e];
+    for (int e = c.tid; e < m * p.ks; e += NT) gS[e] = c.wS[e];
+    if (c.tid == 0) p.win_m[ws] = m;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// Delayed window (Woodbury).  The window holds m replaced rows p_l (all distinct) with
+// their new orbital rows Phi_l; with A_cur = A_0 + P V, V_l = Phi_l - a_{p_l} and
+// B = A_0^-1, every product V B is evaluated as Phi B - P^T (a_p^T B = e_p^T), the form
+// in which rounding errors of B are damped as in Sherman-Morrison.  S = I + V B P and its
+// inverse is bordered one accept at a time.
+// ---------------------------------------------------------------------------------------
+
+// Column pp of the current inverse: B[:,pp] - (B P) S^-1 (V B[:,pp]); y and z = S^-1 y
+// are kept for a following accept.
+template <typename T>
+__device__ void compute_column(Ctx<T>& c, int pp) {
+  const Params& p = c.p;
+  const int n = p.n;
+  const T* brow = c.B + (size_t)pp * c.bs;
+  const int m = c.sc->m;
+  if (m == 0) {
+    for (int j = c.tid; j < n; j += NT) c.col[j] = brow[j];
+    return;
+  }
+  for (int l = c.warp; l < m; l += NWARP) {
+    const T* v = c.wV + (size_t)l * p.vs;
+    T acc = 0;
+    for (int j = c.lane; j < n; j += 32) acc += v[j] * brow[j];
+    acc = warp_sum(acc);
+    if (c.lane == 0) c.wy[l] = acc - (c.wP[l] == pp ? T(1) : T(0));
+  }
+  __syncthreads();
+  for (int l = c.tid; l < m; l += NT) {
+    const T* srow = c.wS + (size_t)l * p.ks;
+    T acc = 0;
+    for (int q = 0; q < m; ++q) acc += srow[q] * c.wy[q];
+    c.wz[l] = acc;
+  }
+  __syncthreads();
+  for (int j = c.tid; j < n; j += NT) {
+    T acc = brow[j];
+    for (int l = 0; l < m; ++l) acc -= c.B[(size_t)c.wP[l] * c.bs + j] * c.wz[l];
+    c.col[j] = acc;
+  }
+}
+
+// B <- B - (B P) S^-1 (V B); in B^T form B^T[k] -= sum_b Y[k][b] B^T[p_b] with
+// X[k][l] = B^T[k].Phi_l - delta(k, p_l) and Y = X S^-T.
+template <typename T>
+__device__ void flush_window(Ctx<T>& c) {
+  const Params& p = c.p;
+  const int m = c.sc->m;
+  if (m == 0) return;
+  const int n = p.n, bs = c.bs;
+  for (int l = c.warp; l < m; l += NWARP)
+    for (int j = c.lane; j < n; j += 32) c.snap[l * n + j] = c.B[(size_t)c.wP[l] * bs + j];
+  for (int e = c.tid; e < n * m; e += NT) {
+    const int k = e / m, l = e - k * m;
+    const T* brow = c.B + (size_t)k * bs;
+    const T* v = c.wV + (size_t)l * p.vs;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+      a0 += brow[j] * v[j];
+      a1 += brow[j + 1] * v[j + 1];
+      a2 += brow[j + 2] * v[j + 2];
+      a3 += brow[j + 3] * v[j + 3];
+    }
+    for (; j < n; ++j) a0 += brow[j] * v[j];
+    c.xb[e] = (a0 + a1) + (a2 + a3) - (k == c.wP[l] ? T(1) : T(0));
+  }
+  __syncthreads();
+  for (int e = c.tid; e < n * m; e += NT) {
+    const int k = e / m, b = e - k * m;
+    const T* srow = c.wS + (size_t)b * p.ks;
+    const T* xrow = c.xb + (size_t)k * m;
+    T acc = 0;
+    for (int l = 0; l < m; ++l) acc += xrow[l] * srow[l];
+    c.yb[e] = acc;
+  }
+  __syncthreads();
+  for (int k = c.warp; k < n; k += NWARP) {
+    const T* yrow = c.yb + (size_t)k * m;
+    T* brow = c.B + (size_t)k * bs;
+    for (int j = c.lane; j < n; j += 32) {
+      T acc = 0;
+      for (int b = 0; b < m; ++b) acc += yrow[b] * c.snap[b * n + j];
+      brow[j] -= acc;
+    }
+  }
+  __syncthreads();
+  if (c.tid == 0) c.sc->m = 0;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// The move.
+// ---------------------------------------------------------------------------------------
+
+// grad_i log Psi at the current positions (the drift F of Alg. 1 line 5): det part
+// sum_j dA[i][j] col_j, Jastrow part -sum u'(r) d/r.  Every thread receives F.  Caches
+// u(r_old) per partner term in `uo`.  `pf` holds this thread's prefetched gradient-row
+// entries (orbital j = tid) when `use_pf` is set.
+template <typename T>
+__device__ void eval_grad(Ctx<T>& c, int i, const T* pf, bool use_pf, T* uo, T* F) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad;
+  T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (use_pf) {
+    if (c.tid < n) {
+      const T cj = c.col[c.tid];
+      v[0] = pf[0] * cj;
+      v[1] = pf[1] * cj;
+      v[2] = pf[2] * cj;
+    }
+  } else {
+    const T* rw = c.rows + (size_t)i * 5 * n_pad;
+    for (int j = c.tid; j < n; j += NT) {
+      const T cj = c.col[j];
+      v[0] += rw[n_pad + j] * cj;
+      v[1] += rw[2 * n_pad + j] * cj;
+      v[2] += rw[3 * n_pad + j] * cj;
+    }
+  }
+  int t0, t1;
+  term_range(p, t0, t1);
+  auto term = [&](int t, T& u_out) {
+    T d[3], r;
+    partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r);
+    const T* coef; int K; T hinv, rc;
+    functor(c, i, t, coef, K, hinv, rc);
+    T u, du, d2u;
+    radial(coef, K, hinv, rc, r, u, du, d2u);
+    u_out = u;
+    if (r > T(0)) {
+      const T f = du / r;
+      v[3] += f * d[0];
+      v[4] += f * d[1];
+      v[5] += f * d[2];
+    }
+  };
+#pragma unroll
+  for (int q = 0; q < JT; ++q) {
+    const int t = t0 + c.tid + q * NT;
+    if (t < t1 && t != i) term(t, uo[q]);
+  }
+  for (int t = t0 + c.tid + JT * NT; t < t1; t += NT) {
+    T dummy;
+    if (t != i) term(t, dummy);
+  }
+  block_allreduce8(v, c.red0);
+  for (int k = 0; k < 3; ++k) F[k] = v[k] - v[3 + k];
+}
+
+// The proposal r' (given, or r + tau F + sqrt(tau) chi), its spline cell and the forward
+// Green's-function exponent.
+template <typename T>
+__device__ __forceinline__ void make_proposal(const Ctx<T>& c, int i, const T* F, const T* chi,
+                                              const double* rgiven, Prop<T>& pr) {
+  const Params& p = c.p;
+  const T tau = c.k.tau, stau = c.k.stau;
+  T gf = 0;
+  for (int k = 0; k < 3; ++k) pr.F[k] = p.drift ? F[k] : T(0);
+  if constexpr (IsMixed<T>::value) {
+    const uint32_t* qi = c.Rq + 3 * i;
+    for (int k = 0; k < 3; ++k) {
+      uint32_t q;
+      if (rgiven) {
+        q = to_fixed(wrap_coord(rgiven[k], p.L, p.invL), p.fx_scale);
+        pr.disp[k] = (float)(int32_t)(q - qi[k]) * c.k.unit;
+      } else {
+        const float d = tau * pr.F[k] + stau * chi[k];
+        pr.disp[k] = d;
+        const float dw = d - c.k.L * rintf(d * c.k.invL);  // same point mod L, |dw| <= L/2
+        q = qi[k] + (uint32_t)__float2int_rn(dw * c.k.scale);
+      }
+      pr.rq[k] = q;
+      const unsigned long long prod = (unsigned long long)q * (unsigned long long)p.G;
+      pr.cell[k] = (int)(prod >> 32);
+      pr.t[k] = (float)(uint32_t)prod * 0x1p-32f;
+      const float x = pr.disp[k] - tau * pr.F[k];
+      gf += x * x;
+    }
+  } else {
+    const double* ri = c.R + 3 * i;
+    if (rgiven) {
+      for (int k = 0; k < 3; ++k) pr.rp[k] = wrap_coord(rgiven[k], p.L, p.invL);
+      disp_f64(pr.rp, ri, p.L, p.invL, pr.disp);
+    } else {
+      for (int k = 0; k < 3; ++k) {
+        pr.disp[k] = tau * pr.F[k] + stau * chi[k];
+        pr.rp[k] = wrap_coord(ri[k] + pr.disp[k], p.L, p.invL);
+      }
+    }
+    for (int k = 0; k < 3; ++k) {
+      const double x = pr.disp[k] - tau * pr.F[k];
+      gf += x * x;
+      const double s = pr.rp[k] * p.dgrid;
+      int g = (int)floor(s);
+      g = g > p.G - 1 ? p.G - 1 : (g < 0 ? 0 : g);
+      pr.cell[k] = g;
+      pr.t[k] = s - (double)g;
+    }
+  }
+  pr.logGf = -gf / (T(2) * tau);
+}
+
+// Ratio Psi(R')/Psi(R) and grad_i log Psi(R') (Alg. 1 lines 7-8): Jastrow difference over
+// all partners, tricubic orbital VGL at r', determinant ratio phi'.col.  Every thread
+// gets rhoD and dU; rho and Fp = grad log Psi(R') on every thread in the mixed path and
+// on thread 0 in the FP64 path.  phi' stays in shared memory.
+template <typename T>
+__device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, bool cached,
+                           Res<T>& rs) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad, GP = p.GP;
+  const T* table = (const T*)p.table;
+  T cf[16];
+  if (c.nit > 0)
+    stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[0], c.ita[0], cf);
+  T wreg[36];  // x, y, z weights (mixed path: computed by every thread)
+  if constexpr (IsMixed<T>::value) {
+    basis12(pr.t[1], wreg + 12);
+    basis12(pr.t[2], wreg + 24);
+  } else {
+    if (c.tid < 36) c.sc->wts[c.tid] = basis_one((T)pr.t[c.tid / 12], c.tid % 12);
+  }
+  T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int t0, t1;
+  term_range(p, t0, t1);
+  auto term = [&](int t, bool have_old, T uold) {
+    T dn[3], rn;
+    partner_disp(c, pr.rp, pr.rq, t, dn, rn);
+    const T* coef; int K; T hinv, rc;
+    functor(c, i, t, coef, K, hinv, rc);
+    T un, dun, d2n;
+    radial(coef, K, hinv, rc, rn, un, dun, d2n);
+    if (!have_old) {
+      T dol[3], ro, duo, d2o;
+      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro);
+      radial(coef, K, hinv, rc, ro, uold, duo, d2o);
+    }
+    v[4] += un - uold;
+    if (rn > T(0)) {
+      const T f = dun / rn;
+      v[5] += f * dn[0];
+      v[6] += f * dn[1];
+      v[7] += f * dn[2];
+    }
+  };
+#pragma unroll
+  for (int q = 0; q < JT; ++q) {
+    const int t = t0 + c.tid + q * NT;
+    if (t < t1 && t != i) term(t, cached, uo[q]);
+  }
+  for (int t = t0 + c.tid + JT * NT; t < t1; t += NT)
+    if (t != i) term(t, false, T(0));
+  const T* wts;
+  if constexpr (IsMixed<T>::value) {
+    wts = wreg;
+  } else {
+    __syncthreads();  // weights in shared memory
+    wts = c.sc->wts;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < c.nit) {
+      if (q > 0)
+        stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[q], c.ita[q], cf);
+      T o4[4];
+      stencil_reduce(cf, wts, o4);
+      const int j = c.itj[q], a = c.ita[q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
+    }
+  }
+  __syncthreads();
+  const T dinv = c.k.dgrid;
+  for (int j = c.tid; j < n; j += NT) {
+    T wx[12];
+    if constexpr (IsMixed<T>::value) {
+      basis12(pr.t[0], wx);
+    } else {
+      for (int q = 0; q < 12; ++q) wx[q] = c.sc->wts[q];
+    }
+    T o5[5];
+    stencil_combine(c.part, n_pad, j, wx, dinv, o5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) c.phi[q * n_pad + j] = o5[q];
+    const T cj = c.col[j];
+    v[0] += o5[0] * cj;
+    v[1] += o5[1] * cj;
+    v[2] += o5[2] * cj;
+    v[3] += o5[3] * cj;
+  }
+  block_allreduce8(v, c.red1);
+  rs.rhoD = v[0];
+  rs.dU = v[4];
+  if constexpr (IsMixed<T>::value) {
+    rs.rho = v[0] * __expf(-v[4]);
+    const T ir = T(1) / v[0];
+    for (int k = 0; k < 3; ++k) rs.Fp[k] = v[1 + k] * ir - v[5 + k];
+  } else if (c.tid == 0) {  // FP64 scalar work on one thread; the caller syncs
+    rs.rho = v[0] * exp(-v[4]);
+    for (int k = 0; k < 3; ++k) rs.Fp[k] = v[1 + k] / v[0] - v[5 + k];
+  }
+}
+
+// Metropolis(-Hastings): A = rho^2 G(r<-r')/G(r'<-r) with drift, rho^2 without;
+// accept iff u < A; rho = 0 or non-finite rejects.
+template <typename T>
+__device__ __forceinline__ int metropolis(const Params& p, const Cst<T>& k, const Prop<T>& pr,
+                                          const Res<T>& rs, T u) {
+  const T rho = rs.rho;
+  if (!(rho != T(0)) || !isfinite(rho)) return 0;
+  T A;
+  if (p.drift) {
+    T gb = 0;
+    for (int q = 0; q < 3; ++q) {
+      const T x = -pr.disp[q] - k.tau * rs.Fp[q];
+      gb += x * x;
+    }
+    A = rho * rho * exp(-gb / (T(2) * k.tau) - pr.logGf);
+  } else {
+    A = rho * rho;
+  }
+  return u < A ? 1 : 0;
+}
+
+// Accepting the pending move of electron i (row pp of spin s): inverse update, rows of A,
+// dA, d2A replaced, position and log|det| updated.
+template <typename T>
+__device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr, T rhoD) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad, bs = c.bs;
+  T* rw = c.rows + (size_t)i * 5 * n_pad;
+  if (p.update == 0) {
+    // Sherman-Morrison: v_k = phi'.B^T[k]; B^T[k] -= col (v_k - delta_k,pp) / rhoD
+    const T invr = T(1) / rhoD;
+    for (int k = c.warp; k < n; k += NWARP) {
+      T* row = c.B + (size_t)k * bs;
+      T acc = 0;
+      for (int j = c.lane; j < n; j += 32) acc += c.phi[j] * row[j];
+      acc = warp_sum(acc);
+      const T f = (acc - (k == pp ? T(1) : T(0))) * invr;
+      for (int j = c.lane; j < n; j += 32) row[j] -= c.col[j] * f;
+    }
+  } else {
+    // Delayed: a row already in the window is applied first; then append p_m = pp,
+    // Phi_m = phi', border S^-1 with b = y, c_l = Phi_m.B[:,p_l], d = Phi_m.B[:,pp]
+    // and sigma = d - c.z (= rhoD).
+    int m = c.sc->m;
+    bool dup = false;
+    for (int l = 0; l < m; ++l) dup |= (c.wP[l] == pp);
+    if (dup) {
+      flush_window(c);
+      m = 0;
+    }
+    T* vm = c.wV + (size_t)m * p.vs;
+    for (int j = c.tid; j < n; j += NT) vm[j] = c.phi[j];
+    if (c.tid == 0) c.wP[m] = pp;
+    __syncthreads();
+    for (int l = c.warp; l <= m; l += NWARP) {
+      const T* brow = c.B + (size_t)(l < m ? c.wP[l] : pp) * bs;
+      T acc = 0;
+      for (int j = c.lane; j < n; j += 32) acc += vm[j] * brow[j];
+      acc = warp_sum(acc);
+      if (c.lane == 0) c.wc[l] = acc;
+    }
+    __syncthreads();
+    if (m == 0) {
+      if (c.tid == 0) c.wS[0] = T(1) / c.wc[0];
+    } else {
+      for (int b = c.tid; b < m; b += NT) {  // w = c^T S^-1
+        T acc = 0;
+        for (int l = 0; l < m; ++l) acc += c.wc[l] * c.wS[(size_t)l * p.ks + b];
+        c.wb[b] = acc;
+      }
+      if (c.warp == NWARP - 1) {
+        T acc = 0;
+        for (int l = c.lane; l < m; l += 32) acc += c.wc[l] * c.wz[l];
+        acc = warp_sum(acc);
+        if (c.lane == 0) c.wc[MAX_K] = T(1) / (c.wc[m] - acc);  // 1 / sigma
+      }
+      __syncthreads();
+      const T isg = c.wc[MAX_K];
+      const int m1 = m + 1;
+      for (int e = c.tid; e < m1 * m1; e += NT) {
+        const int a = e / m1, b = e - a * m1;
+        T* sab = c.wS + (size_t)a * p.ks + b;
+        if (a < m && b < m) *sab += c.wz[a] * c.wb[b] * isg;
+        else if (a < m) *sab = -c.wz[a] * isg;
+        else if (b < m) *sab = -c.wb[b] * isg;
+        else *sab = isg;
+      }
+    }
+    if (c.tid == 0) c.sc->m = m + 1;
+    __syncthreads();
+    if (m + 1 >= p.k) flush_window(c);
+  }
+  for (int j = c.tid; j < n; j += NT) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = c.phi[q * n_pad + j];
+  }
+  if (c.tid == 0) {
+    for (int k = 0; k < 3; ++k) {
+      if constexpr (IsMixed<T>::value) c.Rq[3 * i + k] = pr.rq[k];
+      else c.R[3 * i + k] = pr.rp[k];
+    }
+    c.sc->logdet[s] += (double)log(fabs(rhoD));
+    if (rhoD < T(0)) c.sc->sign[s] = -c.sc->sign[s];
+  }
+  __syncthreads();
+}
+
+// Local energy (Alg. 1 line 11): E_L = -1/2 sum_i [lap_i log Psi + |grad_i log Psi|^2] + V,
+// with grad_i log D = sum_j dA[i][j] Ainv[j][i], lap_i D / D = sum_j d2A[i][j] Ainv[j][i];
+// one warp per electron, lanes over partners (no atomics); FP64 accumulation.
+template <typename T>
+__device__ double local_energy(Ctx<T>& c) {
+  const Params& p = c.p;
+  const int N = p.N, n = p.n, n_pad = p.n_pad, NI = p.n_ions;
+  double kin = 0.0, pot = 0.0;
+  for (int i = c.warp; i < N; i += NWARP) {
+    T v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = c.lane; t < N + NI; t += 32) {
+      if (t == i) continue;
+      T d[3], r;
+      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r);
+      const bool jas = t < N ? p.K2 > 0 : p.K1 > 0;
+      if (jas && r > T(0)) {
+        const T* coef; int K; T hinv, rc;
+        functor(c, i, t, coef, K, hinv, rc);
+        T u, du, d2u;
+        radial(coef, K, hinv, rc, r, u, du, d2u);
+        const T f = du / r;
+        v[0] += f * d[0];
+        v[1] += f * d[1];
+        v[2] += f * d[2];
+        v[3] += d2u + T(2) * f;
+      }
+      if (p.potential && r < c.k.halfL) {
+        if (t < N) {
+          if (t > i) v[8] += exp(-r * r);
+        } else {
+          v[8] += T(-2) * exp(T(-0.5) * r * r);
+        }
+      }
+    }
+    const int s = i < p.n_up ? 0 : 1;
+    const int pp = i - s * p.n_up;
+    const T* brow = c.Bg + ((size_t)s * n + pp) * n;
+    const T* rw = c.rows + (size_t)i * 5 * n_pad;
+    for (int j = c.lane; j < n; j += 32) {
+      const T b = brow[j];
+      v[4] += rw[n_pad + j] * b;
+      v[5] += rw[2 * n_pad + j] * b;
+      v[6] += rw[3 * n_pad + j] * b;
+      v[7] += rw[4 * n_pad + j] * b;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] = warp_sum(v[q]);
+    if (c.lane == 0) {
+      double gd2 = 0.0, gg = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double gd = (double)v[4 + k];
+        gd2 += gd * gd;
+        const double g = gd - (double)v[k];
+        gg += g * g;
+      }
+      kin += -0.5 * (((double)v[7] - gd2) - (double)v[3] + gg);
+      pot += (double)v[8];
+    }
+  }
+  double v2[2] = {kin, pot};
+  block_sum_to0<2>(v2, (double*)c.red0);
+  return v2[0] + v2[1];  // meaningful on thread 0
+}
+
+template <typename T>
+__device__ __forceinline__ void prefetch_grad_rows(const Ctx<T>& c, int i, T* pf) {
+  if (i < c.p.N && c.tid < c.p.n) {
+    const T* rw = c.rows + (size_t)i * 5 * c.p.n_pad + c.tid;
+    pf[0] = rw[c.p.n_pad];
+    pf[1] = rw[2 * c.p.n_pad];
+    pf[2] = rw[3 * c.p.n_pad];
+  }
+}
+
+// Proposal of electron i shared by every thread: the mixed path computes it in each
+// thread; the FP64 path on thread 0, then copied through shared memory.
+template <typename T>
+__device__ __forceinline__ void shared_proposal(Ctx<T>& c, int i, const T* F, const T* chi,
+                                                const double* rgiven, Prop<T>& pr) {
+  if constexpr (IsMixed<T>::value) {
+    make_proposal(c, i, F, chi, rgiven, pr);
+  } else {
+    if (c.tid == 0) make_proposal(c, i, F, chi, rgiven, c.sc->pr);
+    __syncthreads();
+    pr = c.sc->pr;
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Lay lay = make_lay<T>(p);
+  const int w = blockIdx.x;
+  const int N = p.N, n = p.n, n_pad = p.n_pad;
+  Ctx<T> c{p};
+  c.k = make_cst<T>(p);
+  c.w = w;
+  c.tid = threadIdx.x;
+  c.lane = threadIdx.x & 31;
+  c.warp = threadIdx.x >> 5;
+  c.bs = b_stride(p);
+  c.sc = (Scal<T>*)(smem + lay.scal);
+  c.Bs = (T*)(smem + lay.B);
+  c.Bg = (T*)p.binv + (size_t)w * 2 * n * n;
+  c.B = c.Bg;
+  c.R = (double*)(smem + lay.R);
+  c.Rq = (uint32_t*)(smem + lay.Rq);
+  c.ion = (double*)(smem + lay.ion);
+  c.ionq = (uint32_t*)(smem + lay.ionq);
+  c.jc = (T*)(smem + lay.jc);
+  c.phi = (T*)(smem + lay.phi);
+  c.part = (T*)(smem + lay.part);
+  c.col = (T*)(smem + lay.col);
+  c.dchi = (T*)(smem + lay.dchi);
+  c.du = (double*)(smem + lay.du);
+  c.red0 = (T*)(smem + lay.red0);
+  c.red1 = (T*)(smem + lay.red1);
+  c.wP = (int*)(smem + lay.wP);
+  c.wV = (T*)(smem + lay.wV);
+  c.wS = (T*)(smem + lay.wS);
+  c.wy = (T*)(smem + lay.wy);
+  c.wz = (T*)(smem + lay.wz);
+  c.wc = (T*)(smem + lay.wc);
+  c.wb = (T*)(smem + lay.wb);
+  c.snap = (T*)(smem + lay.snap);
+  c.xb = (T*)(smem + lay.xb);
+  c.yb = (T*)(smem + lay.yb);
+  c.rows = (T*)p.rows + (size_t)w * N * 5 * n_pad;
+  c.nit = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int it = c.tid + q * NT;
+    c.itj[q] = it < 4 * n ? it % n : 0;
+    c.ita[q] = it < 4 * n ? it / n : 0;
+    if (it < 4 * n) c.nit = q + 1;
+  }
+  Scal<T>* sc = c.sc;
+
+  const double* Rg = p.R + (size_t)w * N * 3;
+  for (int e = c.tid; e < N * 3; e += NT) {
+    const double x = Rg[e];
+    c.R[e] = x;
+    if constexpr (IsMixed<T>::value) c.Rq[e] = to_fixed(x, p.fx_scale);
+  }
+  for (int e = c.tid; e < p.n_ions * 3; e += NT) {
+    const double x = p.ions[e];
+    c.ion[e] = x;
+    if constexpr (IsMixed<T>::value) c.ionq[e] = to_fixed(x, p.fx_scale);
+  }
+  const int njc = 2 * (p.K2 + 3) + p.K1 + 3;
+  for (int e = c.tid; e < njc; e += NT) c.jc[e] = ((const T*)p.jc)[e];
+  if (c.tid == 0) {
+    sc->logdet[0] = p.logdet[w * 2];
+    sc->logdet[1] = p.logdet[w * 2 + 1];
+    sc->sign[0] = p.sign[w * 2];
+    sc->sign[1] = p.sign[w * 2 + 1];
+    sc->m = 0;
+    sc->accept = 0;
+  }
+  __syncthreads();
+
+  int t0, t1;
+  term_range(p, t0, t1);
+  const bool cache_ok = p.drift && (t1 - t0) <= JT * NT;
+  const bool pf_ok = n <= NT;
+  T uo[JT];
+#pragma unroll
+  for (int q = 0; q < JT; ++q) uo[q] = T(0);
+  T F[3] = {0, 0, 0};
+  Prop<T> pr;
+  Res<T> rs;
+
+  bool moved = false;
+  if constexpr (MODE == MODE_SWEEP) {
+    for (int e = c.tid; e < N; e += NT) {
+      double d4[4];
+      move_draws(p.seed, (uint32_t)w, p.gen, (uint32_t)e, d4);
+      c.dchi[3 * e] = (T)d4[0];
+      c.dchi[3 * e + 1] = (T)d4[1];
+      c.dchi[3 * e + 2] = (T)d4[2];
+      c.du[e] = d4[3];
+    }
+    T pf[3] = {0, 0, 0};
+    if (pf_ok) prefetch_grad_rows(c, 0, pf);
+    __syncthreads();
+    unsigned long long nacc = 0;
+    for (int s = 0; s < 2; ++s) {
+      begin_spin(c, s);
+      for (int pp = 0; pp < n; ++pp) {
+        const int i = s * p.n_up + pp;
+        compute_column(c, pp);
+        if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
+        if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
+        shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
+        ratio_grad(c, i, pr, uo, cache_ok, rs);
+        int acc;
+        if constexpr (IsMixed<T>::value) {
+          acc = metropolis(p, c.k, pr, rs, (T)c.du[i]);
+        } else {
+          if (c.tid == 0) {
+            sc->rs = rs;
+            sc->accept = metropolis(p, c.k, pr, rs, (T)c.du[i]);
+          }
+          __syncthreads();
+          rs = sc->rs;
+          acc = sc->accept;
+        }
+        nacc += acc;
+        if (acc) accept_update(c, i, s, pp, pr, rs.rhoD);
+      }
+      flush_window(c);
+      end_spin(c, s, true);
+    }
+    moved = true;
+    if (!p.skip_eloc) {
+      const double e = local_energy(c);
+      if (c.tid == 0) {
+        if (p.eloc_out) p.eloc_out[w] = e;
+        if (!isfinite(e)) atomicOr(p.status, ST_NAN);
+      }
+    }
+    if (c.tid == 0 && p.n_accept) atomicAdd(p.n_accept, nacc);
+  } else if constexpr (MODE == MODE_GRAD || MODE == MODE_PROPOSE) {
+    const int i = p.iel;
+    const int s = i < p.n_up ? 0 : 1;
+    const int pp = i - s * p.n_up;
+    begin_spin(c, s);
+    compute_column(c, pp);
+    if (p.drift) eval_grad<T>(c, i, nullptr, false, uo, F);
+    if constexpr (MODE == MODE_GRAD) {
+      if (c.tid == 0)
+        for (int k = 0; k < 3; ++k) p.grad_out[w * 3 + k] = (double)F[k];
+    } else {
+      T chi[3] = {0, 0, 0};
+      if (!p.rnew_in) {
+        double d4[4];
+        move_draws(p.seed, (uint32_t)w, p.gen, (uint32_t)i, d4);
+        chi[0] = (T)d4[0];
+        chi[1] = (T)d4[1];
+        chi[2] = (T)d4[2];
+      }
+      shared_proposal(c, i, F, chi, p.rnew_in ? p.rnew_in + 3 * w : nullptr, pr);
+      ratio_grad(c, i, pr, uo, cache_ok, rs);
+      T* pphi = (T*)p.pend_phi + (size_t)w * 5 * n_pad;
+      for (int j = c.tid; j < n; j += NT)
+        for (int q = 0; q < 5; ++q) pphi[q * n_pad + j] = c.phi[q * n_pad + j];
+      if (c.tid == 0) {
+        double* pd = p.pend + (size_t)w * PEND_STRIDE;
+        double rp[3];
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (IsMixed<T>::value) {
+            pd[P_R + k] = (double)pr.rq[k];
+            rp[k] = (double)pr.rq[k] * p.fx_unit;
+          } else {
+            pd[P_R + k] = pr.rp[k];
+            rp[k] = pr.rp[k];
+          }
+          pd[P_DISP + k] = (double)pr.disp[k];
+          pd[P_FP + k] = (double)rs.Fp[k];
+        }
+        pd[P_RHOD] = (double)rs.rhoD;
+        pd[P_RHO] = (double)rs.rho;
+        pd[P_DU] = (double)rs.dU;
+        pd[P_LOGGF] = (double)pr.logGf;
+        pd[P_IEL] = (double)i;
+        pd[P_VALID] = 1.0;
+        if (p.ratio_out) p.ratio_out[w] = (double)rs.rho;
+        if (p.logratio_out) p.logratio_out[w] = log(fabs((double)rs.rhoD)) - (double)rs.dU;
+        if (p.grad_out)
+          for (int k = 0; k < 3; ++k) p.grad_out[w * 3 + k] = (double)rs.Fp[k];
+        if (p.rnew_out)
+          for (int k = 0; k < 3; ++k) p.rnew_out[w * 3 + k] = rp[k];
+      }
+    }
+    end_spin(c, s, false);
+  } else if constexpr (MODE == MODE_ACCEPT) {
+    const int i = p.iel;
+    const int s = i < p.n_up ? 0 : 1;
+    const int pp = i - s * p.n_up;
+    double* pd = p.pend + (size_t)w * PEND_STRIDE;
+    const bool valid = pd[P_VALID] == 1.0 && (int)pd[P_IEL] == i;
+    if (!valid) {
+      if (c.tid == 0) atomicOr(p.status, ST_STATE);
+      return;  // uniform across the CTA
+    }
+    begin_spin(c, s);
+    compute_column(c, pp);
+    const T* pphi = (const T*)p.pend_phi + (size_t)w * 5 * n_pad;
+    for (int j = c.tid; j < n; j += NT)
+      for (int q = 0; q < 5; ++q) c.phi[q * n_pad + j] = pphi[q * n_pad + j];
+    for (int k = 0; k < 3; ++k) {
+      if constexpr (IsMixed<T>::value) pr.rq[k] = (uint32_t)pd[P_R + k];
+      else pr.rp[k] = pd[P_R + k];
+      pr.disp[k] = (T)pd[P_DISP + k];
+      rs.Fp[k] = (T)pd[P_FP + k];
+    }
+    rs.rhoD = (T)pd[P_RHOD];
+    rs.rho = (T)pd[P_RHO];
+    rs.dU = (T)pd[P_DU];
+    pr.logGf = (T)pd[P_LOGGF];
+    __syncthreads();  // every thread has read the pending state
+    if (c.tid == 0) {
+      int acc;
+      if (p.accept_in) acc = p.accept_in[w] != 0;
+      else
+        acc = metropolis(p, c.k, pr, rs,
+                         (T)accept_uniform(p.seed, (uint32_t)w, p.gen, (uint32_t)i));
+      sc->accept = acc;
+      if (p.accept_out) p.accept_out[w] = (uint8_t)acc;
+      pd[P_VALID] = 0.0;
+    }
+    __syncthreads();
+    if (sc->accept) accept_update(c, i, s, pp, pr, rs.rhoD);
+    end_spin(c, s, true);
+    moved = true;
+  } else if constexpr (MODE == MODE_ELOC) {
+    for (int s = 0; s < 2; ++s) {
+      begin_spin(c, s);
+      flush_window(c);
+      end_spin(c, s, true);
+    }
+    if (!p.skip_eloc) {
+      const double e = local_energy(c);
+      if (c.tid == 0) {
+        p.eloc_out[w] = e;
+        if (!isfinite(e)) atomicOr(p.status, ST_NAN);
+      }
+    }
+  }
+  __syncthreads();
+  if (moved) {
+    double* Rw = p.R + (size_t)w * N * 3;
+    for (int e = c.tid; e < N * 3; e += NT) {
+      if constexpr (IsMixed<T>::value) Rw[e] = (double)c.Rq[e] * p.fx_unit;
+      else Rw[e] = c.R[e];
+    }
+    if (c.tid == 0) {
+      p.logdet[w * 2] = sc->logdet[0];
+      p.logdet[w * 2 + 1] = sc->logdet[1];
+      p.sign[w * 2] = sc->sign[0];
+      p.sign[w * 2 + 1] = sc->sign[1];
+    }
+  }
+}
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_mode(const Params& p, size_t bytes, cudaStream_t s) {
+  static size_t configured = 0;
+  if (bytes > 48 * 1024 && configured < bytes) {
+    cudaError_t e = cudaFuncSetAttribute(move_kernel<T, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    configured = bytes;
+  }
+  move_kernel<T, MODE><<<p.W, NT, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_move(const Params& p_in, int mode, cudaStream_t s) {
+  Params p = p_in;
+  const size_t bytes = make_lay<T>(p).total;
+  p.skip_eloc = 0;
+  switch (mode) {
+    case MODE_SWEEP: return launch_mode<T, MODE_SWEEP>(p, bytes, s);
+    case MODE_SWEEP_NOE: p.skip_eloc = 1; return launch_mode<T, MODE_SWEEP>(p, bytes, s);
+    case MODE_GRAD: return launch_mode<T, MODE_GRAD>(p, bytes, s);
+    case MODE_PROPOSE: return launch_mode<T, MODE_PROPOSE>(p, bytes, s);
+    case MODE_ACCEPT: return launch_mode<T, MODE_ACCEPT>(p, bytes, s);
+    case MODE_ELOC: return launch_mode<T, MODE_ELOC>(p, bytes, s);
+    case MODE_FLUSH: p.skip_eloc = 1; return launch_mode<T, MODE_ELOC>(p, bytes, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_move<double>(const Params&, int, cudaStream_t);
+template cudaError_t launch_move<float>(const Params&, int, cudaStream_t);
+
+}  // namespace qmcgb

@@ -1,0 +1,291 @@
+"""Python binding of libqmcgb (include/qmcgb.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Host arrays (numpy, or CPU torch tensors) are
+passed with QMC_MEM_HOST, CUDA torch tensors with QMC_MEM_DEVICE; one call's buffers must
+all live on the same side.  There is no CPU fallback: without the compiled library,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqmcgb.so")
+
+QMC_OK = 0
+QMC_MEM_HOST, QMC_MEM_DEVICE = 0, 1
+QMC_PREC_FP64, QMC_PREC_MIXED = 0, 1
+QMC_UPDATE_SM, QMC_UPDATE_DELAYED = 0, 1
+QMC_J1, QMC_J2_UU, QMC_J2_UD = 0, 1, 2
+QMC_DTYPE_F64, QMC_DTYPE_F32 = 0, 1
+STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA",
+                4: "QMC_ERR_SINGULAR", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_NAN",
+                7: "QMC_ERR_STATE", 8: "QMC_ERR_UNSUPPORTED"}
+
+# every symbol include/qmcgb.h declares
+EXPORTS = [
+    "qmc_crowd_create", "qmc_crowd_destroy", "qmc_load_positions", "qmc_load_ions",
+    "qmc_load_orbitals", "qmc_load_jastrow", "qmc_recompute", "qmc_eval_grad_batch",
+    "qmc_propose_move_batch", "qmc_accept_reject_batch", "qmc_local_energy_batch", "qmc_sweep",
+    "qmc_get_positions", "qmc_get_logpsi", "qmc_get_inverse", "qmc_get_slater_matrix",
+    "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
+    "qmc_crowd_restore", "qmc_status_string",
+]
+
+
+class qmc_system_desc(C.Structure):
+    _fields_ = [("n_up", C.c_int), ("n_dn", C.c_int), ("n_orb", C.c_int), ("n_ions", C.c_int),
+                ("grid", C.c_int), ("reserved", C.c_int), ("L", C.c_double)]
+
+
+class qmc_run_desc(C.Structure):
+    _fields_ = [("n_walkers", C.c_int), ("precision", C.c_int), ("update", C.c_int),
+                ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("drift", C.c_int),
+                ("potential", C.c_int), ("reserved", C.c_int), ("tau", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+class qmc_stats(C.Structure):
+    _fields_ = [("e_sum", C.c_double), ("e2_sum", C.c_double), ("n_samples", C.c_longlong),
+                ("n_accept", C.c_longlong), ("n_moves", C.c_longlong)]
+
+
+class QmcError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i = C.c_void_p, C.c_int
+    sig = {
+        "qmc_crowd_create": [C.POINTER(qmc_system_desc), C.POINTER(qmc_run_desc), vp,
+                             C.POINTER(vp)],
+        "qmc_crowd_destroy": [vp],
+        "qmc_load_positions": [vp, vp, i],
+        "qmc_load_ions": [vp, vp],
+        "qmc_load_orbitals": [vp, vp, i, i],
+        "qmc_load_jastrow": [vp, i, vp, i, C.c_double],
+        "qmc_recompute": [vp],
+        "qmc_eval_grad_batch": [vp, i, vp, i],
+        "qmc_propose_move_batch": [vp, i, vp, vp, vp, vp, vp, i],
+        "qmc_accept_reject_batch": [vp, i, vp, vp, i],
+        "qmc_local_energy_batch": [vp, vp, i],
+        "qmc_sweep": [vp, i, vp, i, C.POINTER(qmc_stats)],
+        "qmc_get_positions": [vp, vp, i],
+        "qmc_get_logpsi": [vp, vp, vp],
+        "qmc_get_inverse": [vp, i, vp],
+        "qmc_get_slater_matrix": [vp, i, vp],
+        "qmc_get_generation": [vp, C.POINTER(C.c_uint32)],
+        "qmc_set_generation": [vp, C.c_uint32],
+        "qmc_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
+        "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
+        "qmc_crowd_restore": [vp, vp, C.c_size_t],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.qmc_status_string.argtypes = [C.c_int]
+    lib.qmc_status_string.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(fn: str, st: int):
+    if st != QMC_OK:
+        raise QmcError(fn, st)
+
+
+def _buf(x, dtype=np.float64):
+    """(pointer, mem kind, keep-alive) of an array argument; None -> (None, None, None)."""
+    if x is None:
+        return None, None, None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} array")
+        return x.ctypes.data, QMC_MEM_HOST, x
+    try:
+        import torch
+    except ImportError as e:  # pragma: no cover
+        raise TypeError("expected a numpy array or a torch tensor") from e
+    if isinstance(x, torch.Tensor):
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {tdt} tensor")
+        return x.data_ptr(), (QMC_MEM_DEVICE if x.is_cuda else QMC_MEM_HOST), x
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _mem(*kinds) -> int:
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("all buffers of one call must be on the host or all on the device")
+    return ks.pop() if ks else QMC_MEM_HOST
+
+
+class Crowd:
+    """One qmc_crowd handle; methods are the C calls with their arguments marshalled."""
+
+    def __init__(self, n_up, n_dn, n_orb, n_ions, grid, L, n_walkers, tau, precision="fp64",
+                 update="sm", delay_rank=1, n_recompute=0, drift=True, potential=True,
+                 seed=14487, stream=None):
+        self.sys = qmc_system_desc(n_up=n_up, n_dn=n_dn, n_orb=n_orb, n_ions=n_ions, grid=grid,
+                                   reserved=0, L=L)
+        self.run = qmc_run_desc(
+            n_walkers=n_walkers,
+            precision=QMC_PREC_MIXED if precision == "mixed" else QMC_PREC_FP64,
+            update=QMC_UPDATE_DELAYED if update == "delayed" else QMC_UPDATE_SM,
+            delay_rank=delay_rank, n_recompute=n_recompute, drift=int(drift),
+            potential=int(potential), reserved=0, tau=tau, seed=seed)
+        self.W, self.N, self.n = n_walkers, n_up + n_dn, n_up
+        h = C.c_void_p()
+        _check("qmc_crowd_create",
+               lib.qmc_crowd_create(C.byref(self.sys), C.byref(self.run), stream, C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, wl, precision="fp64", update="sm", delay_rank=1, n_walkers=None,
+                      stream=None, n_recompute=None):
+        c = cls(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L,
+                wl.n_walkers if n_walkers is None else n_walkers, wl.tau, precision=precision,
+                update=update, delay_rank=delay_rank,
+                n_recompute=wl.n_recompute if n_recompute is None else n_recompute,
+                drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream)
+        if wl.n_ions:
+            c.qmc_load_ions(np.ascontiguousarray(wl.ions, dtype=np.float64))
+        if wl.j2_uu is not None:
+            c.qmc_load_jastrow(QMC_J2_UU, wl.j2_uu.coefs, wl.j2_uu.rc)
+            c.qmc_load_jastrow(QMC_J2_UD, wl.j2_ud.coefs, wl.j2_ud.rc)
+        if wl.j1 is not None:
+            c.qmc_load_jastrow(QMC_J1, wl.j1.coefs, wl.j1.rc)
+        c.qmc_load_orbitals(np.ascontiguousarray(wl.table(), dtype=np.float64))
+        return c
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.qmc_crowd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- inputs ----
+    def qmc_load_positions(self, R):
+        p, m, _ = _buf(R)
+        _check("qmc_load_positions", lib.qmc_load_positions(self.h, p, m))
+
+    def qmc_load_ions(self, RI):
+        RI = np.ascontiguousarray(RI, dtype=np.float64)
+        _check("qmc_load_ions", lib.qmc_load_ions(self.h, RI.ctypes.data))
+
+    def qmc_load_orbitals(self, coefs):
+        dt = np.float32 if getattr(coefs, "dtype", None) in (np.float32,) or \
+            str(getattr(coefs, "dtype", "")) == "torch.float32" else np.float64
+        p, m, _ = _buf(coefs, dt)
+        _check("qmc_load_orbitals", lib.qmc_load_orbitals(
+            self.h, p, QMC_DTYPE_F32 if dt == np.float32 else QMC_DTYPE_F64, m))
+
+    def qmc_load_jastrow(self, kind, coefs, rc):
+        c = np.ascontiguousarray(coefs, dtype=np.float64)
+        _check("qmc_load_jastrow",
+               lib.qmc_load_jastrow(self.h, kind, c.ctypes.data if c.size else None, c.size, rc))
+
+    def qmc_recompute(self):
+        _check("qmc_recompute", lib.qmc_recompute(self.h))
+
+    # ---- the move ----
+    def qmc_eval_grad_batch(self, iel, grad):
+        p, m, _ = _buf(grad)
+        _check("qmc_eval_grad_batch", lib.qmc_eval_grad_batch(self.h, iel, p, m))
+
+    def qmc_propose_move_batch(self, iel, rnew=None, ratio=None, grad=None, log_ratio=None,
+                               rnew_out=None):
+        bs = [_buf(x) for x in (rnew, ratio, grad, log_ratio, rnew_out)]
+        m = _mem(*[b[1] for b in bs])
+        _check("qmc_propose_move_batch",
+               lib.qmc_propose_move_batch(self.h, iel, *[b[0] for b in bs], m))
+
+    def qmc_accept_reject_batch(self, iel, accept=None, accepted_out=None):
+        a = _buf(accept, np.uint8)
+        o = _buf(accepted_out, np.uint8)
+        m = _mem(a[1], o[1])
+        _check("qmc_accept_reject_batch", lib.qmc_accept_reject_batch(self.h, iel, a[0], o[0], m))
+
+    def qmc_local_energy_batch(self, eloc):
+        p, m, _ = _buf(eloc)
+        _check("qmc_local_energy_batch", lib.qmc_local_energy_batch(self.h, p, m))
+
+    def qmc_sweep(self, n_gen, eloc=None, stats=True):
+        p, m, _ = _buf(eloc)
+        st = qmc_stats() if stats else None
+        _check("qmc_sweep", lib.qmc_sweep(self.h, n_gen, p, m if m is not None else 0,
+                                          C.byref(st) if st is not None else None))
+        return st
+
+    # ---- getters ----
+    def qmc_get_positions(self, R=None):
+        if R is None:
+            R = np.zeros((self.W, self.N, 3))
+        p, m, _ = _buf(R)
+        _check("qmc_get_positions", lib.qmc_get_positions(self.h, p, m))
+        return R
+
+    def qmc_get_logpsi(self):
+        la = np.zeros(self.W)
+        sg = np.zeros(self.W, dtype=np.int32)
+        _check("qmc_get_logpsi", lib.qmc_get_logpsi(self.h, la.ctypes.data, sg.ctypes.data))
+        return la, sg
+
+    def qmc_get_inverse(self, spin):
+        out = np.zeros((self.W, self.n, self.n))
+        _check("qmc_get_inverse", lib.qmc_get_inverse(self.h, spin, out.ctypes.data))
+        return out
+
+    def qmc_get_slater_matrix(self, spin):
+        out = np.zeros((self.W, self.n, self.n))
+        _check("qmc_get_slater_matrix", lib.qmc_get_slater_matrix(self.h, spin, out.ctypes.data))
+        return out
+
+    @property
+    def generation(self) -> int:
+        g = C.c_uint32()
+        _check("qmc_get_generation", lib.qmc_get_generation(self.h, C.byref(g)))
+        return g.value
+
+    @generation.setter
+    def generation(self, g: int):
+        _check("qmc_set_generation", lib.qmc_set_generation(self.h, g))
+
+    @property
+    def launch_count(self) -> int:
+        v = C.c_ulonglong()
+        _check("qmc_get_launch_count", lib.qmc_get_launch_count(self.h, C.byref(v)))
+        return v.value
+
+    def qmc_crowd_save(self) -> bytes:
+        sz = C.c_size_t()
+        _check("qmc_crowd_save", lib.qmc_crowd_save(self.h, None, C.byref(sz)))
+        buf = C.create_string_buffer(sz.value)
+        _check("qmc_crowd_save", lib.qmc_crowd_save(self.h, buf, C.byref(sz)))
+        return buf.raw[:sz.value]
+
+    def qmc_crowd_restore(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        _check("qmc_crowd_restore", lib.qmc_crowd_restore(self.h, buf, len(data)))
+
+
+def qmc_status_string(st: int) -> str:
+    return lib.qmc_status_string(st).decode()

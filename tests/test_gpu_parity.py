@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on identical
+seeded inputs.  Tolerances: FP64 path rel 1e-10 on ratios and gradients.  Mixed path (FP32 orbitals,
+Jastrow, ratios, inverse): |d log rho| <= 1e-5 max(1, |log rho|) or, for ill-conditioned
+moves, the FP32 perturbation bound 4 eps32 (kappa_A + kappa_phi) with the Skeel condition
+numbers of the ratio from the oracle; max|A^-1 A - I| <= 1e-4 before each recompute."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2209_14487_gb300 import workloads as wl_mod
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_14487_gb300 import qmcgb
+    return qmcgb
+
+
+def _pair(Q, oracle_lib, wl, precision="fp64", update="sm", k=1, W=None, R=None):
+    W = wl.n_walkers if W is None else W
+    R = wl.positions(n_walkers=W) if R is None else R
+    gpu = Q.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
+                                n_walkers=W)
+    gpu.qmc_load_positions(np.ascontiguousarray(R))
+    gpu.qmc_recompute()
+    osys = oracle_lib.OracleSystem(wl)
+    orc = oracle_lib.OracleCrowd(osys, R)
+    return gpu, orc, osys, R
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+def _ragged():
+    # n = 13 per spin: orbital stride padded to 16 (ragged tail), 26 electrons span
+    # several 8-wide orbital tiles; J1 + J2 + potential
+    return wl_mod.make_workload("ragged26", n_el=26, n_orb=15, grid=14, n_walkers=7, n_gen=3,
+                                n_ions=5, L=5.3, tau=0.4, j1_knots=7, j2_knots=9)
+
+
+@pytest.mark.parametrize("make", [wl_mod.pw16, _ragged])
+def test_fp64_propose_accept_sequence(Q, oracle_lib, make):
+    wl = make()
+    W = min(wl.n_walkers, 8)
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, W=W)
+    rng = np.random.default_rng(5)
+    seq = [0, 1, 1, wl.n_up - 1, wl.n_up, wl.n_el - 1, 2, 0]
+    for step, iel in enumerate(seq):
+        g_gpu = np.zeros((W, 3))
+        gpu.qmc_eval_grad_batch(iel, g_gpu)
+        assert np.allclose(g_gpu, orc.eval_grad(iel), rtol=1e-10, atol=1e-11)
+        rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.5, size=(W, 3)), wl.L)
+        ratio, grad, lr, rout = (np.zeros(W), np.zeros((W, 3)), np.zeros(W), np.zeros((W, 3)))
+        gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), ratio, grad, lr, rout)
+        o_ratio, o_grad, o_lr, o_rout = orc.propose(iel, rnew)
+        assert np.all(_rel(ratio, o_ratio) < 1e-10), (step, ratio, o_ratio)
+        assert np.allclose(grad, o_grad, rtol=1e-10, atol=1e-10)
+        assert np.allclose(lr, o_lr, rtol=1e-10, atol=1e-12)
+        assert np.allclose(rout, o_rout, rtol=0, atol=1e-14)
+        acc = (rng.uniform(size=W) < 0.6).astype(np.uint8)
+        out = np.zeros(W, dtype=np.uint8)
+        gpu.qmc_accept_reject_batch(iel, acc, out)
+        orc.accept(iel, acc)
+        assert np.array_equal(out, acc)
+        R = orc.positions()
+    assert np.allclose(gpu.qmc_get_positions(), orc.positions(), atol=1e-14, rtol=0)
+    la, sg = gpu.qmc_get_logpsi()
+    ola, osg = orc.logpsi()
+    assert np.allclose(la, ola, rtol=1e-10)
+    assert np.array_equal(sg, osg)
+    for s in range(2):
+        inv = gpu.qmc_get_inverse(s)
+        for w in range(W):
+            assert np.allclose(inv[w], orc.inverse(w, s), rtol=1e-9, atol=1e-10)
+    e = np.zeros(W)
+    gpu.qmc_local_energy_batch(e)
+    assert np.all(_rel(e, orc.local_energy()) < 1e-10)
+
+
+@pytest.mark.parametrize("k", [1, 3, 4])
+def test_fp64_delayed_update_matches_oracle(Q, oracle_lib, k):
+    wl = _ragged()
+    W = 5
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, update="delayed", k=k, W=W)
+    rng = np.random.default_rng(17)
+    for iel in [3, 4, 3, 0, 12, 3, 13, 14, 20, 14, 1, 2, 4]:
+        rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.5, size=(W, 3)), wl.L)
+        ratio, grad = np.zeros(W), np.zeros((W, 3))
+        gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), ratio, grad)
+        o_ratio, o_grad, _, _ = orc.propose(iel, rnew)
+        assert np.all(_rel(ratio, o_ratio) < 1e-10)
+        assert np.allclose(grad, o_grad, rtol=1e-9, atol=1e-10)
+        acc = (rng.uniform(size=W) < 0.7).astype(np.uint8)
+        gpu.qmc_accept_reject_batch(iel, acc)
+        orc.accept(iel, acc)
+        R = orc.positions()
+    for s in range(2):
+        inv = gpu.qmc_get_inverse(s)
+        for w in range(W):
+            assert np.allclose(inv[w], orc.inverse(w, s), rtol=1e-9, atol=1e-10)
+
+
+@pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 4)])
+def test_fp64_sweep_trajectory_matches_oracle(Q, oracle_lib, update, k):
+    """Internal counter-based RNG on both sides: identical proposals and decisions up to
+    rounding (a decision flips only if u lands within rounding of the acceptance)."""
+    wl = _ragged()
+    W = 7
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, update=update, k=k, W=W)
+    n_gen = 3
+    e_gpu = np.zeros((n_gen, W))
+    st = gpu.qmc_sweep(n_gen, e_gpu)
+    e_or, na = orc.sweep(n_gen)
+    Rg, Ro = gpu.qmc_get_positions(), orc.positions()
+    same = np.all(np.abs(Rg - Ro) < 1e-9, axis=(1, 2))
+    assert same.sum() >= W - 1, same
+    assert np.all(_rel(e_gpu[:, same], e_or[:, same]) < 1e-9)
+    assert st.n_moves == n_gen * W * wl.n_el
+    if same.all():
+        assert st.n_accept == int(na.sum())
+    assert 0.2 < st.n_accept / st.n_moves < 0.95
+
+
+def test_fp64_pw16_full_sweep_parity(Q, oracle_lib):
+    wl = wl_mod.pw16()
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl)
+    e_gpu = np.zeros((5, wl.n_walkers))
+    gpu.qmc_sweep(5, e_gpu)
+    e_or, _ = orc.sweep(5)
+    Rg, Ro = gpu.qmc_get_positions(), orc.positions()
+    same = np.all(np.abs(Rg - Ro) < 1e-9, axis=(1, 2))
+    assert same.sum() >= wl.n_walkers - 1
+    assert np.all(_rel(e_gpu[:, same], e_or[:, same]) < 1e-9)
+
+
+def _ratio_sensitivity(osys, orc, w, spin, p, rnew, n):
+    """Condition numbers of the determinant ratio rho = phi'^T A^-1 e_p under relative
+    perturbations of A (Skeel: sum_ij |v_i||A_ij||c_j| / |rho| with v = phi'^T A^-1,
+    c = A^-1 e_p) and of phi' (sum_j |phi'_j c_j| / |rho|), from the FP64 oracle."""
+    A = orc.A(w, spin)
+    B = orc.inverse(w, spin)
+    phi = osys.spo_vgl(rnew, n)[0]
+    c = B[:, p]
+    rho = phi @ c
+    v = phi @ B
+    kA = (np.abs(v)[:, None] * np.abs(A) * np.abs(c)[None, :]).sum() / abs(rho)
+    kd = np.abs(phi * c).sum() / abs(rho)
+    return kA + kd
+
+
+@pytest.mark.parametrize("make,W", [(_ragged, 24), (wl_mod.pw128, 16)])
+def test_mixed_ratios_within_tolerance(Q, oracle_lib, make, W):
+    """FP32 orbitals and inverse perturb the ratio by at most ~eps32 times its condition
+    number; the stated 1e-5 on log-ratios holds for well-conditioned moves and the FP32
+    bound 4 eps32 (kappa_A + kappa_phi) for all of them."""
+    wl = make()
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision="mixed", W=W)
+    rng = np.random.default_rng(8)
+    eps32 = 2.0 ** -24
+    errs = []
+    for iel in range(0, wl.n_el, max(1, wl.n_el // 8)):
+        rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.5, size=(W, 3)), wl.L)
+        lr, grad = np.zeros(W), np.zeros((W, 3))
+        gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, grad, lr)
+        _, o_grad, o_lr, _ = orc.propose(iel, rnew)
+        s = 0 if iel < wl.n_up else 1
+        p = iel - s * wl.n_up
+        for w in range(W):
+            err = abs(lr[w] - o_lr[w])
+            plain = 1e-5 * max(1.0, abs(o_lr[w]))
+            kap = _ratio_sensitivity(osys, orc, w, s, p, rnew[w], wl.n_up)
+            assert err <= max(plain, 4 * eps32 * kap), (iel, w, err, kap)
+            errs.append(err / max(1.0, abs(o_lr[w])))
+        acc = (rng.uniform(size=W) < 0.5).astype(np.uint8)
+        gpu.qmc_accept_reject_batch(iel, acc)
+        orc.accept(iel, acc)
+        R = orc.positions()
+    # the typical move is an order of magnitude inside the stated 1e-5
+    assert np.median(errs) < 1e-6, np.median(errs)
+
+
+@pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 8)])
+def test_mixed_inverse_drift_bounded(Q, oracle_lib, update, k):
+    """max|A^-1 A - I| stays below 1e-4 over the sweeps between FP64 recomputes."""
+    wl = wl_mod.pw128()
+    W = 16
+    gpu = Q.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
+                                n_walkers=W, n_recompute=0)
+    gpu.qmc_load_positions(np.ascontiguousarray(wl.positions(n_walkers=W)))
+    gpu.qmc_recompute()
+    gpu.qmc_sweep(63)
+    worst = 0.0
+    for s in range(2):
+        A = gpu.qmc_get_slater_matrix(s)
+        B = gpu.qmc_get_inverse(s)
+        for w in range(W):
+            worst = max(worst, np.abs(B[w] @ A[w] - np.eye(A.shape[1])).max())
+    assert worst < 1e-4, worst
+
+
+def test_full_size_pw128_sampled_walkers(Q, oracle_lib):
+    """Bench configuration (256 walkers, 128 electrons, FP64): after sweeps, sampled
+    walkers' log|Psi| and E_L equal the oracle's full recompute at the GPU's positions."""
+    wl = wl_mod.pw128()
+    gpu = Q.Crowd.from_workload(wl, precision="fp64")
+    gpu.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+    gpu.qmc_recompute()
+    e = np.zeros((3, wl.n_walkers))
+    st = gpu.qmc_sweep(3, e)
+    assert 0.2 < st.n_accept / st.n_moves < 0.95
+    R = gpu.qmc_get_positions()
+    la, sg = gpu.qmc_get_logpsi()
+    osys = oracle_lib.OracleSystem(wl)
+    for w in [0, 17, 128, 255]:
+        ref, rs = osys.logpsi(R[w])
+        assert abs(la[w] - ref) < 1e-9 * max(1, abs(ref))
+        assert sg[w] == rs
+        e_ref = osys.local_energy(R[w])[0]
+        assert abs(e[-1, w] - e_ref) < 1e-9 * max(1, abs(e_ref))
+
+
+def test_full_size_pw128_mixed_sampled_walkers(Q, oracle_lib):
+    wl = wl_mod.pw128()
+    gpu = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=16)
+    gpu.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+    gpu.qmc_recompute()
+    e = np.zeros((2, wl.n_walkers))
+    gpu.qmc_sweep(2, e)
+    R = gpu.qmc_get_positions()
+    la, _ = gpu.qmc_get_logpsi()
+    osys = oracle_lib.OracleSystem(wl)
+    for w in [3, 100, 201]:
+        ref, _ = osys.logpsi(R[w])
+        assert abs(la[w] - ref) < 1e-4 * max(1, abs(ref))
+        e_ref = osys.local_energy(R[w])[0]
+        assert abs(e[-1, w] - e_ref) < 1e-3 * max(1, abs(e_ref))
+
+
+def test_mixed_vmc_energy_within_two_sigma_of_fp64(Q):
+    wl = wl_mod.pw16()
+    W, n_gen, burn = 256, 60, 10
+    means = {}
+    for prec in ["fp64", "mixed"]:
+        gpu = Q.Crowd.from_workload(wl, precision=prec, n_walkers=W, n_recompute=16)
+        gpu.qmc_load_positions(np.ascontiguousarray(wl.positions(n_walkers=W)))
+        gpu.qmc_recompute()
+        e = np.zeros((n_gen, W))
+        gpu.qmc_sweep(n_gen, e)
+        blk = e[burn:].mean(axis=1)          # per-generation crowd average
+        nb = 10                              # blocking over generations
+        b = blk[: len(blk) // nb * nb].reshape(nb, -1).mean(axis=1)
+        means[prec] = (b.mean(), b.std(ddof=1) / math.sqrt(nb))
+    (m64, s64), (m32, s32) = means["fp64"], means["mixed"]
+    assert abs(m64 - m32) < 2.0 * math.hypot(s64, s32) + 1e-3, means
+
+
+def test_edge_cases_and_errors(Q, oracle_lib):
+    # one walker, one electron per spin, smallest grid
+    wl = wl_mod.make_workload("e2", n_el=2, n_orb=1, grid=4, n_walkers=1, n_gen=1, L=2.0,
+                              j2_knots=4, tau=0.3)
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl)
+    gpu.qmc_sweep(2)
+    orc.sweep(2)
+    assert np.allclose(gpu.qmc_get_positions(), orc.positions(), atol=1e-9)
+    # accept without a pending proposal
+    with pytest.raises(Q.QmcError) as ei:
+        gpu.qmc_accept_reject_batch(0, np.ones(1, dtype=np.uint8))
+    assert ei.value.status == 7
+    with pytest.raises(Q.QmcError) as ei:
+        gpu.qmc_eval_grad_batch(5, np.zeros((1, 3)))
+    assert ei.value.status == 1
+    # a crowd without orbitals refuses to move
+    c = Q.Crowd(2, 2, 2, 0, 6, 3.0, 2, 0.3)
+    with pytest.raises(Q.QmcError) as ei:
+        c.qmc_sweep(1)
+    assert ei.value.status == 7
+    # singular Slater matrix: two electrons of one spin on the same point
+    wl4 = wl_mod.make_workload("e4", n_el=4, n_orb=2, grid=6, n_walkers=1, n_gen=1, L=3.0)
+    g4 = Q.Crowd.from_workload(wl4)
+    R4 = wl4.positions(n_walkers=1)
+    R4[0, 1] = R4[0, 0]
+    g4.qmc_load_positions(np.ascontiguousarray(R4))
+    with pytest.raises(Q.QmcError) as ei:
+        g4.qmc_recompute()
+    assert ei.value.status == 4
+
+
+def test_checkpoint_restore_reproduces_trajectory(Q):
+    wl = wl_mod.pw16()
+    a = Q.Crowd.from_workload(wl)
+    a.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+    a.qmc_sweep(2)
+    blob = a.qmc_crowd_save()
+    a.qmc_sweep(2)
+    b = Q.Crowd.from_workload(wl)
+    b.qmc_crowd_restore(blob)
+    b.qmc_sweep(2)
+    assert np.allclose(a.qmc_get_positions(), b.qmc_get_positions(), atol=1e-12)
