@@ -173,6 +173,29 @@ int qmc_crowd_restore(qmc_crowd* crowd, const void* buf, size_t size);
 
 const char* qmc_status_string(int status);
 
+/* Allocation-free FP64 inverse of a batch of dense matrices.  The paper has no
+ * counterpart: this call exists for callers that must not allocate device memory when
+ * they need it, such as code in a host callback, a latency-critical loop where
+ * cudaMalloc's implicit synchronisation is not allowed, or a runtime that owns all device
+ * memory through its own pool.
+ *   a      [batch][n][n] device, row major (not modified)
+ *   inv    [batch][n][n] device: inv[b][j][l] = (a_b^-1)[j][l]; filled with NaN when a_b
+ *          is singular
+ *   logdet [batch] device: log|det a_b| (-inf when singular)
+ *   sign   [batch] device: sign of det a_b, 0 when a zero pivot shows a_b singular
+ * LU with partial pivoting in FP64, asynchronous on cuda_stream (NULL: legacy default
+ * stream).  The LU factors live in one 16 MiB static device array that the library holds
+ * on every GPU that loads it until the process exits; a batch larger than 2^21 / n^2
+ * matrices runs as several launches in stream order.  Limits: 1 <= n <= 1024 (else
+ * QMC_ERR_INVALID_ARG / QMC_ERR_UNSUPPORTED), batch >= 0.  No device memory is allocated
+ * or freed and no allocating library routine is called.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and corrupt each other's results.  Nothing in the
+ * array has to start at zero: each launch overwrites the factors it reads. */
+int qmc_inverse_noalloc(const double* a, int n, int batch, double* inv, double* logdet,
+                        int* sign, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

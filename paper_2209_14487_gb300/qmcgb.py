@@ -32,7 +32,7 @@ EXPORTS = [
     "qmc_propose_move_batch", "qmc_accept_reject_batch", "qmc_local_energy_batch", "qmc_sweep",
     "qmc_get_positions", "qmc_get_logpsi", "qmc_get_inverse", "qmc_get_slater_matrix",
     "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
-    "qmc_crowd_restore", "qmc_status_string",
+    "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc",
 ]
 
 
@@ -93,6 +93,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = C.c_int
+    lib.qmc_inverse_noalloc.argtypes = [vp, i, i, vp, vp, vp, vp]
+    lib.qmc_inverse_noalloc.restype = C.c_int
     lib.qmc_status_string.argtypes = [C.c_int]
     lib.qmc_status_string.restype = C.c_char_p
     return lib
@@ -285,6 +287,23 @@ class Crowd:
     def qmc_crowd_restore(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         _check("qmc_crowd_restore", lib.qmc_crowd_restore(self.h, buf, len(data)))
+
+
+def qmc_inverse_noalloc(a, inv, logdet, sign, stream=None):
+    """FP64 inverse, log|det| and sign of a batch of n x n matrices without any device
+    allocation (all four arguments are CUDA tensors: a, inv float64 [batch][n][n], logdet
+    float64 [batch], sign int32 [batch]); asynchronous on `stream` (a cudaStream_t
+    handle, None for the legacy default stream)."""
+    import torch
+    for t in (a, inv, logdet, sign):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise TypeError("qmc_inverse_noalloc takes contiguous CUDA tensors")
+    if a.dtype != torch.float64 or inv.dtype != torch.float64 or logdet.dtype != torch.float64 \
+            or sign.dtype != torch.int32:
+        raise TypeError("a, inv, logdet: float64; sign: int32")
+    batch, n = a.shape[0], a.shape[-1]
+    _check("qmc_inverse_noalloc", lib.qmc_inverse_noalloc(
+        a.data_ptr(), n, batch, inv.data_ptr(), logdet.data_ptr(), sign.data_ptr(), stream))
 
 
 def qmc_status_string(st: int) -> str:
