@@ -121,7 +121,9 @@ __device__ __forceinline__ void radial(const T* __restrict__ c, int K, T hinv, T
   u = du = d2u = T(0);
   if (!(r < rc)) return;
   const T x = r * hinv;
-  int i = (int)floor(x);
+  int i;
+  if constexpr (sizeof(T) == 4) i = __float2int_rd(x);
+  else i = __double2int_rd(x);
   i = i > K - 1 ? K - 1 : (i < 0 ? 0 : i);
   const T t = x - T(i);
   const T t2 = t * t, t3 = t2 * t, s = T(1) - t;

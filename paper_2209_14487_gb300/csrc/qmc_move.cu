@@ -166,16 +166,19 @@ struct Ctx {
 // ---------------------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void partner_disp(const Ctx<T>& c, const double* x, const uint32_t* q,
-                                             int t, T* d, T& r) {
+                                             int t, T* d, T& r, T& rinv) {
   const Params& p = c.p;
   if constexpr (IsMixed<T>::value) {
     const uint32_t* b = t < p.N ? c.Rq + 3 * t : c.ionq + 3 * (t - p.N);
     disp_fx(q, b, c.k.unit, d);
-    r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    rinv = rsqrtf(r2);
+    r = r2 * rinv;
   } else {
     const double* b = t < p.N ? c.R + 3 * t : c.ion + 3 * (t - p.N);
     disp_f64(x, b, p.L, p.invL, d);
     r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    rinv = 1.0 / r;
   }
 }
 
@@ -379,15 +382,15 @@ __device__ void eval_grad(Ctx<T>& c, int i, const T* pf, bool use_pf, T* uo, T* 
   int t0, t1;
   term_range(p, t0, t1);
   auto term = [&](int t, T& u_out) {
-    T d[3], r;
-    partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r);
+    T d[3], r, rinv;
+    partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r, rinv);
     const T* coef; int K; T hinv, rc;
     functor(c, i, t, coef, K, hinv, rc);
     T u, du, d2u;
     radial(coef, K, hinv, rc, r, u, du, d2u);
     u_out = u;
     if (r > T(0)) {
-      const T f = du / r;
+      const T f = du * rinv;
       v[3] += f * d[0];
       v[4] += f * d[1];
       v[5] += f * d[2];
@@ -483,20 +486,20 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   int t0, t1;
   term_range(p, t0, t1);
   auto term = [&](int t, bool have_old, T uold) {
-    T dn[3], rn;
-    partner_disp(c, pr.rp, pr.rq, t, dn, rn);
+    T dn[3], rn, rninv;
+    partner_disp(c, pr.rp, pr.rq, t, dn, rn, rninv);
     const T* coef; int K; T hinv, rc;
     functor(c, i, t, coef, K, hinv, rc);
     T un, dun, d2n;
     radial(coef, K, hinv, rc, rn, un, dun, d2n);
     if (!have_old) {
-      T dol[3], ro, duo, d2o;
-      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro);
+      T dol[3], ro, roinv, duo, d2o;
+      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro, roinv);
       radial(coef, K, hinv, rc, ro, uold, duo, d2o);
     }
     v[4] += un - uold;
     if (rn > T(0)) {
-      const T f = dun / rn;
+      const T f = dun * rninv;
       v[5] += f * dn[0];
       v[6] += f * dn[1];
       v[7] += f * dn[2];
@@ -589,14 +592,27 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
   const int n = p.n, n_pad = p.n_pad, bs = c.bs;
   T* rw = c.rows + (size_t)i * 5 * n_pad;
   if (p.update == 0) {
-    // Sherman-Morrison: v_k = phi'.B^T[k]; B^T[k] -= col (v_k - delta_k,pp) / rhoD
+    // Sherman-Morrison: v_k = phi'.B^T[k] (one thread per row), then
+    // B^T[k] -= col (v_k - delta_k,pp) / rhoD (one warp per row); f_k reuses `part`.
     const T invr = T(1) / rhoD;
+    T* fk = c.part;
+    for (int k = c.tid; k < n; k += NT) {
+      const T* row = c.B + (size_t)k * bs;
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      int j = 0;
+      for (; j + 4 <= n; j += 4) {
+        a0 += row[j] * c.phi[j];
+        a1 += row[j + 1] * c.phi[j + 1];
+        a2 += row[j + 2] * c.phi[j + 2];
+        a3 += row[j + 3] * c.phi[j + 3];
+      }
+      for (; j < n; ++j) a0 += row[j] * c.phi[j];
+      fk[k] = ((a0 + a1) + (a2 + a3) - (k == pp ? T(1) : T(0))) * invr;
+    }
+    __syncthreads();
     for (int k = c.warp; k < n; k += NWARP) {
+      const T f = fk[k];
       T* row = c.B + (size_t)k * bs;
-      T acc = 0;
-      for (int j = c.lane; j < n; j += 32) acc += c.phi[j] * row[j];
-      acc = warp_sum(acc);
-      const T f = (acc - (k == pp ? T(1) : T(0))) * invr;
       for (int j = c.lane; j < n; j += 32) row[j] -= c.col[j] * f;
     }
   } else {
@@ -679,15 +695,15 @@ __device__ double local_energy(Ctx<T>& c) {
     T v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int t = c.lane; t < N + NI; t += 32) {
       if (t == i) continue;
-      T d[3], r;
-      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r);
+      T d[3], r, rinv;
+      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r, rinv);
       const bool jas = t < N ? p.K2 > 0 : p.K1 > 0;
       if (jas && r > T(0)) {
         const T* coef; int K; T hinv, rc;
         functor(c, i, t, coef, K, hinv, rc);
         T u, du, d2u;
         radial(coef, K, hinv, rc, r, u, du, d2u);
-        const T f = du / r;
+        const T f = du * rinv;
         v[0] += f * d[0];
         v[1] += f * d[1];
         v[2] += f * d[2];
