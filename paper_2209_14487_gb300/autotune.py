@@ -1,0 +1,89 @@
+"""Autotuner for the inverse-update scheme of a crowd: Sherman-Morrison or a delayed
+(Woodbury) window of rank k, chosen by timing a few generations of each candidate on the
+current GPU.  Results are cached in a JSON file keyed by system size, crowd size,
+precision and GPU name.
+
+The timing uses CUDA events on a dedicated stream around qmc_sweep(1) calls; the crowd
+under test is built from the same workload the caller will run.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+DEFAULT_CANDIDATES = (("sm", 1), ("delayed", 2), ("delayed", 4), ("delayed", 8),
+                      ("delayed", 16), ("delayed", 32))
+
+
+def cache_path() -> str:
+    return os.environ.get("QMCGB_TUNE_CACHE",
+                          os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                       ".autotune_cache.json"))
+
+
+def _key(wl, precision: str, gpu: str) -> str:
+    return (f"{gpu}|N={wl.n_el}|n={wl.n_up}|G={wl.grid}|W={wl.n_walkers}|NI={wl.n_ions}|"
+            f"{precision}")
+
+
+def time_candidate(wl, precision: str, update: str, k: int, gens: int = 4,
+                   warmup: int = 2) -> float:
+    """Median milliseconds of one generation of the crowd with this update scheme."""
+    import torch
+
+    from . import qmcgb
+    prev = torch.cuda.current_stream()
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    try:
+        c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
+                                      stream=s.cuda_stream)
+        c.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+        c.qmc_recompute()
+        for _ in range(warmup):
+            c.qmc_sweep(1, stats=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(gens)]
+        for a, b in ev:
+            a.record(s)
+            c.qmc_sweep(1, stats=False)
+            b.record(s)
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        c.close()
+        return ms[len(ms) // 2]
+    finally:
+        torch.cuda.set_stream(prev)
+
+
+def tune(wl, precision: str = "mixed", candidates=DEFAULT_CANDIDATES, gens: int = 4,
+         use_cache: bool = True):
+    """(update, k, {candidate: ms}) for the fastest candidate; cached per GPU and shape."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = _key(wl, precision, gpu)
+    path = cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            e = cache[key]
+            return e["update"], e["k"], e["table"]
+    table = {}
+    for update, k in candidates:
+        table[f"{update}:{k}"] = time_candidate(wl, precision, update, k, gens=gens)
+    best = min(table, key=table.get)
+    update, k = best.split(":")[0], int(best.split(":")[1])
+    cache[key] = {"update": update, "k": k, "table": table}
+    try:
+        with open(path + ".tmp", "w") as fh:
+            json.dump(cache, fh, indent=1)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+    return update, k, table

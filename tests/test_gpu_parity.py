@@ -312,3 +312,32 @@ def test_checkpoint_restore_reproduces_trajectory(Q):
     b.qmc_crowd_restore(blob)
     b.qmc_sweep(2)
     assert np.allclose(a.qmc_get_positions(), b.qmc_get_positions(), atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pw512_inverse_in_global_memory(Q, oracle_lib, precision):
+    """n = 256 per spin: the 256 KB (FP32) inverse block does not fit in shared memory,
+    so the kernel works on the global-memory inverse; 4 stencil items per thread and
+    two Jastrow partner passes per thread."""
+    wl = wl_mod.pw512()
+    W = 3
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision=precision, W=W)
+    rng = np.random.default_rng(12)
+    for iel in [0, 255, 256, 511, 17]:
+        rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.4, size=(W, 3)), wl.L)
+        lr, grad = np.zeros(W), np.zeros((W, 3))
+        gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, grad, lr)
+        _, o_grad, o_lr, _ = orc.propose(iel, rnew)
+        tol = 1e-10 if precision == "fp64" else 2e-4
+        assert np.all(np.abs(lr - o_lr) <= tol * np.maximum(1.0, np.abs(o_lr))), (lr, o_lr)
+        acc = np.array([1, 0, 1], dtype=np.uint8)
+        gpu.qmc_accept_reject_batch(iel, acc)
+        orc.accept(iel, acc)
+        R = orc.positions()
+    if precision == "fp64":
+        e = np.zeros((1, W))
+        gpu.qmc_sweep(1, e)
+        e_or, _ = orc.sweep(1)
+        same = np.all(np.abs(gpu.qmc_get_positions() - orc.positions()) < 1e-9, axis=(1, 2))
+        assert same.sum() >= W - 1
+        assert np.all(np.abs(e[:, same] - e_or[:, same]) < 1e-9 * np.abs(e_or[:, same]))

@@ -445,3 +445,31 @@ def test_metropolis_samples_psi_squared(oracle_lib, drift, wave):
     chi2 = ((counts - exp_counts) ** 2 / exp_counts).sum()
     pval = stats.chi2.sf(chi2, nb ** 3 - 1)
     assert pval > 1e-3, (chi2, pval)
+
+
+def test_potential_and_jastrow_pair_structure_closed_forms(oracle_lib):
+    """Two electrons (opposite spins) and one ion in a large cell: V and U by hand."""
+    L = 20.0
+    j2 = wl_mod.jastrow_coefs(8, 0.5, 3.0, cusp=-0.5)
+    j2l = wl_mod.jastrow_coefs(8, 0.5, 3.0, cusp=-0.25)
+    j1 = wl_mod.jastrow_coefs(6, -0.3, 3.0, cusp=None)
+    ions = np.array([[10.0, 10.0, 10.0]])
+    osys = oracle_lib.OracleSystem(None, n_up=1, n_dn=1, n_orb=1, n_ions=1, ions=ions, L=L,
+                                   potential=1, j2_K=8, j2_rc=3.0, j2_uu=j2l.coefs,
+                                   j2_ud=j2.coefs, j1_K=6, j1_rc=3.0, j1=j1.coefs, grid=4,
+                                   table=np.zeros((4, 4, 4, 1)))
+    R = np.array([[10.0, 10.0, 11.2], [10.0, 9.3, 10.0]])
+    r12 = math.sqrt(0.7 ** 2 + 1.2 ** 2)
+    V = math.exp(-r12 ** 2) - 2 * math.exp(-0.5 * 1.2 ** 2) - 2 * math.exp(-0.5 * 0.7 ** 2)
+    assert abs(osys.potential(R) - V) < 1e-14
+    U = (oracle_lib.radial(j2.coefs, 3.0, r12)[0] + oracle_lib.radial(j1.coefs, 3.0, 1.2)[0]
+         + oracle_lib.radial(j1.coefs, 3.0, 0.7)[0])
+    assert abs(osys.jastrow_U(R) - U) < 1e-14
+    # minimum image across the boundary and the L/2 truncation of V
+    R2 = np.array([[0.2, 10.0, 10.0], [19.9, 10.0, 10.0]])
+    ions2 = np.array([[0.0, 0.0, 0.0]])
+    osys2 = oracle_lib.OracleSystem(None, n_up=1, n_dn=1, n_orb=1, n_ions=1, ions=ions2, L=L,
+                                    potential=1, grid=4, table=np.zeros((4, 4, 4, 1)),
+                                    j2_K=8, j2_rc=3.0, j2_uu=j2l.coefs, j2_ud=j2.coefs)
+    assert abs(osys2.potential(R2) - math.exp(-0.3 ** 2)) < 1e-14  # ion beyond L/2 of both
+    assert abs(osys2.jastrow_U(R2) - oracle_lib.radial(j2.coefs, 3.0, 0.3)[0]) < 1e-14
