@@ -531,6 +531,14 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
       for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
     }
   }
+  for (int it = c.tid + 4 * NT; it < 4 * n; it += NT) {  // n > 256: items beyond four
+    const int j = it % n, a = it / n;
+    stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], j, a, cf);
+    T o4[4];
+    stencil_reduce(cf, wts, o4);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
+  }
   __syncthreads();
   const T dinv = c.k.dgrid;
   for (int j = c.tid; j < n; j += NT) {

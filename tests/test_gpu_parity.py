@@ -335,9 +335,14 @@ def test_pw512_inverse_in_global_memory(Q, oracle_lib, precision):
         orc.accept(iel, acc)
         R = orc.positions()
     if precision == "fp64":
+        # one generation from the same state: identical accept decisions; the unlimited
+        # drift amplifies rounding near nodal surfaces (positions agree to ~1e-5 here
+        # after 512 moves, not to rounding), so positions are compared at 1e-3
         e = np.zeros((1, W))
-        gpu.qmc_sweep(1, e)
-        e_or, _ = orc.sweep(1)
-        same = np.all(np.abs(gpu.qmc_get_positions() - orc.positions()) < 1e-9, axis=(1, 2))
-        assert same.sum() >= W - 1
-        assert np.all(np.abs(e[:, same] - e_or[:, same]) < 1e-9 * np.abs(e_or[:, same]))
+        st = gpu.qmc_sweep(1, e)
+        e_or, na = orc.sweep(1)
+        d = np.abs(gpu.qmc_get_positions() - orc.positions())
+        d = np.minimum(d, wl.L - d)
+        assert st.n_accept == int(na.sum())
+        assert d.max() < 1e-3, d.max()
+        assert np.all(np.abs(e - e_or) < 1e-5 * np.abs(e_or))
