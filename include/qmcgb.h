@@ -69,6 +69,8 @@ typedef struct qmc_system_desc {
 } qmc_system_desc;
 
 /* How the crowd is driven. */
+enum { QMC_STAGING_AUTO = 0, QMC_STAGING_LDG = 1 };
+
 typedef struct qmc_run_desc {
   int n_walkers;    /* W >= 1                                                         */
   int precision;    /* QMC_PREC_FP64: FP64 everywhere; QMC_PREC_MIXED: FP32 orbitals,  *
@@ -78,7 +80,9 @@ typedef struct qmc_run_desc {
   int n_recompute;  /* generations between FP64 recomputes of A^-1; 0 = never        */
   int drift;        /* 1: drift-diffusion proposal with Metropolis-Hastings            */
   int potential;    /* 1: add the model potential to E_L                              */
-  int reserved;
+  int staging;      /* QMC_STAGING_AUTO (0): each move's 4x4x4 x n orbital stencil is  *
+                     * copied to shared memory with one TMA tensor copy when it fits;  *
+                     * QMC_STAGING_LDG: the stencil is read with per-thread loads      */
   double tau;       /* time step                                                      */
   uint64_t seed;    /* Philox key: (low 32 bits, walker ^ high 32 bits)               */
 } qmc_run_desc;
@@ -164,6 +168,12 @@ int qmc_get_generation(qmc_crowd* crowd, uint32_t* gen);
 int qmc_set_generation(qmc_crowd* crowd, uint32_t gen);
 /* Number of kernel launches this crowd has issued so far. */
 int qmc_get_launch_count(qmc_crowd* crowd, unsigned long long* count);
+/* The move kernel's configuration, chosen at creation from the shared memory a CTA may
+ * use: 1 in *b_in_smem when the moving spin's inverse is staged in shared memory, 1 in
+ * *stencil_tma when each move's orbital stencil arrives by TMA, and the kernel's dynamic
+ * shared memory in bytes.  Any output pointer may be NULL.  Errors: INVALID_ARG. */
+int qmc_get_kernel_config(const qmc_crowd* crowd, int* b_in_smem, int* stencil_tma,
+                          int* smem_bytes);
 
 /* Checkpoint: positions, generation and RNG seed.  With buf == NULL, *size receives the
  * byte count; otherwise *size must hold at least that many bytes.  Restoring recomputes

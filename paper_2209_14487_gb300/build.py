@@ -63,7 +63,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags: list | None =
         objs = list(ex.map(compile_one, srcs))
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [exe] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcuda"]
+        cmd = [exe] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,6 +1,9 @@
 // Crowd runtime behind the C ABI of include/qmcgb.h: device state of a crowd of walkers
 // (arXiv:2209.14487, Sec. III "crowd"), its stream, the generation counter of the
 // counter-based RNG and the FP64 recompute cadence.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -47,6 +50,8 @@ struct qmc_crowd {
   bool has_orbitals = false, has_positions = false, stale = true;
   uint32_t gen = 0;
   unsigned long long launches = 0;
+  alignas(64) CUtensorMap tmap;  // the padded table as a 4-D tensor, for the stencil copy
+  size_t smem = 0;               // dynamic shared memory of the move kernel
 };
 
 namespace {
@@ -117,8 +122,42 @@ int launch_status(qmc_crowd* c, cudaError_t e) {
 }
 
 int move(qmc_crowd* c, int mode) {
-  if (is_mixed(c)) return launch_status(c, qmcgb::launch_move<float>(c->p, mode, c->stream));
-  return launch_status(c, qmcgb::launch_move<double>(c->p, mode, c->stream));
+  const void* tm = c->p.use_tma ? (const void*)&c->tmap : nullptr;
+  if (is_mixed(c)) return launch_status(c, qmcgb::launch_move<float>(c->p, mode, tm, c->stream));
+  return launch_status(c, qmcgb::launch_move<double>(c->p, mode, tm, c->stream));
+}
+
+// The padded table [GP][GP][GP][n_pad] (x slowest) as a 4-D tensor, innermost first, with
+// a box of one full 4x4x4 stencil: one copy per move lands it in shared memory.
+bool encode_table_map(qmc_crowd* c) {
+  const Params& p = c->p;
+  const cuuint64_t es = (cuuint64_t)c->es;
+  const cuuint64_t GP = (cuuint64_t)p.GP, np = (cuuint64_t)p.n_pad;
+  cuuint64_t dims[4] = {np, GP, GP, GP};
+  cuuint64_t strides[3] = {np * es, GP * np * es, GP * GP * np * es};  // bytes, dims 1..3
+  cuuint32_t box[4] = {(cuuint32_t)np, 4, 4, 4};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  std::memset(&c->tmap, 0, sizeof(c->tmap));
+  // the driver's encoder, looked up at run time so the library needs no driver at link
+  // or load time (hosts without a GPU still load it)
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  CUresult r = encode(
+      &c->tmap, is_mixed(c) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+      c->d_table, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 int read_status(qmc_crowd* c) {
@@ -129,6 +168,7 @@ int read_status(qmc_crowd* c) {
   if (st & qmcgb::ST_SINGULAR) return QMC_ERR_SINGULAR;
   if (st & qmcgb::ST_NAN) return QMC_ERR_NAN;
   if (st & qmcgb::ST_STATE) return QMC_ERR_STATE;
+  if (st & qmcgb::ST_TIMEOUT) return QMC_ERR_TIMEOUT;
   return QMC_OK;
 }
 
@@ -217,6 +257,8 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
       (run->delay_rank < 1 || run->delay_rank > qmcgb::MAX_K))
     return QMC_ERR_INVALID_ARG;
   if (run->n_recompute < 0) return QMC_ERR_INVALID_ARG;
+  if (run->staging != QMC_STAGING_AUTO && run->staging != QMC_STAGING_LDG)
+    return QMC_ERR_INVALID_ARG;
   if (sys->n_dn != sys->n_up) return QMC_ERR_UNSUPPORTED;
   if (sys->n_up > 1024 || sys->grid > 1024) return QMC_ERR_UNSUPPORTED;
 
@@ -259,18 +301,30 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.seed = run->seed;
   const int es = c->es;
 
-  // stage the moving spin's inverse in shared memory when the whole CTA fits
+  // Shared-memory plan, first that fits: the moving spin's inverse and the TMA-staged
+  // stencil, the inverse alone, the stencil alone, neither.  A TMA box is at most 256
+  // elements wide, so the staged stencil needs n_pad <= 256.
   const int optin = qmcgb::max_smem_optin();
-  p.b_in_smem = 1;
-  size_t smem = qmcgb::move_smem_bytes(p, es);
-  if (optin > 0 && smem > (size_t)optin) {
-    p.b_in_smem = 0;
+  const bool tma_ok = run->staging == QMC_STAGING_AUTO && p.n_pad <= 256;
+  const int plans[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
+  size_t smem = 0;
+  bool placed = false;
+  for (const auto& pl : plans) {
+    if (pl[1] && !tma_ok) continue;
+    p.b_in_smem = pl[0];
+    p.use_tma = pl[1];
+    p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
     smem = qmcgb::move_smem_bytes(p, es);
+    if (optin <= 0 || smem <= (size_t)optin) {
+      placed = true;
+      break;
+    }
   }
-  if (optin > 0 && smem > (size_t)optin) {
+  if (!placed) {
     delete c;
     return QMC_ERR_UNSUPPORTED;
   }
+  c->smem = smem;
 
   const size_t GP = (size_t)p.GP;
   int st = QMC_OK;
@@ -314,6 +368,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     delete c;
     return QMC_ERR_CUDA;
   }
+  if (p.use_tma && !encode_table_map(c)) p.use_tma = 0;  // plain loads then
   sync_params(c);
   int js = upload_jastrow(c);
   if (js) {
@@ -677,6 +732,14 @@ int qmc_get_generation(qmc_crowd* c, uint32_t* gen) {
 int qmc_set_generation(qmc_crowd* c, uint32_t gen) {
   if (!c) return QMC_ERR_INVALID_ARG;
   c->gen = gen;
+  return QMC_OK;
+}
+
+int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, int* smem_bytes) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (b_in_smem) *b_in_smem = c->p.b_in_smem;
+  if (stencil_tma) *stencil_tma = c->p.use_tma;
+  if (smem_bytes) *smem_bytes = (int)c->smem;
   return QMC_OK;
 }
 

@@ -70,6 +70,55 @@ __device__ __forceinline__ double accept_uniform(uint64_t seed, uint32_t walker,
   return uniform53(c[0], c[1]);
 }
 
+// FP32 draws of the mixed path from the same Philox words: 24-bit uniforms
+// (x >> 8 + 1/2) 2^-24 and an FP32 Box-Muller transform.
+__device__ __forceinline__ float uniform24(uint32_t x) {
+  return ((float)(x >> 8) + 0.5f) * 0x1p-24f;
+}
+
+__device__ __forceinline__ void move_draws_f32(uint64_t seed, uint32_t walker, uint32_t gen,
+                                               uint32_t iel, float* out) {
+  const uint32_t k0 = (uint32_t)seed, k1 = walker ^ (uint32_t)(seed >> 32);
+  uint32_t c[4] = {gen, iel, 0u, 0u};
+  philox4x32_10(c, k0, k1);
+  const float rad = sqrtf(-2.0f * logf(uniform24(c[0])));
+  float sn, cs;
+  sincospif(2.0f * uniform24(c[2]), &sn, &cs);
+  out[0] = rad * cs;
+  out[1] = rad * sn;
+  uint32_t c2[4] = {gen, iel, 1u, 0u};
+  philox4x32_10(c2, k0, k1);
+  out[2] = sqrtf(-2.0f * logf(uniform24(c2[0]))) * cospif(2.0f * uniform24(c2[2]));
+  uint32_t c3[4] = {gen, iel, 2u, 0u};
+  philox4x32_10(c3, k0, k1);
+  out[3] = uniform24(c3[0]);
+}
+
+__device__ __forceinline__ float accept_uniform_f32(uint64_t seed, uint32_t walker, uint32_t gen,
+                                                    uint32_t iel) {
+  uint32_t c[4] = {gen, iel, 2u, 0u};
+  philox4x32_10(c, (uint32_t)seed, walker ^ (uint32_t)(seed >> 32));
+  return uniform24(c[0]);
+}
+
+// Draws in the path's precision: FP64 Box-Muller for T = double, FP32 for T = float.
+template <typename T>
+__device__ __forceinline__ void draws_t(uint64_t seed, uint32_t walker, uint32_t gen,
+                                        uint32_t iel, T* out) {
+  if constexpr (sizeof(T) == 8) {
+    move_draws(seed, walker, gen, iel, out);
+  } else {
+    move_draws_f32(seed, walker, gen, iel, out);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T accept_uniform_t(uint64_t seed, uint32_t walker, uint32_t gen,
+                                              uint32_t iel) {
+  if constexpr (sizeof(T) == 8) return accept_uniform(seed, walker, gen, iel);
+  else return accept_uniform_f32(seed, walker, gen, iel);
+}
+
 // ---------------------------------------------------------------------------------------
 // Uniform cubic B-spline basis: weight q of a cell at t (q = 0..3 value, 4..7 first
 // derivative, 8..11 second derivative, all in cell units).
@@ -237,6 +286,94 @@ __device__ __forceinline__ void block_allreduce8(R* v, R* red) {
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
+}
+
+// Twenty-four values summed over the CTA (three transposed warp sums, one barrier); every
+// thread receives all totals.  `red` holds NWARP * 24 values.
+template <typename R>
+__device__ __forceinline__ void block_allreduce24(R* v, R* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const R c = warp_sum8_transposed(v + 8 * g);
+    if ((lane & 3) == 0) red[warp * 24 + 8 * g + (lane >> 2)] = c;
+  }
+  __syncthreads();
+  R t = R(0);
+  if (lane < 24) {
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) t += red[w * 24 + lane];
+  }
+#pragma unroll
+  for (int q = 0; q < 24; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
+}
+
+// ---------------------------------------------------------------------------------------
+// TMA and mbarrier helpers (inline PTX, sm_90+ forms available on sm_103a).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One 4-D tile of a tensor map into shared memory, completing on `bar`.
+// Coordinates are innermost first; c0 * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2,
+                                            int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"((unsigned long long)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for phase `parity` of `bar`, for at most about one second of wall time (and at
+// most 2^22 polls); false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+  return false;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -7,7 +7,10 @@
 
 namespace qmcgb {
 
-constexpr int NT = 256;            // threads per CTA of the walker kernels
+#ifndef QMCGB_NT
+#define QMCGB_NT 256
+#endif
+constexpr int NT = QMCGB_NT;       // threads per CTA of the walker kernels
 constexpr int NWARP = NT / 32;
 constexpr int MAX_K = 64;          // largest delay rank
 constexpr int MAX_KNOTS = 64;      // largest radial functor (free coefficients)
@@ -30,7 +33,7 @@ enum Mode {
 };
 
 // status bits written by kernels
-enum { ST_SINGULAR = 1, ST_NAN = 2, ST_STATE = 4 };
+enum { ST_SINGULAR = 1, ST_NAN = 2, ST_STATE = 4, ST_TIMEOUT = 8 };
 
 struct Params {
   int W, N, n_up, n;        // n = electrons per spin = occupied orbitals
@@ -40,6 +43,8 @@ struct Params {
   int K2, K1;               // free radial coefficients (0 = term absent)
   int b_in_smem;            // inverse of the moving spin staged in shared memory
   int skip_eloc;            // sweep without the local energy (a recompute comes first)
+  int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
+  int stencil_bytes;        // bytes of that copy
   int vs, ks;               // padded strides of the window's V rows and S^-1 rows
   uint32_t gen;
   double L, invL, tau, sqrt_tau, dgrid;   // dgrid = G / L
@@ -76,8 +81,10 @@ struct Params {
 size_t move_smem_bytes(const Params& p, int elem_bytes);
 int max_smem_optin();
 
+// tmap: host copy of the table's CUtensorMap (128 bytes), or null when p.use_tma == 0.
 template <typename T>
-cudaError_t launch_move(const Params& p, int mode, cudaStream_t s);
+cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s);
+int stencil_tma_bytes(const Params& p, int elem_bytes);
 template <typename T>
 cudaError_t launch_eval_rows(const Params& p, cudaStream_t s);
 template <typename T>

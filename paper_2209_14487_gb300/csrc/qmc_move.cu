@@ -13,7 +13,10 @@
 // evaluates the (cheap, deterministic) proposal and acceptance itself after each block
 // reduction, so the move needs three barriers plus one per accepted move; the FP64 path,
 // where GB300's FP64 rate makes redundant scalar work expensive, lets thread 0 do it.
+#include <cuda.h>
+
 #include <cmath>
+#include <cstring>
 
 #include "qmc_device.cuh"
 #include "qmc_internal.h"
@@ -38,11 +41,26 @@ struct Res {
   T rhoD, dU, rho, Fp[3];
 };
 
+// Drift of the next electron i1 (same spin, row pp1) gathered during the current move:
+// Jastrow gradient over all partners but the moving electron i (sj) plus the difference
+// of i's term between r'_i and r_i (dj), and a = dA_i1 . B[:,pp1], b = dA_i1 . col,
+// e = phi' . B[:,pp1], so that after an accept the determinant part is a - (e / rhoD) b.
+template <typename T>
+struct Next {
+  int i1, pp1;
+  const T* pf;           // this thread's dA row entries of i1 (orbital j = tid)
+  T a[3], b[3], e, sj[3], dj[3];
+  T uo[4];               // u(r_i1, r_t) of this thread's partner terms (t != i)
+  T ui_old, ui_new;      // the term with partner i, before and after the move
+  int qi;                // which of this thread's terms is partner i (-1: none)
+};
+
 template <typename T>
 struct Scal {
   Prop<T> pr;
   Res<T> rs;
   double logdet[2];
+  float lsum[2], lcomp[2];  // mixed path: Kahan sums of log|rhoD| since the kernel began
   int sign[2];
   int accept, m;
   T wts[48];
@@ -74,13 +92,18 @@ __device__ __forceinline__ Cst<T> make_cst(const Params& p) {
 }
 
 struct Lay {
-  size_t scal, B, R, Rq, ion, ionq, jc, phi, part, col, dchi, du, red0, red1;
+  size_t scal, bar, stc, B, R, Rq, ion, ionq, jc, phi, part, col, dchi, du, red0, red1;
   size_t wP, wV, wS, wy, wz, wc, wb, snap, xb, yb, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline int b_stride(const Params& p) { return p.b_in_smem ? p.n + 1 : p.n; }
+// Row stride of the inverse staged in shared memory: n + 4 floats (16-byte aligned rows,
+// conflict-free float4 reads by one thread per row) or n + 1 doubles.
+template <typename T>
+__host__ __device__ inline int b_stride(const Params& p) {
+  return p.b_in_smem ? p.n + (sizeof(T) == 4 ? 4 : 1) : p.n;
+}
 
 template <typename T>
 __host__ __device__ inline Lay make_lay(const Params& p) {
@@ -88,7 +111,9 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   Lay L{};
   size_t o = 0;
   L.scal = o; o += al16(sizeof(Scal<T>));
-  L.B = o; o += al16(p.b_in_smem ? (size_t)p.n * (p.n + 1) * es : 0);
+  L.bar = o; o += 16;
+  L.stc = o; o += p.use_tma ? al16((size_t)p.stencil_bytes + 128) : 0;  // +128: alignment slack
+  L.B = o; o += al16(p.b_in_smem ? (size_t)p.n * b_stride<T>(p) * es : 0);
   L.R = o; o += al16((size_t)p.N * 3 * 8);
   L.Rq = o; o += al16((size_t)p.N * 3 * 4);
   L.ion = o; o += al16((size_t)p.n_ions * 3 * 8);
@@ -98,9 +123,9 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.part = o; o += al16((size_t)16 * p.n_pad * es);
   L.col = o; o += al16((size_t)p.n_pad * es);
   L.dchi = o; o += al16((size_t)p.N * 3 * es);
-  L.du = o; o += al16((size_t)p.N * 8);
-  L.red0 = o; o += al16((size_t)NWARP * 8 * 8);
-  L.red1 = o; o += al16((size_t)NWARP * 8 * 8);
+  L.du = o; o += al16((size_t)p.N * es);
+  L.red0 = o; o += al16((size_t)NWARP * 24 * 8);
+  L.red1 = o; o += al16((size_t)NWARP * 24 * 8);
   L.wP = L.wV = L.wS = L.wy = L.wz = L.wc = L.wb = L.snap = L.xb = L.yb = o;
   if (p.update == 1) {
     L.wP = o; o += al16((size_t)MAX_K * 4);
@@ -118,6 +143,8 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   return L;
 }
 
+int stencil_tma_bytes(const Params& p, int elem_bytes) { return 64 * p.n_pad * elem_bytes; }
+
 size_t move_smem_bytes(const Params& p, int elem_bytes) {
   return elem_bytes == 4 ? make_lay<float>(p).total : make_lay<double>(p).total;
 }
@@ -128,6 +155,8 @@ struct Ctx {
   Cst<T> k;
   int w, tid, lane, warp;
   int bs;   // row stride of B
+  int upd;  // 0: Sherman-Morrison, 1: delayed window (a template constant of the kernel)
+  int bsm;  // where B lives: 1 shared, 2 global, 0 decided at run time (template constant)
   Scal<T>* sc;
   T* B;     // inverse (transposed) of the moving spin: shared or global
   T* Bs;    // shared staging buffer (if p.b_in_smem)
@@ -141,7 +170,7 @@ struct Ctx {
   T* part;
   T* col;
   T* dchi;
-  double* du;
+  T* du;
   T* red0;
   T* red1;
   int* wP;
@@ -155,6 +184,10 @@ struct Ctx {
   T* xb;
   T* yb;
   T* rows;  // this walker's global orbital rows [N][5][n_pad]
+  T* stc;   // TMA-staged stencil [4][4][4][n_pad] (x, y, z, orbital)
+  uint64_t* bar;
+  const void* tmap;
+  uint32_t tma_phase;
   // stencil items of this thread (orbital j, x offset a), at most 4
   int nit;
   int itj[4], ita[4];
@@ -213,14 +246,16 @@ __device__ void begin_spin(Ctx<T>& c, int s) {
   const Params& p = c.p;
   const int n = p.n;
   T* Bg = c.Bg + (size_t)s * n * n;
-  if (p.b_in_smem) {
+  const bool in_smem = c.bsm == 1 || (c.bsm == 0 && p.b_in_smem);
+  if (in_smem) {
     for (int r = c.warp; r < n; r += NWARP)
       for (int j = c.lane; j < n; j += 32) c.Bs[r * c.bs + j] = Bg[(size_t)r * n + j];
-    c.B = c.Bs;
-  } else {
-    c.B = Bg;
   }
-  if (p.update == 1) {
+  // a compile-time choice where possible, so accesses through c.B are shared-memory ones
+  if (c.bsm == 1) c.B = c.Bs;
+  else if (c.bsm == 2) c.B = Bg;
+  else c.B = in_smem ? c.Bs : Bg;
+  if (c.upd == 1) {
     const int ws = c.w * 2 + s;
     const int m = p.win_m[ws];
     const T* gV = (const T*)p.win_V + (size_t)ws * p.k * p.vs;
@@ -246,7 +281,7 @@ __device__ void end_spin(Ctx<T>& c, int s, bool store) {
     for (int r = c.warp; r < n; r += NWARP)
       for (int j = c.lane; j < n; j += 32) Bg[(size_t)r * n + j] = c.Bs[r * c.bs + j];
   }
-  if (p.update == 1) {
+  if (c.upd == 1) {
     const int ws = c.w * 2 + s;
     const int m = c.sc->m;
     T* gV = (T*)p.win_V + (size_t)ws * p.k * p.vs;
@@ -420,6 +455,30 @@ __device__ __forceinline__ void make_proposal(const Ctx<T>& c, int i, const T* F
   for (int k = 0; k < 3; ++k) pr.F[k] = p.drift ? F[k] : T(0);
   if constexpr (IsMixed<T>::value) {
     const uint32_t* qi = c.Rq + 3 * i;
+    if (!rgiven) {
+      // lanes 0-2 of every warp take one dimension each, then share it over the warp
+      const int k = c.lane < 3 ? c.lane : 0;
+      const float Fk = k == 0 ? pr.F[0] : (k == 1 ? pr.F[1] : pr.F[2]);
+      const float d = tau * Fk + stau * chi[k];
+      const float dw = d - c.k.L * rintf(d * c.k.invL);  // same point mod L, |dw| <= L/2
+      const uint32_t q = qi[k] + (uint32_t)__float2int_rn(dw * c.k.scale);
+      const unsigned long long prod = (unsigned long long)q * (unsigned long long)p.G;
+      const int cell = (int)(prod >> 32);
+      const float t = (float)(uint32_t)prod * 0x1p-32f;
+      const float x = d - tau * Fk;
+      const unsigned full = 0xffffffffu;
+#pragma unroll
+      for (int kk = 0; kk < 3; ++kk) {
+        pr.disp[kk] = __shfl_sync(full, d, kk);
+        pr.rq[kk] = __shfl_sync(full, q, kk);
+        pr.cell[kk] = __shfl_sync(full, cell, kk);
+        pr.t[kk] = __shfl_sync(full, t, kk);
+        const float xk = __shfl_sync(full, x, kk);
+        gf += xk * xk;
+      }
+      pr.logGf = -gf / (T(2) * tau);
+      return;
+    }
     for (int k = 0; k < 3; ++k) {
       uint32_t q;
       if (rgiven) {
@@ -467,14 +526,22 @@ __device__ __forceinline__ void make_proposal(const Ctx<T>& c, int i, const T* F
 // gets rhoD and dU; rho and Fp = grad log Psi(R') on every thread in the mixed path and
 // on thread 0 in the FP64 path.  phi' stays in shared memory.
 template <typename T>
-__device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, bool cached,
-                           Res<T>& rs) {
+__device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, bool cached,
+                           Res<T>& rs, Next<T>* nx = nullptr) {
   const Params& p = c.p;
   const int n = p.n, n_pad = p.n_pad, GP = p.GP;
   const T* table = (const T*)p.table;
   T cf[16];
-  if (c.nit > 0)
+  const bool tma = p.use_tma;
+  if (tma) {
+    if (c.tid == 0) {  // the whole 4x4x4 x n_pad stencil in one copy
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(c.bar, (uint32_t)p.stencil_bytes);
+      tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
+    }
+  } else if (c.nit > 0) {
     stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[0], c.ita[0], cf);
+  }
   T wreg[36];  // x, y, z weights (mixed path: computed by every thread)
   if constexpr (IsMixed<T>::value) {
     basis12(pr.t[1], wreg + 12);
@@ -512,6 +579,49 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   }
   for (int t = t0 + c.tid + JT * NT; t < t1; t += NT)
     if (t != i) term(t, false, T(0));
+  T w[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // next-electron partials
+  if (nx) {
+    // w[0..2] a, w[3..5] b, w[6] e, w[8..10] sj, w[11..13] dj
+    const int i1 = nx->i1;
+    nx->qi = -1;
+#pragma unroll
+    for (int q = 0; q < JT; ++q) {
+      const int t = t0 + c.tid + q * NT;
+      if (t < t1 && t != i1) {
+        const T* coef; int K; T hinv, rc;
+        functor(c, i1, t, coef, K, hinv, rc);
+        T d[3], r, rinv, u, du, d2u;
+        partner_disp(c, c.R + 3 * i1, c.Rq + 3 * i1, t, d, r, rinv);
+        radial(coef, K, hinv, rc, r, u, du, d2u);
+        T f = r > T(0) ? du * rinv : T(0);
+        w[8] += f * d[0];
+        w[9] += f * d[1];
+        w[10] += f * d[2];
+        nx->uo[q] = u;
+        if (t == i) {  // the moving electron at r'
+          T dn[3], rn, rninv, un, dun, d2n;
+          if constexpr (IsMixed<T>::value) {
+            disp_fx(c.Rq + 3 * i1, pr.rq, c.k.unit, dn);
+            const T r2 = dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2];
+            rninv = rsqrtf(r2);
+            rn = r2 * rninv;
+          } else {
+            disp_f64(c.R + 3 * i1, pr.rp, c.p.L, c.p.invL, dn);
+            rn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
+            rninv = T(1) / rn;
+          }
+          radial(coef, K, hinv, rc, rn, un, dun, d2n);
+          const T fn = rn > T(0) ? dun * rninv : T(0);
+          w[11] = fn * dn[0] - f * d[0];
+          w[12] = fn * dn[1] - f * d[1];
+          w[13] = fn * dn[2] - f * d[2];
+          nx->ui_old = u;
+          nx->ui_new = un;
+          nx->qi = q;
+        }
+      }
+    }
+  }
   const T* wts;
   if constexpr (IsMixed<T>::value) {
     wts = wreg;
@@ -519,11 +629,21 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     __syncthreads();  // weights in shared memory
     wts = c.sc->wts;
   }
+  bool ok = true;
+  if (tma) {
+    ok = mbar_wait_bounded(c.bar, c.tma_phase);
+    c.tma_phase ^= 1u;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     if (q < c.nit) {
-      if (q > 0)
+      if (tma) {
+        const T* sb = c.stc + (size_t)(c.ita[q] * 16) * n_pad + c.itj[q];
+#pragma unroll
+        for (int bc = 0; bc < 16; ++bc) cf[bc] = sb[(size_t)bc * n_pad];
+      } else if (q > 0) {
         stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[q], c.ita[q], cf);
+      }
       T o4[4];
       stencil_reduce(cf, wts, o4);
       const int j = c.itj[q], a = c.ita[q];
@@ -531,15 +651,30 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
       for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
     }
   }
-  for (int it = c.tid + 4 * NT; it < 4 * n; it += NT) {  // n > 256: items beyond four
+  for (int it = c.tid + 4 * NT; it < 4 * n; it += NT) {  // items beyond four per thread
     const int j = it % n, a = it / n;
-    stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], j, a, cf);
+    if (tma) {
+      const T* sb = c.stc + (size_t)(a * 16) * n_pad + j;
+      for (int bc = 0; bc < 16; ++bc) cf[bc] = sb[(size_t)bc * n_pad];
+    } else {
+      stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], j, a, cf);
+    }
     T o4[4];
     stencil_reduce(cf, wts, o4);
 #pragma unroll
     for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
   }
-  __syncthreads();
+  if (tma) {
+    // a stencil copy that never lands: record it, give the copy one more bounded wait,
+    // and leave the kernel (uniformly, every thread sees the vote)
+    if (__syncthreads_or(!ok)) {
+      if (c.tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      if (!ok) mbar_wait_bounded(c.bar, c.tma_phase ^ 1u);
+      return false;
+    }
+  } else {
+    __syncthreads();
+  }
   const T dinv = c.k.dgrid;
   for (int j = c.tid; j < n; j += NT) {
     T wx[12];
@@ -557,8 +692,37 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     v[1] += o5[1] * cj;
     v[2] += o5[2] * cj;
     v[3] += o5[3] * cj;
+    if (nx) {
+      const T bn = c.B[(size_t)nx->pp1 * c.bs + j];
+      // j == tid here (n <= NT on this path): the prefetched dA entries of i1
+      w[0] += nx->pf[0] * bn;
+      w[1] += nx->pf[1] * bn;
+      w[2] += nx->pf[2] * bn;
+      w[3] += nx->pf[0] * cj;
+      w[4] += nx->pf[1] * cj;
+      w[5] += nx->pf[2] * cj;
+      w[6] += o5[0] * bn;
+    }
   }
-  block_allreduce8(v, c.red1);
+  if (nx) {
+    T v24[24];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v24[q] = v[q];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v24[8 + q] = w[q];
+    block_allreduce24(v24, c.red1);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = v24[q];
+    for (int k = 0; k < 3; ++k) {
+      nx->a[k] = v24[8 + k];
+      nx->b[k] = v24[11 + k];
+      nx->sj[k] = v24[16 + k];
+      nx->dj[k] = v24[19 + k];
+    }
+    nx->e = v24[14];
+  } else {
+    block_allreduce8(v, c.red1);
+  }
   rs.rhoD = v[0];
   rs.dU = v[4];
   if constexpr (IsMixed<T>::value) {
@@ -569,6 +733,7 @@ __device__ void ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     rs.rho = v[0] * exp(-v[4]);
     for (int k = 0; k < 3; ++k) rs.Fp[k] = v[1 + k] / v[0] - v[5 + k];
   }
+  return true;
 }
 
 // Metropolis(-Hastings): A = rho^2 G(r<-r')/G(r'<-r) with drift, rho^2 without;
@@ -599,29 +764,79 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
   const Params& p = c.p;
   const int n = p.n, n_pad = p.n_pad, bs = c.bs;
   T* rw = c.rows + (size_t)i * 5 * n_pad;
-  if (p.update == 0) {
+  if (c.upd == 0) {
     // Sherman-Morrison: v_k = phi'.B^T[k] (one thread per row), then
     // B^T[k] -= col (v_k - delta_k,pp) / rhoD (one warp per row); f_k reuses `part`.
     const T invr = T(1) / rhoD;
     T* fk = c.part;
-    for (int k = c.tid; k < n; k += NT) {
-      const T* row = c.B + (size_t)k * bs;
-      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-      int j = 0;
-      for (; j + 4 <= n; j += 4) {
-        a0 += row[j] * c.phi[j];
-        a1 += row[j + 1] * c.phi[j + 1];
-        a2 += row[j + 2] * c.phi[j + 2];
-        a3 += row[j + 3] * c.phi[j + 3];
+    bool vec = false;
+    if constexpr (sizeof(T) == 4) vec = (n % 16 == 0) && (bs % 4 == 0) && (4 * n <= NT);
+    if (vec) {
+      // four threads per row, each a quarter of the row in float4 reads, two shuffles
+      if constexpr (sizeof(T) == 4) {
+        const int k = c.tid >> 2, qd = c.tid & 3, nq = n >> 2;  // nq floats per quarter
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (k < n) {
+          const float4* r4 = reinterpret_cast<const float4*>(c.B + (size_t)k * bs + qd * nq);
+          const float4* p4 = reinterpret_cast<const float4*>(c.phi + qd * nq);
+          for (int q = 0; q < nq / 4; ++q) {
+            const float4 b = r4[q], f = p4[q];
+            a0 += b.x * f.x;
+            a1 += b.y * f.y;
+            a2 += b.z * f.z;
+            a3 += b.w * f.w;
+          }
+        }
+        float acc = (a0 + a1) + (a2 + a3);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (k < n && qd == 0) fk[k] = (acc - (k == pp ? 1.f : 0.f)) * invr;
       }
-      for (; j < n; ++j) a0 += row[j] * c.phi[j];
-      fk[k] = ((a0 + a1) + (a2 + a3) - (k == pp ? T(1) : T(0))) * invr;
+    } else {
+      for (int k = c.tid; k < n; k += NT) {
+        const T* row = c.B + (size_t)k * bs;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int j = 0;
+        for (; j + 4 <= n; j += 4) {
+          a0 += row[j] * c.phi[j];
+          a1 += row[j + 1] * c.phi[j + 1];
+          a2 += row[j + 2] * c.phi[j + 2];
+          a3 += row[j + 3] * c.phi[j + 3];
+        }
+        for (; j < n; ++j) a0 += row[j] * c.phi[j];
+        fk[k] = ((a0 + a1) + (a2 + a3) - (k == pp ? T(1) : T(0))) * invr;
+      }
     }
     __syncthreads();
-    for (int k = c.warp; k < n; k += NWARP) {
-      const T f = fk[k];
-      T* row = c.B + (size_t)k * bs;
-      for (int j = c.lane; j < n; j += 32) row[j] -= c.col[j] * f;
+    // B^T[k][j] -= col[j] f_k: each warp takes rows warp, warp + NWARP, ...; four rows at a
+    // time with every load issued before the stores (the compiler cannot prove that the
+    // row, col and f pointers do not alias)
+    for (int k0 = c.warp; k0 < n; k0 += 4 * NWARP) {
+      T f[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = k0 + r * NWARP;
+        f[r] = k < n ? fk[k] : T(0);
+      }
+      for (int j0 = 0; j0 < n; j0 += 64) {
+        const int ja = j0 + c.lane, jb = j0 + 32 + c.lane;
+        const T ca = ja < n ? c.col[ja] : T(0), cb = jb < n ? c.col[jb] : T(0);
+        T va[4], vb[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int k = k0 + r * NWARP;
+          const T* row = c.B + (size_t)k * bs;
+          va[r] = (k < n && ja < n) ? row[ja] : T(0);
+          vb[r] = (k < n && jb < n) ? row[jb] : T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int k = k0 + r * NWARP;
+          T* row = c.B + (size_t)k * bs;
+          if (k < n && ja < n) row[ja] = va[r] - ca * f[r];
+          if (k < n && jb < n) row[jb] = vb[r] - cb * f[r];
+        }
+      }
     }
   } else {
     // Delayed: a row already in the window is applied first; then append p_m = pp,
@@ -685,7 +900,14 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
       if constexpr (IsMixed<T>::value) c.Rq[3 * i + k] = pr.rq[k];
       else c.R[3 * i + k] = pr.rp[k];
     }
-    c.sc->logdet[s] += (double)log(fabs(rhoD));
+    if constexpr (IsMixed<T>::value) {
+      const float y = logf(fabsf(rhoD)) - c.sc->lcomp[s];
+      const float t = c.sc->lsum[s] + y;
+      c.sc->lcomp[s] = (t - c.sc->lsum[s]) - y;
+      c.sc->lsum[s] = t;
+    } else {
+      c.sc->logdet[s] += log(fabs(rhoD));
+    }
     if (rhoD < T(0)) c.sc->sign[s] = -c.sc->sign[s];
   }
   __syncthreads();
@@ -736,17 +958,20 @@ __device__ double local_energy(Ctx<T>& c) {
       v[6] += rw[3 * n_pad + j] * b;
       v[7] += rw[4 * n_pad + j] * b;
     }
+    {
+      const T t8 = warp_sum8_transposed(v);  // lane 4q holds the total of value q
 #pragma unroll
-    for (int q = 0; q < 9; ++q) v[q] = warp_sum(v[q]);
+      for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t8, 4 * q);
+      v[8] = warp_sum(v[8]);
+    }
     if (c.lane == 0) {
-      double gd2 = 0.0, gg = 0.0;
+      T gd2 = 0, gg = 0;
       for (int k = 0; k < 3; ++k) {
-        const double gd = (double)v[4 + k];
-        gd2 += gd * gd;
-        const double g = gd - (double)v[k];
+        gd2 += v[4 + k] * v[4 + k];
+        const T g = v[4 + k] - v[k];
         gg += g * g;
       }
-      kin += -0.5 * (((double)v[7] - gd2) - (double)v[3] + gg);
+      kin += (double)(T(-0.5) * ((v[7] - gd2) - v[3] + gg));
       pot += (double)v[8];
     }
   }
@@ -779,8 +1004,9 @@ __device__ __forceinline__ void shared_proposal(Ctx<T>& c, int i, const T* F, co
   }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
+template <typename T, int MODE, int UPD, int BSM>
+__global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
+                                                     const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Lay lay = make_lay<T>(p);
   const int w = blockIdx.x;
@@ -791,7 +1017,9 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
   c.tid = threadIdx.x;
   c.lane = threadIdx.x & 31;
   c.warp = threadIdx.x >> 5;
-  c.bs = b_stride(p);
+  c.bs = b_stride<T>(p);
+  c.upd = UPD;
+  c.bsm = BSM;
   c.sc = (Scal<T>*)(smem + lay.scal);
   c.Bs = (T*)(smem + lay.B);
   c.Bg = (T*)p.binv + (size_t)w * 2 * n * n;
@@ -805,7 +1033,7 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
   c.part = (T*)(smem + lay.part);
   c.col = (T*)(smem + lay.col);
   c.dchi = (T*)(smem + lay.dchi);
-  c.du = (double*)(smem + lay.du);
+  c.du = (T*)(smem + lay.du);
   c.red0 = (T*)(smem + lay.red0);
   c.red1 = (T*)(smem + lay.red1);
   c.wP = (int*)(smem + lay.wP);
@@ -819,6 +1047,10 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
   c.xb = (T*)(smem + lay.xb);
   c.yb = (T*)(smem + lay.yb);
   c.rows = (T*)p.rows + (size_t)w * N * 5 * n_pad;
+  c.bar = (uint64_t*)(smem + lay.bar);
+  c.stc = (T*)((reinterpret_cast<uintptr_t>(smem + lay.stc) + 127) & ~(uintptr_t)127);
+  c.tmap = &tmap;
+  c.tma_phase = 0;
   c.nit = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -847,7 +1079,12 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
     sc->logdet[1] = p.logdet[w * 2 + 1];
     sc->sign[0] = p.sign[w * 2];
     sc->sign[1] = p.sign[w * 2 + 1];
+    sc->lsum[0] = sc->lsum[1] = sc->lcomp[0] = sc->lcomp[1] = 0.0f;
     sc->m = 0;
+    if (p.use_tma) {
+      mbar_init(c.bar, 1);
+      mbar_fence_init();
+    }
     sc->accept = 0;
   }
   __syncthreads();
@@ -866,33 +1103,49 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
   bool moved = false;
   if constexpr (MODE == MODE_SWEEP) {
     for (int e = c.tid; e < N; e += NT) {
-      double d4[4];
-      move_draws(p.seed, (uint32_t)w, p.gen, (uint32_t)e, d4);
-      c.dchi[3 * e] = (T)d4[0];
-      c.dchi[3 * e + 1] = (T)d4[1];
-      c.dchi[3 * e + 2] = (T)d4[2];
+      T d4[4];
+      draws_t<T>(p.seed, (uint32_t)w, p.gen, (uint32_t)e, d4);
+      c.dchi[3 * e] = d4[0];
+      c.dchi[3 * e + 1] = d4[1];
+      c.dchi[3 * e + 2] = d4[2];
       c.du[e] = d4[3];
     }
     T pf[3] = {0, 0, 0};
     if (pf_ok) prefetch_grad_rows(c, 0, pf);
     __syncthreads();
     unsigned long long nacc = 0;
+    // mixed Sherman-Morrison sweep with drift: the drift of electron i+1 is gathered
+    // during move i (Next), so a move needs no separate gradient pass
+    constexpr bool kPre = IsMixed<T>::value && UPD == 0;
+    const bool pre = kPre && p.drift && pf_ok && cache_ok;
     for (int s = 0; s < 2; ++s) {
       begin_spin(c, s);
+      bool have_F = false;
       for (int pp = 0; pp < n; ++pp) {
         const int i = s * p.n_up + pp;
         compute_column(c, pp);
-        if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
+        if (p.drift && !have_F) eval_grad(c, i, pf, pf_ok, uo, F);
         if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
         shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
-        ratio_grad(c, i, pr, uo, cache_ok, rs);
+        Next<T> nx;
+        const bool use_next = pre && pp + 1 < n;
+        bool fine;
+        if (use_next) {
+          nx.i1 = i + 1;
+          nx.pp1 = pp + 1;
+          nx.pf = pf;
+          fine = ratio_grad(c, i, pr, uo, cache_ok, rs, &nx);
+        } else {
+          fine = ratio_grad(c, i, pr, uo, cache_ok, rs);
+        }
+        if (!fine) return;  // uniform: a stencil copy timed out (status word set)
         int acc;
         if constexpr (IsMixed<T>::value) {
-          acc = metropolis(p, c.k, pr, rs, (T)c.du[i]);
+          acc = metropolis(p, c.k, pr, rs, c.du[i]);
         } else {
           if (c.tid == 0) {
             sc->rs = rs;
-            sc->accept = metropolis(p, c.k, pr, rs, (T)c.du[i]);
+            sc->accept = metropolis(p, c.k, pr, rs, c.du[i]);
           }
           __syncthreads();
           rs = sc->rs;
@@ -900,6 +1153,22 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
         }
         nacc += acc;
         if (acc) accept_update(c, i, s, pp, pr, rs.rhoD);
+        if constexpr (kPre) {
+          have_F = use_next;
+          if (use_next) {
+            const T f = acc ? nx.e / rs.rhoD : T(0);
+            for (int k = 0; k < 3; ++k)
+              F[k] = (nx.a[k] - f * nx.b[k]) - (nx.sj[k] + (acc ? nx.dj[k] : T(0)));
+#pragma unroll
+            for (int q = 0; q < JT; ++q) uo[q] = nx.uo[q];
+            if (nx.qi >= 0) {
+              const T ui = acc ? nx.ui_new : nx.ui_old;
+#pragma unroll
+              for (int q = 0; q < JT; ++q)
+                if (q == nx.qi) uo[q] = ui;
+            }
+          }
+        }
       }
       flush_window(c);
       end_spin(c, s, true);
@@ -926,14 +1195,14 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
     } else {
       T chi[3] = {0, 0, 0};
       if (!p.rnew_in) {
-        double d4[4];
-        move_draws(p.seed, (uint32_t)w, p.gen, (uint32_t)i, d4);
-        chi[0] = (T)d4[0];
-        chi[1] = (T)d4[1];
-        chi[2] = (T)d4[2];
+        T d4[4];
+        draws_t<T>(p.seed, (uint32_t)w, p.gen, (uint32_t)i, d4);
+        chi[0] = d4[0];
+        chi[1] = d4[1];
+        chi[2] = d4[2];
       }
       shared_proposal(c, i, F, chi, p.rnew_in ? p.rnew_in + 3 * w : nullptr, pr);
-      ratio_grad(c, i, pr, uo, cache_ok, rs);
+      if (!ratio_grad(c, i, pr, uo, cache_ok, rs)) return;
       T* pphi = (T*)p.pend_phi + (size_t)w * 5 * n_pad;
       for (int j = c.tid; j < n; j += NT)
         for (int q = 0; q < 5; ++q) pphi[q * n_pad + j] = c.phi[q * n_pad + j];
@@ -997,7 +1266,7 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
       if (p.accept_in) acc = p.accept_in[w] != 0;
       else
         acc = metropolis(p, c.k, pr, rs,
-                         (T)accept_uniform(p.seed, (uint32_t)w, p.gen, (uint32_t)i));
+                         accept_uniform_t<T>(p.seed, (uint32_t)w, p.gen, (uint32_t)i));
       sc->accept = acc;
       if (p.accept_out) p.accept_out[w] = (uint8_t)acc;
       pd[P_VALID] = 0.0;
@@ -1028,8 +1297,8 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p) {
       else Rw[e] = c.R[e];
     }
     if (c.tid == 0) {
-      p.logdet[w * 2] = sc->logdet[0];
-      p.logdet[w * 2 + 1] = sc->logdet[1];
+      p.logdet[w * 2] = sc->logdet[0] + (double)sc->lsum[0];
+      p.logdet[w * 2 + 1] = sc->logdet[1] + (double)sc->lsum[1];
       p.sign[w * 2] = sc->sign[0];
       p.sign[w * 2 + 1] = sc->sign[1];
     }
@@ -1043,37 +1312,59 @@ int max_smem_optin() {
   return v;
 }
 
-template <typename T, int MODE>
-static cudaError_t launch_mode(const Params& p, size_t bytes, cudaStream_t s) {
+template <typename T, int MODE, int UPD, int BSM>
+static cudaError_t launch_upd(const Params& p, size_t bytes, const CUtensorMap& tm,
+                              cudaStream_t s) {
   static size_t configured = 0;
   if (bytes > 48 * 1024 && configured < bytes) {
-    cudaError_t e = cudaFuncSetAttribute(move_kernel<T, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(move_kernel<T, MODE, UPD, BSM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     configured = bytes;
   }
-  move_kernel<T, MODE><<<p.W, NT, bytes, s>>>(p);
+  move_kernel<T, MODE, UPD, BSM><<<p.W, NT, bytes, s>>>(p, tm);
   return cudaGetLastError();
 }
 
+// The sweep is specialised on where the inverse lives; the fine-grained calls are not.
+template <typename T, int MODE>
+static cudaError_t launch_mode(const Params& p, size_t bytes, const CUtensorMap& tm,
+                               cudaStream_t s) {
+  if constexpr (MODE == MODE_SWEEP) {
+    if (p.update == 1)
+      return p.b_in_smem ? launch_upd<T, MODE, 1, 1>(p, bytes, tm, s)
+                         : launch_upd<T, MODE, 1, 2>(p, bytes, tm, s);
+    return p.b_in_smem ? launch_upd<T, MODE, 0, 1>(p, bytes, tm, s)
+                       : launch_upd<T, MODE, 0, 2>(p, bytes, tm, s);
+  } else {
+    return p.update == 1 ? launch_upd<T, MODE, 1, 0>(p, bytes, tm, s)
+                         : launch_upd<T, MODE, 0, 0>(p, bytes, tm, s);
+  }
+}
+
 template <typename T>
-cudaError_t launch_move(const Params& p_in, int mode, cudaStream_t s) {
+cudaError_t launch_move(const Params& p_in, int mode, const void* tmap, cudaStream_t s) {
   Params p = p_in;
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  if (p.use_tma && tmap) std::memcpy(&tm, tmap, sizeof(tm));
+  else p.use_tma = 0;
+  p.stencil_bytes = stencil_tma_bytes(p, (int)sizeof(T));
   const size_t bytes = make_lay<T>(p).total;
   p.skip_eloc = 0;
   switch (mode) {
-    case MODE_SWEEP: return launch_mode<T, MODE_SWEEP>(p, bytes, s);
-    case MODE_SWEEP_NOE: p.skip_eloc = 1; return launch_mode<T, MODE_SWEEP>(p, bytes, s);
-    case MODE_GRAD: return launch_mode<T, MODE_GRAD>(p, bytes, s);
-    case MODE_PROPOSE: return launch_mode<T, MODE_PROPOSE>(p, bytes, s);
-    case MODE_ACCEPT: return launch_mode<T, MODE_ACCEPT>(p, bytes, s);
-    case MODE_ELOC: return launch_mode<T, MODE_ELOC>(p, bytes, s);
-    case MODE_FLUSH: p.skip_eloc = 1; return launch_mode<T, MODE_ELOC>(p, bytes, s);
+    case MODE_SWEEP: return launch_mode<T, MODE_SWEEP>(p, bytes, tm, s);
+    case MODE_SWEEP_NOE: p.skip_eloc = 1; return launch_mode<T, MODE_SWEEP>(p, bytes, tm, s);
+    case MODE_GRAD: return launch_mode<T, MODE_GRAD>(p, bytes, tm, s);
+    case MODE_PROPOSE: return launch_mode<T, MODE_PROPOSE>(p, bytes, tm, s);
+    case MODE_ACCEPT: return launch_mode<T, MODE_ACCEPT>(p, bytes, tm, s);
+    case MODE_ELOC: return launch_mode<T, MODE_ELOC>(p, bytes, tm, s);
+    case MODE_FLUSH: p.skip_eloc = 1; return launch_mode<T, MODE_ELOC>(p, bytes, tm, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template cudaError_t launch_move<double>(const Params&, int, cudaStream_t);
-template cudaError_t launch_move<float>(const Params&, int, cudaStream_t);
+template cudaError_t launch_move<double>(const Params&, int, const void*, cudaStream_t);
+template cudaError_t launch_move<float>(const Params&, int, const void*, cudaStream_t);
 
 }  // namespace qmcgb

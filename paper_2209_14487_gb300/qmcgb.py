@@ -21,6 +21,7 @@ QMC_PREC_FP64, QMC_PREC_MIXED = 0, 1
 QMC_UPDATE_SM, QMC_UPDATE_DELAYED = 0, 1
 QMC_J1, QMC_J2_UU, QMC_J2_UD = 0, 1, 2
 QMC_DTYPE_F64, QMC_DTYPE_F32 = 0, 1
+QMC_STAGING_AUTO, QMC_STAGING_LDG = 0, 1
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA",
                 4: "QMC_ERR_SINGULAR", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_NAN",
                 7: "QMC_ERR_STATE", 8: "QMC_ERR_UNSUPPORTED"}
@@ -32,7 +33,7 @@ EXPORTS = [
     "qmc_propose_move_batch", "qmc_accept_reject_batch", "qmc_local_energy_batch", "qmc_sweep",
     "qmc_get_positions", "qmc_get_logpsi", "qmc_get_inverse", "qmc_get_slater_matrix",
     "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
-    "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc",
+    "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
 ]
 
 
@@ -44,7 +45,7 @@ class qmc_system_desc(C.Structure):
 class qmc_run_desc(C.Structure):
     _fields_ = [("n_walkers", C.c_int), ("precision", C.c_int), ("update", C.c_int),
                 ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("drift", C.c_int),
-                ("potential", C.c_int), ("reserved", C.c_int), ("tau", C.c_double),
+                ("potential", C.c_int), ("staging", C.c_int), ("tau", C.c_double),
                 ("seed", C.c_uint64)]
 
 
@@ -86,6 +87,7 @@ def _load():
         "qmc_get_generation": [vp, C.POINTER(C.c_uint32)],
         "qmc_set_generation": [vp, C.c_uint32],
         "qmc_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
+        "qmc_get_kernel_config": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -140,7 +142,7 @@ class Crowd:
 
     def __init__(self, n_up, n_dn, n_orb, n_ions, grid, L, n_walkers, tau, precision="fp64",
                  update="sm", delay_rank=1, n_recompute=0, drift=True, potential=True,
-                 seed=14487, stream=None):
+                 seed=14487, stream=None, staging="auto"):
         self.sys = qmc_system_desc(n_up=n_up, n_dn=n_dn, n_orb=n_orb, n_ions=n_ions, grid=grid,
                                    reserved=0, L=L)
         self.run = qmc_run_desc(
@@ -148,7 +150,8 @@ class Crowd:
             precision=QMC_PREC_MIXED if precision == "mixed" else QMC_PREC_FP64,
             update=QMC_UPDATE_DELAYED if update == "delayed" else QMC_UPDATE_SM,
             delay_rank=delay_rank, n_recompute=n_recompute, drift=int(drift),
-            potential=int(potential), reserved=0, tau=tau, seed=seed)
+            potential=int(potential), staging=QMC_STAGING_LDG if staging == "ldg" else QMC_STAGING_AUTO,
+            tau=tau, seed=seed)
         self.W, self.N, self.n = n_walkers, n_up + n_dn, n_up
         h = C.c_void_p()
         _check("qmc_crowd_create",
@@ -157,12 +160,13 @@ class Crowd:
 
     @classmethod
     def from_workload(cls, wl, precision="fp64", update="sm", delay_rank=1, n_walkers=None,
-                      stream=None, n_recompute=None):
+                      stream=None, n_recompute=None, staging="auto"):
         c = cls(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L,
                 wl.n_walkers if n_walkers is None else n_walkers, wl.tau, precision=precision,
                 update=update, delay_rank=delay_rank,
                 n_recompute=wl.n_recompute if n_recompute is None else n_recompute,
-                drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream)
+                drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream,
+                staging=staging)
         if wl.n_ions:
             c.qmc_load_ions(np.ascontiguousarray(wl.ions, dtype=np.float64))
         if wl.j2_uu is not None:
@@ -276,6 +280,14 @@ class Crowd:
         v = C.c_ulonglong()
         _check("qmc_get_launch_count", lib.qmc_get_launch_count(self.h, C.byref(v)))
         return v.value
+
+    @property
+    def kernel_config(self) -> dict:
+        """{'b_in_smem', 'stencil_tma', 'smem_bytes'} of this crowd's move kernel."""
+        b, t, m = C.c_int(), C.c_int(), C.c_int()
+        _check("qmc_get_kernel_config",
+               lib.qmc_get_kernel_config(self.h, C.byref(b), C.byref(t), C.byref(m)))
+        return {"b_in_smem": b.value, "stencil_tma": t.value, "smem_bytes": m.value}
 
     def qmc_crowd_save(self) -> bytes:
         sz = C.c_size_t()
