@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "electron moves/sec over crowd, FP32-mixed vs FP64 GPU, at stated energy error"
 UNIT = "electron-moves/s"
-KERNEL_SRC = os.path.join(ROOT, "paper_2209_14487_gb300", "csrc", "qmc_move.cu")
+CSRC = os.path.join(ROOT, "paper_2209_14487_gb300", "csrc")
 
 
 def bytes_per_move(n, N, s, p_acc, update, k):
@@ -46,9 +46,9 @@ def bytes_per_move(n, N, s, p_acc, update, k):
 
 def source_sha() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.dirname(KERNEL_SRC))):
+    for f in sorted(os.listdir(CSRC)):
         if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(os.path.dirname(KERNEL_SRC), f), "rb").read())
+            h.update(open(os.path.join(CSRC, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -70,6 +70,7 @@ typedef struct qmc_system_desc {
 
 /* How the crowd is driven. */
 enum { QMC_STAGING_AUTO = 0, QMC_STAGING_LDG = 1 };
+enum { QMC_ENGINE_AUTO = 0, QMC_ENGINE_SIMT = 1 };
 
 typedef struct qmc_run_desc {
   int n_walkers;    /* W >= 1                                                         */
@@ -85,6 +86,11 @@ typedef struct qmc_run_desc {
                      * QMC_STAGING_LDG: the stencil is read with per-thread loads      */
   double tau;       /* time step                                                      */
   uint64_t seed;    /* Philox key: (low 32 bits, walker ^ high 32 bits)               */
+  int cta_threads;  /* threads per walker CTA of the move kernel: 128, 256, or 0 for  *
+                     * the library's choice (128 up to 128 electrons per spin)         */
+  int engine;       /* QMC_ENGINE_AUTO (0): in the mixed path with the delayed update   *
+                     * and the inverse in global memory, windows are flushed on the    *
+                     * tensor cores (tcgen05, 3xTF32); QMC_ENGINE_SIMT: CUDA cores     */
 } qmc_run_desc;
 
 /* Per-call statistics of qmc_sweep, accumulated in FP64 over walkers and generations. */
@@ -170,10 +176,12 @@ int qmc_set_generation(qmc_crowd* crowd, uint32_t gen);
 int qmc_get_launch_count(qmc_crowd* crowd, unsigned long long* count);
 /* The move kernel's configuration, chosen at creation from the shared memory a CTA may
  * use: 1 in *b_in_smem when the moving spin's inverse is staged in shared memory, 1 in
- * *stencil_tma when each move's orbital stencil arrives by TMA, and the kernel's dynamic
- * shared memory in bytes.  Any output pointer may be NULL.  Errors: INVALID_ARG. */
+ * *stencil_tma when each move's orbital stencil arrives by TMA, the kernel's dynamic
+ * shared memory in bytes, its threads per CTA, and 1 in *tc_flush when delayed windows
+ * are flushed on the tensor cores.  Any output pointer may be NULL.
+ * Errors: INVALID_ARG. */
 int qmc_get_kernel_config(const qmc_crowd* crowd, int* b_in_smem, int* stencil_tma,
-                          int* smem_bytes);
+                          int* smem_bytes, int* cta_threads, int* tc_flush);
 
 /* Checkpoint: positions, generation and RNG seed.  With buf == NULL, *size receives the
  * byte count; otherwise *size must hold at least that many bytes.  Restoring recomputes
@@ -182,6 +190,8 @@ int qmc_crowd_save(qmc_crowd* crowd, void* buf, size_t* size);
 int qmc_crowd_restore(qmc_crowd* crowd, const void* buf, size_t size);
 
 const char* qmc_status_string(int status);
+/* Text of the CUDA error behind the calling thread's last QMC_ERR_CUDA ("no error" if none). */
+const char* qmc_last_cuda_error(void);
 
 /* Allocation-free FP64 inverse of a batch of dense matrices.  The paper has no
  * counterpart: this call exists for callers that must not allocate device memory when

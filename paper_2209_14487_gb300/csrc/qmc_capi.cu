@@ -14,6 +14,32 @@
 
 using qmcgb::Params;
 
+namespace qmcgb {
+
+int stencil_tma_bytes(const Params& p, int elem_bytes) { return 64 * p.n_pad * elem_bytes; }
+
+size_t move_smem_bytes(const Params& p, int elem_bytes) {
+  return p.nt == 128 ? nt128::move_smem_bytes(p, elem_bytes) : nt256::move_smem_bytes(p, elem_bytes);
+}
+
+template <typename T>
+cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s) {
+  return p.nt == 128 ? nt128::launch_move<T>(p, mode, tmap, s) : nt256::launch_move<T>(p, mode, tmap, s);
+}
+
+int sweep_ctas_per_sm(const Params& p) {
+  return p.nt == 128 ? nt128::sweep_ctas_per_sm(p) : nt256::sweep_ctas_per_sm(p);
+}
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+}  // namespace qmcgb
+
 struct qmc_crowd {
   qmc_system_desc sys;
   qmc_run_desc run;
@@ -50,16 +76,24 @@ struct qmc_crowd {
   bool has_orbitals = false, has_positions = false, stale = true;
   uint32_t gen = 0;
   unsigned long long launches = 0;
-  alignas(64) CUtensorMap tmap;  // the padded table as a 4-D tensor, for the stencil copy
+  CUtensorMap tmap;  // (128-byte aligned type) the padded table as a 4-D tensor, for the stencil copy
   size_t smem = 0;               // dynamic shared memory of the move kernel
 };
 
 namespace {
 
-#define CK(call)                                 \
-  do {                                           \
-    cudaError_t e_ = (call);                     \
-    if (e_ != cudaSuccess) return QMC_ERR_CUDA;  \
+// The last CUDA error a call of this thread returned as QMC_ERR_CUDA.
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda = e;
+  return QMC_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_);   \
   } while (0)
 
 bool is_mixed(const qmc_crowd* c) { return c->run.precision == QMC_PREC_MIXED; }
@@ -118,7 +152,7 @@ void sync_params(qmc_crowd* c) {
 
 int launch_status(qmc_crowd* c, cudaError_t e) {
   ++c->launches;
-  return e == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+  return e == cudaSuccess ? QMC_OK : cuda_fail(e);
 }
 
 int move(qmc_crowd* c, int mode) {
@@ -227,6 +261,8 @@ int check_iel(const qmc_crowd* c, int iel) {
 
 extern "C" {
 
+const char* qmc_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
+
 const char* qmc_status_string(int status) {
   switch (status) {
     case QMC_OK: return "ok";
@@ -259,6 +295,9 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   if (run->n_recompute < 0) return QMC_ERR_INVALID_ARG;
   if (run->staging != QMC_STAGING_AUTO && run->staging != QMC_STAGING_LDG)
     return QMC_ERR_INVALID_ARG;
+  if (run->cta_threads != 0 && run->cta_threads != 128 && run->cta_threads != 256)
+    return QMC_ERR_INVALID_ARG;
+  if (run->engine != QMC_ENGINE_AUTO && run->engine != QMC_ENGINE_SIMT) return QMC_ERR_INVALID_ARG;
   if (sys->n_dn != sys->n_up) return QMC_ERR_UNSUPPORTED;
   if (sys->n_up > 1024 || sys->grid > 1024) return QMC_ERR_UNSUPPORTED;
 
@@ -282,6 +321,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.n_up = sys->n_up;
   p.n = n;
   p.n_pad = (n + 7) & ~7;
+  p.nt = run->cta_threads ? run->cta_threads : (n <= 128 ? 128 : 256);
   p.n_ions = sys->n_ions;
   p.G = sys->grid;
   p.GP = sys->grid + 3;
@@ -306,6 +346,10 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   // elements wide, so the staged stencil needs n_pad <= 256.
   const int optin = qmcgb::max_smem_optin();
   const bool tma_ok = run->staging == QMC_STAGING_AUTO && p.n_pad <= 256;
+  // The tensor-core flush (mixed delayed path, inverse in global memory, n % 4 == 0) adds
+  // a 64 KB operand stage unless it can share the stencil buffer.
+  const bool tc_ok = run->engine == QMC_ENGINE_AUTO && run->precision == QMC_PREC_MIXED &&
+                     run->update == QMC_UPDATE_DELAYED && n % 4 == 0;
   const int plans[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   size_t smem = 0;
   bool placed = false;
@@ -313,6 +357,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     if (pl[1] && !tma_ok) continue;
     p.b_in_smem = pl[0];
     p.use_tma = pl[1];
+    p.tc_flush = (tc_ok && !pl[0]) ? 1 : 0;
     p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
     smem = qmcgb::move_smem_bytes(p, es);
     if (optin <= 0 || smem <= (size_t)optin) {
@@ -320,9 +365,31 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
       break;
     }
   }
+  if (!placed && tc_ok) {  // without the tensor-core stage
+    for (const auto& pl : plans) {
+      if (pl[0] || (pl[1] && !tma_ok)) continue;
+      p.b_in_smem = 0;
+      p.use_tma = pl[1];
+      p.tc_flush = 0;
+      p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
+      smem = qmcgb::move_smem_bytes(p, es);
+      if (optin <= 0 || smem <= (size_t)optin) {
+        placed = true;
+        break;
+      }
+    }
+  }
   if (!placed) {
     delete c;
     return QMC_ERR_UNSUPPORTED;
+  }
+  // TMEM: every resident CTA of the sweep holds 128 of the SM's 512 columns
+  if (p.tc_flush) {
+    const int per_sm = qmcgb::sweep_ctas_per_sm(p);
+    if (per_sm < 1 || per_sm > 4) {
+      p.tc_flush = 0;
+      smem = qmcgb::move_smem_bytes(p, es);
+    }
   }
   c->smem = smem;
 
@@ -441,7 +508,8 @@ int qmc_load_orbitals(qmc_crowd* c, const void* coefs, int dtype, int mem) {
   ++c->launches;
   cudaError_t e2 = cudaStreamSynchronize(c->stream);
   if (tmp) cudaFree(tmp);
-  if (e != cudaSuccess || e2 != cudaSuccess) return QMC_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (e2 != cudaSuccess) return cuda_fail(e2);
   c->has_orbitals = true;
   c->stale = true;
   return QMC_OK;
@@ -735,8 +803,11 @@ int qmc_set_generation(qmc_crowd* c, uint32_t gen) {
   return QMC_OK;
 }
 
-int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, int* smem_bytes) {
+int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, int* smem_bytes,
+                          int* cta_threads, int* tc_flush) {
   if (!c) return QMC_ERR_INVALID_ARG;
+  if (tc_flush) *tc_flush = c->p.tc_flush;
+  if (cta_threads) *cta_threads = c->p.nt;
   if (b_in_smem) *b_in_smem = c->p.b_in_smem;
   if (stencil_tma) *stencil_tma = c->p.use_tma;
   if (smem_bytes) *smem_bytes = (int)c->smem;

@@ -223,9 +223,9 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
-// Sums V values over the CTA; thread 0 receives the totals in v.  `red` holds
-// NWARP * V values; the caller syncs before `red` is reused.
-template <int V, typename R>
+// Sums V values over a CTA of NW warps; thread 0 receives the totals in v.  `red` holds
+// NW * V values; the caller syncs before `red` is reused.
+template <int NW, int V, typename R>
 __device__ __forceinline__ void block_sum_to0(R* v, R* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ __forceinline__ void block_sum_to0(R* v, R* red) {
 #pragma unroll
     for (int q = 0; q < V; ++q) {
       R acc = red[q];
-      for (int wi = 1; wi < NWARP; ++wi) acc += red[wi * V + q];
+      for (int wi = 1; wi < NW; ++wi) acc += red[wi * V + q];
       v[q] = acc;
     }
   }
@@ -271,9 +271,10 @@ __device__ __forceinline__ R warp_sum8_transposed(const R* v) {
   return c;
 }
 
-// Sums eight values over the CTA and hands every thread all eight totals (one barrier).
-// `red` holds NWARP * 8 values and must not be rewritten before every warp has read it.
-template <typename R>
+// Sums eight values over a CTA of NW warps and hands every thread all eight totals (one
+// barrier).  `red` holds NW * 8 values and must not be rewritten before every warp has
+// read it.
+template <int NW, typename R>
 __device__ __forceinline__ void block_allreduce8(R* v, R* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const R c = warp_sum8_transposed(v);
@@ -282,30 +283,10 @@ __device__ __forceinline__ void block_allreduce8(R* v, R* red) {
   R t = R(0);
   if (lane < 8) {
 #pragma unroll
-    for (int w = 0; w < NWARP; ++w) t += red[w * 8 + lane];
+    for (int w = 0; w < NW; ++w) t += red[w * 8 + lane];
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
-}
-
-// Twenty-four values summed over the CTA (three transposed warp sums, one barrier); every
-// thread receives all totals.  `red` holds NWARP * 24 values.
-template <typename R>
-__device__ __forceinline__ void block_allreduce24(R* v, R* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int g = 0; g < 3; ++g) {
-    const R c = warp_sum8_transposed(v + 8 * g);
-    if ((lane & 3) == 0) red[warp * 24 + 8 * g + (lane >> 2)] = c;
-  }
-  __syncthreads();
-  R t = R(0);
-  if (lane < 24) {
-#pragma unroll
-    for (int w = 0; w < NWARP; ++w) t += red[w * 24 + lane];
-  }
-#pragma unroll
-  for (int q = 0; q < 24; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -374,6 +355,99 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (global_ns() - t0 > 1000000000ull) return false;
   }
   return false;
+}
+
+// ---------------------------------------------------------------------------------------
+// tcgen05 (fifth-generation tensor core) helpers: TMEM allocation, the kind::tf32 MMA with
+// both operands in shared memory and the accumulator in TMEM, completion through an
+// mbarrier, and TMEM loads for the epilogue.  All cta_group::1 (one SM per tile).
+// ---------------------------------------------------------------------------------------
+
+// Allocates `ncols` TMEM columns (a power of two, 32..512) for the CTA; the base address
+// is written to *dst.  Executed by one whole warp.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+// Frees a TMEM allocation; by the warp that allocated it.
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling: core matrices of
+// 8 rows x 16 bytes stored as 128 contiguous bytes, `lbo` bytes apart along K and `sbo`
+// bytes apart along M (or N).  Bits 46-48 hold the descriptor version (0b001).
+__device__ __forceinline__ uint64_t tc_smem_desc(const void* base, uint32_t lbo, uint32_t sbo) {
+  const uint32_t a = smem_addr(base);
+  return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::tf32 with FP32 accumulation, both operands K-major,
+// dense, M = 128 and N (a multiple of 16, 16..256).
+__device__ __forceinline__ uint32_t tc_idesc_tf32(uint32_t n_cols) {
+  return (1u << 4)              // D format: F32
+         | (2u << 7)            // A format: TF32
+         | (2u << 10)           // B format: TF32
+         | ((n_cols >> 3) << 17)  // N / 8
+         | ((128u >> 4) << 24);   // M / 16
+}
+
+// D[tmem] (+)= A[smem] . B[smem]^T for one K-step of 8 TF32 elements; one thread issues.
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// One arrival on `bar` once every MMA this thread issued before has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (lane = warp quadrant base +
+// lane id, encoded in taddr's upper half); waits for the load before returning.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// x = hi + lo with hi, lo TF32 (round to nearest): the split of the 3xTF32 products
+// A.B ~ Ahi.Bhi + Ahi.Blo + Alo.Bhi, which keep FP32 accuracy on the TF32 pipe.
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+  lo = __uint_as_float(l);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -7,11 +7,8 @@
 
 namespace qmcgb {
 
-#ifndef QMCGB_NT
-#define QMCGB_NT 256
-#endif
-constexpr int NT = QMCGB_NT;       // threads per CTA of the walker kernels
-constexpr int NWARP = NT / 32;
+constexpr int LA_NT = 256;         // threads per CTA of the row, LU and Jastrow kernels
+constexpr int LA_NWARP = LA_NT / 32;
 constexpr int MAX_K = 64;          // largest delay rank
 constexpr int MAX_KNOTS = 64;      // largest radial functor (free coefficients)
 constexpr int PEND_STRIDE = 24;    // doubles of pending-proposal state per walker
@@ -43,7 +40,9 @@ struct Params {
   int K2, K1;               // free radial coefficients (0 = term absent)
   int b_in_smem;            // inverse of the moving spin staged in shared memory
   int skip_eloc;            // sweep without the local energy (a recompute comes first)
+  int nt;                   // threads per CTA of the move kernel: 128 or 256
   int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
+  int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
   int stencil_bytes;        // bytes of that copy
   int vs, ks;               // padded strides of the window's V rows and S^-1 rows
   uint32_t gen;
@@ -80,11 +79,23 @@ struct Params {
 
 size_t move_smem_bytes(const Params& p, int elem_bytes);
 int max_smem_optin();
+int sweep_ctas_per_sm(const Params& p);
 
 // tmap: host copy of the table's CUtensorMap (128 bytes), or null when p.use_tma == 0.
+// The move kernel is compiled once per CTA width (p.nt); these dispatch on it.
 template <typename T>
 cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s);
 int stencil_tma_bytes(const Params& p, int elem_bytes);
+#define QMCGB_DECLARE_MOVE_WIDTH(NS)                                                      \
+  namespace NS {                                                                        \
+  template <typename T>                                                                 \
+  cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s); \
+  size_t move_smem_bytes(const Params& p, int elem_bytes);                              \
+  int sweep_ctas_per_sm(const Params& p);                                               \
+  }
+QMCGB_DECLARE_MOVE_WIDTH(nt128)
+QMCGB_DECLARE_MOVE_WIDTH(nt256)
+#undef QMCGB_DECLARE_MOVE_WIDTH
 template <typename T>
 cudaError_t launch_eval_rows(const Params& p, cudaStream_t s);
 template <typename T>

@@ -10,7 +10,7 @@ namespace qmcgb {
 
 // One CTA per (walker, electron): phi, grad phi, lap phi of the occupied orbitals at r_i.
 template <typename T>
-__global__ void __launch_bounds__(NT) eval_rows_kernel(const Params p) {
+__global__ void __launch_bounds__(LA_NT) eval_rows_kernel(const Params p) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* part = (T*)smem;  // [16][n_pad]
   __shared__ T wts[48];
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(NT) eval_rows_kernel(const Params p) {
   if (threadIdx.x < 3) basis12(tt[threadIdx.x], wts + 12 * threadIdx.x);
   __syncthreads();
   const T* table = (const T*)p.table;
-  for (int it = threadIdx.x; it < 4 * n; it += NT) {
+  for (int it = threadIdx.x; it < 4 * n; it += LA_NT) {
     T cf[16], o4[4];
     stencil_load(table, p.GP, n_pad, cell[0], cell[1], cell[2], it % n, it / n, cf);
     stencil_reduce(cf, wts, o4);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(NT) eval_rows_kernel(const Params p) {
   }
   __syncthreads();
   T* rw = (T*)p.rows + ((size_t)w * p.N + i) * 5 * n_pad;
-  for (int j = threadIdx.x; j < n; j += NT) {
+  for (int j = threadIdx.x; j < n; j += LA_NT) {
     T o5[5];
     stencil_combine(part, n_pad, j, wts, (T)p.dgrid, o5);
     for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = o5[q];
@@ -59,11 +59,11 @@ __global__ void __launch_bounds__(NT) eval_rows_kernel(const Params p) {
 // crowd's precision, log|det A_s| and its sign, and empties the delayed window.
 // `ws` is scratch: 2 n^2 doubles per (walker, spin).
 template <typename T>
-__global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* ws) {
+__global__ void __launch_bounds__(LA_NT) recompute_kernel(const Params p, double* ws) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* piv = (int*)smem;  // [n]
-  __shared__ double red_v[NWARP];
-  __shared__ int red_i[NWARP];
+  __shared__ double red_v[LA_NWARP];
+  __shared__ int red_i[LA_NWARP];
   __shared__ int s_piv, s_sing, s_sign;
   __shared__ double s_logabs;
   const int ws_id = blockIdx.x, w = ws_id / 2, s = ws_id - 2 * w;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
   double* LU = ws + (size_t)ws_id * 2 * n * n;
   double* X = LU + (size_t)n * n;
   const T* rows = (const T*)p.rows + (size_t)w * p.N * 5 * n_pad;
-  for (int e = tid; e < n * n; e += NT) {
+  for (int e = tid; e < n * n; e += LA_NT) {
     const int l = e / n, j = e - l * n;
     LU[e] = (double)rows[((size_t)(s * p.n_up + l)) * 5 * n_pad + j];
   }
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
   for (int k = 0; k < n; ++k) {
     double best = -1.0;
     int bi = k;
-    for (int i = k + tid; i < n; i += NT) {
+    for (int i = k + tid; i < n; i += LA_NT) {
       const double v = fabs(LU[(size_t)i * n + k]);
       if (v > best) { best = v; bi = i; }
     }
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
     if (tid == 0) {
       double b = red_v[0];
       int ib = red_i[0];
-      for (int q = 1; q < NWARP; ++q)
+      for (int q = 1; q < LA_NWARP; ++q)
         if (red_v[q] > b || (red_v[q] == b && red_i[q] < ib)) { b = red_v[q]; ib = red_i[q]; }
       piv[k] = ib;
       s_piv = ib;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
     if (s_sing) break;
     const int pk = s_piv;
     if (pk != k) {
-      for (int j = tid; j < n; j += NT) {
+      for (int j = tid; j < n; j += LA_NT) {
         const double t = LU[(size_t)k * n + j];
         LU[(size_t)k * n + j] = LU[(size_t)pk * n + j];
         LU[(size_t)pk * n + j] = t;
@@ -119,10 +119,10 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
       if (akk < 0.0) s_sign = -s_sign;
       s_logabs += log(fabs(akk));
     }
-    for (int i = k + 1 + tid; i < n; i += NT) LU[(size_t)i * n + k] /= akk;
+    for (int i = k + 1 + tid; i < n; i += LA_NT) LU[(size_t)i * n + k] /= akk;
     __syncthreads();
     const int m = n - k - 1;
-    for (int e = tid; e < m * m; e += NT) {
+    for (int e = tid; e < m * m; e += LA_NT) {
       const int i = k + 1 + e / m, j = k + 1 + (e - (e / m) * m);
       LU[(size_t)i * n + j] -= LU[(size_t)i * n + k] * LU[(size_t)k * n + j];
     }
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
     }
     return;
   }
-  for (int col = tid; col < n; col += NT) {
+  for (int col = tid; col < n; col += LA_NT) {
     for (int i = 0; i < n; ++i) X[(size_t)i * n + col] = (i == col) ? 1.0 : 0.0;
     for (int k = 0; k < n; ++k) {
       const int pk = piv[k];
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(NT) recompute_kernel(const Params p, double* w
   }
   __syncthreads();
   T* Bg = (T*)p.binv + ((size_t)w * 2 + s) * n * n;
-  for (int e = tid; e < n * n; e += NT) {
+  for (int e = tid; e < n * n; e += LA_NT) {
     const int k = e / n, i = e - k * n;  // B^T[k][i] = (A^-1)[i][k]
     Bg[e] = (T)X[(size_t)i * n + k];
   }
@@ -194,14 +194,14 @@ __global__ void pad_table_kernel(const Params p, const void* src, int src_f32, i
 
 // U(R) per walker in FP64 accumulation (for log|Psi| queries).
 template <typename T>
-__global__ void __launch_bounds__(NT) jastrow_U_kernel(const Params p, double* U) {
-  __shared__ double red[NWARP];
+__global__ void __launch_bounds__(LA_NT) jastrow_U_kernel(const Params p, double* U) {
+  __shared__ double red[LA_NWARP];
   const int w = blockIdx.x, N = p.N, NI = p.n_ions;
   const double* R = p.R + (size_t)w * N * 3;
   const T* jc = (const T*)p.jc;
   double acc = 0.0;
   if (p.K2 > 0) {
-    for (int q = threadIdx.x; q < N * N; q += NT) {
+    for (int q = threadIdx.x; q < N * N; q += LA_NT) {
       const int i = q / N, j = q - i * N;
       if (j <= i) continue;
       double d[3];
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NT) jastrow_U_kernel(const Params p, double* U
     }
   }
   if (p.K1 > 0) {
-    for (int q = threadIdx.x; q < N * NI; q += NT) {
+    for (int q = threadIdx.x; q < N * NI; q += LA_NT) {
       const int i = q / NI, I = q - i * NI;
       double d[3];
       disp_f64(R + 3 * i, p.ions + 3 * I, p.L, p.invL, d);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NT) jastrow_U_kernel(const Params p, double* U
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < NWARP; ++q) t += red[q];
+    for (int q = 0; q < LA_NWARP; ++q) t += red[q];
     U[w] = t;
   }
 }
@@ -249,13 +249,13 @@ cudaError_t launch_eval_rows(const Params& p, cudaStream_t s) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
-  eval_rows_kernel<T><<<p.W * p.N, NT, bytes, s>>>(p);
+  eval_rows_kernel<T><<<p.W * p.N, LA_NT, bytes, s>>>(p);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s) {
-  recompute_kernel<T><<<p.W * 2, NT, (size_t)p.n * sizeof(int), s>>>(p, ws);
+  recompute_kernel<T><<<p.W * 2, LA_NT, (size_t)p.n * sizeof(int), s>>>(p, ws);
   return cudaGetLastError();
 }
 
@@ -268,7 +268,7 @@ cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int 
 
 template <typename T>
 cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s) {
-  jastrow_U_kernel<T><<<p.W, NT, 0, s>>>(p, U);
+  jastrow_U_kernel<T><<<p.W, LA_NT, 0, s>>>(p, U);
   return cudaGetLastError();
 }
 

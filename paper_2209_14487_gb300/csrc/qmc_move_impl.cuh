@@ -13,6 +13,14 @@
 // evaluates the (cheap, deterministic) proposal and acceptance itself after each block
 // reduction, so the move needs three barriers plus one per accepted move; the FP64 path,
 // where GB300's FP64 rate makes redundant scalar work expensive, lets thread 0 do it.
+//
+// This file is the kernel's implementation, compiled once per CTA width: a translation
+// unit defines QMCGB_MOVE_NT (threads per CTA) and QMCGB_MOVE_NS (the namespace of that
+// width) and includes it.  Narrow CTAs suit small determinants: a move is a chain of short
+// block reductions, and fewer warps make each barrier and each reduction cheaper.
+#ifndef QMCGB_MOVE_NT
+#error "define QMCGB_MOVE_NT and QMCGB_MOVE_NS before including qmc_move_impl.cuh"
+#endif
 #include <cuda.h>
 
 #include <cmath>
@@ -22,8 +30,17 @@
 #include "qmc_internal.h"
 
 namespace qmcgb {
+namespace QMCGB_MOVE_NS {
 
-constexpr int JT = 4;  // Jastrow partner terms cached per thread (N + N_ions <= JT * NT)
+constexpr int NT = QMCGB_MOVE_NT;  // threads per CTA
+constexpr int NWARP = NT / 32;
+constexpr int JT = 4;
+// Tensor-core flush: operand tiles of 128 rows x 32 K-elements, FP32 split into TF32 hi and
+// lo parts; A and B operand stages of 32 KB each.
+constexpr int TC_TILE = 128;
+constexpr int TC_KC = 32;
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE * TC_KC * 4;
+constexpr uint32_t TC_COLS = 128;  // TMEM columns a CTA allocates  // Jastrow partner terms cached per thread (N + N_ions <= JT * NT)
 
 // Per-move proposal state (registers of every thread in the mixed path; in the FP64 path
 // thread 0 builds it in shared memory and the others copy it).
@@ -41,20 +58,6 @@ struct Res {
   T rhoD, dU, rho, Fp[3];
 };
 
-// Drift of the next electron i1 (same spin, row pp1) gathered during the current move:
-// Jastrow gradient over all partners but the moving electron i (sj) plus the difference
-// of i's term between r'_i and r_i (dj), and a = dA_i1 . B[:,pp1], b = dA_i1 . col,
-// e = phi' . B[:,pp1], so that after an accept the determinant part is a - (e / rhoD) b.
-template <typename T>
-struct Next {
-  int i1, pp1;
-  const T* pf;           // this thread's dA row entries of i1 (orbital j = tid)
-  T a[3], b[3], e, sj[3], dj[3];
-  T uo[4];               // u(r_i1, r_t) of this thread's partner terms (t != i)
-  T ui_old, ui_new;      // the term with partner i, before and after the move
-  int qi;                // which of this thread's terms is partner i (-1: none)
-};
-
 template <typename T>
 struct Scal {
   Prop<T> pr;
@@ -63,6 +66,7 @@ struct Scal {
   float lsum[2], lcomp[2];  // mixed path: Kahan sums of log|rhoD| since the kernel began
   int sign[2];
   int accept, m;
+  uint32_t tmem;  // TMEM base address of the tensor-core flush
   T wts[48];
 };
 
@@ -92,7 +96,7 @@ __device__ __forceinline__ Cst<T> make_cst(const Params& p) {
 }
 
 struct Lay {
-  size_t scal, bar, stc, B, R, Rq, ion, ionq, jc, phi, part, col, dchi, du, red0, red1;
+  size_t scal, bar, stc, tcs, B, R, Rq, ion, ionq, jc, phi, part, col, dchi, du, red0, red1;
   size_t wP, wV, wS, wy, wz, wc, wb, snap, xb, yb, total;
 };
 
@@ -113,6 +117,13 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.scal = o; o += al16(sizeof(Scal<T>));
   L.bar = o; o += 16;
   L.stc = o; o += p.use_tma ? al16((size_t)p.stencil_bytes + 128) : 0;  // +128: alignment slack
+  // tensor-core flush staging: shares the stencil buffer (unused during a flush) when that
+  // is large enough
+  L.tcs = L.stc;
+  if (p.tc_flush && !(p.use_tma && p.stencil_bytes >= TC_STAGE_BYTES)) {
+    L.tcs = o;
+    o += al16((size_t)TC_STAGE_BYTES + 128);
+  }
   L.B = o; o += al16(p.b_in_smem ? (size_t)p.n * b_stride<T>(p) * es : 0);
   L.R = o; o += al16((size_t)p.N * 3 * 8);
   L.Rq = o; o += al16((size_t)p.N * 3 * 4);
@@ -124,8 +135,8 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.col = o; o += al16((size_t)p.n_pad * es);
   L.dchi = o; o += al16((size_t)p.N * 3 * es);
   L.du = o; o += al16((size_t)p.N * es);
-  L.red0 = o; o += al16((size_t)NWARP * 24 * 8);
-  L.red1 = o; o += al16((size_t)NWARP * 24 * 8);
+  L.red0 = o; o += al16((size_t)NWARP * 8 * 8);  // eight values per warp, FP64 at most
+  L.red1 = o; o += al16((size_t)NWARP * 8 * 8);
   L.wP = L.wV = L.wS = L.wy = L.wz = L.wc = L.wb = L.snap = L.xb = L.yb = o;
   if (p.update == 1) {
     L.wP = o; o += al16((size_t)MAX_K * 4);
@@ -142,8 +153,6 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.total = o;
   return L;
 }
-
-int stencil_tma_bytes(const Params& p, int elem_bytes) { return 64 * p.n_pad * elem_bytes; }
 
 size_t move_smem_bytes(const Params& p, int elem_bytes) {
   return elem_bytes == 4 ? make_lay<float>(p).total : make_lay<double>(p).total;
@@ -185,9 +194,13 @@ struct Ctx {
   T* yb;
   T* rows;  // this walker's global orbital rows [N][5][n_pad]
   T* stc;   // TMA-staged stencil [4][4][4][n_pad] (x, y, z, orbital)
-  uint64_t* bar;
+  uint64_t* bar;      // [0] stencil copies, [1] tensor-core MMA completion
   const void* tmap;
   uint32_t tma_phase;
+  uint32_t mma_phase;
+  float* tcs;         // tensor-core staging: A hi, A lo, B hi, B lo (128 x 32 each)
+  bool tc;            // windows flushed on the tensor cores (TMEM held by this CTA)
+  bool failed;        // a bounded wait ran out (status set); the sweep stops
   // stencil items of this thread (orbital j, x offset a), at most 4
   int nit;
   int itj[4], ita[4];
@@ -339,7 +352,7 @@ __device__ void compute_column(Ctx<T>& c, int pp) {
 // B <- B - (B P) S^-1 (V B); in B^T form B^T[k] -= sum_b Y[k][b] B^T[p_b] with
 // X[k][l] = B^T[k].Phi_l - delta(k, p_l) and Y = X S^-T.
 template <typename T>
-__device__ void flush_window(Ctx<T>& c) {
+__device__ void flush_window_simt(Ctx<T>& c) {
   const Params& p = c.p;
   const int m = c.sc->m;
   if (m == 0) return;
@@ -383,6 +396,231 @@ __device__ void flush_window(Ctx<T>& c) {
   __syncthreads();
   if (c.tid == 0) c.sc->m = 0;
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------
+// The flush on the tensor cores (mixed path, inverse in global memory).  The two products
+// of the flush, X = B^T Phi^T and B^T -= Y snap, run as tcgen05 kind::tf32 MMAs of 128-row
+// tiles with FP32 operands split into TF32 hi + lo parts (3 MMAs per K-step: hi.hi,
+// hi.lo, lo.hi), accumulated in FP32 in TMEM; the small m x m product Y = X S^-T stays on
+// the CUDA cores.  Operand tiles are staged through shared memory in the K-major layout
+// without swizzling: the float4 slot e of a 128 x 32 tile (row 8 (e >> 6) + (e & 7),
+// K-group (e >> 3) & 7) sits at byte 16 e, so core matrices are 128 B apart along K and
+// 1024 B apart along the rows.
+// ---------------------------------------------------------------------------------------
+
+// Slot e of a stage: its row and first K index (within the tile).
+__device__ __forceinline__ void tc_slot(int e, int& r, int& kk) {
+  r = ((e >> 6) << 3) + (e & 7);
+  kk = ((e >> 3) & 7) << 2;
+}
+
+__device__ __forceinline__ void tc_store_split(float* hi, float* lo, int e, float4 v) {
+  float4 h, l;
+  tf32_split(v.x, h.x, l.x);
+  tf32_split(v.y, h.y, l.y);
+  tf32_split(v.z, h.z, l.z);
+  tf32_split(v.w, h.w, l.w);
+  reinterpret_cast<float4*>(hi)[e] = h;
+  reinterpret_cast<float4*>(lo)[e] = l;
+}
+
+// Issues the 3xTF32 MMAs of one staged chunk (ksteps K-steps of 8) into TMEM column base d
+// and commits them to the MMA mbarrier; thread 0 only.
+__device__ __forceinline__ void tc_issue_chunk(const float* st, uint32_t d, uint32_t idesc,
+                                               int ksteps, bool first, uint64_t* bar) {
+  tc_fence_after_sync();
+  const float* ahi = st;
+  const float* alo = st + TC_TILE * TC_KC;
+  const float* bhi = st + 2 * TC_TILE * TC_KC;
+  const float* blo = st + 3 * TC_TILE * TC_KC;
+  for (int s = 0; s < ksteps; ++s) {
+    const int off = s * 64;  // two core matrices (8 K-elements) per step
+    const uint64_t a_h = tc_smem_desc(ahi + off, 128, 1024);
+    const uint64_t a_l = tc_smem_desc(alo + off, 128, 1024);
+    const uint64_t b_h = tc_smem_desc(bhi + off, 128, 1024);
+    const uint64_t b_l = tc_smem_desc(blo + off, 128, 1024);
+    tc_mma_tf32(d, a_h, b_h, idesc, (first && s == 0) ? 0u : 1u);
+    tc_mma_tf32(d, a_h, b_l, idesc, 1u);
+    tc_mma_tf32(d, a_l, b_h, idesc, 1u);
+  }
+  tc_commit(bar);
+}
+
+// Waits for the chunk's MMAs (bounded); on a timeout every thread learns of it, the status
+// word records it, and the copies get one more bounded wait.  False on timeout.
+template <typename T>
+__device__ bool tc_wait(Ctx<T>& c) {
+  const bool ok = mbar_wait_bounded(c.bar + 1, c.mma_phase);
+  c.mma_phase ^= 1u;
+  if (__syncthreads_or(!ok)) {
+    if (c.tid == 0) atomicOr(c.p.status, ST_TIMEOUT);
+    if (!ok) mbar_wait_bounded(c.bar + 1, c.mma_phase ^ 1u);
+    c.failed = true;
+    return false;
+  }
+  return true;
+}
+
+// Global rows of B^T for a stage: slots e = tid, tid + NT, ... (1024 slots per 128 x 32).
+constexpr int TC_SLOTS = TC_TILE * TC_KC / 4;
+constexpr int TC_PER_T = TC_SLOTS / NT;
+
+template <typename T>
+__device__ __forceinline__ void tc_load_bt(const Ctx<T>& c, int r0, int k0, float4* v) {
+  const int n = c.p.n;
+#pragma unroll
+  for (int q = 0; q < TC_PER_T; ++q) {
+    int r, kk;
+    tc_slot(c.tid + q * NT, r, kk);
+    r += r0;
+    kk += k0;
+    v[q] = (r < n && kk < n)
+               ? __ldcg(reinterpret_cast<const float4*>(c.B + (size_t)r * c.bs + kk))
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <typename T>
+__device__ void flush_window_tc(Ctx<T>& c) {
+  if constexpr (IsMixed<T>::value) {
+    const Params& p = c.p;
+    const int m = c.sc->m;
+    if (m == 0) return;
+    const int n = p.n, bs = c.bs;
+    const int mp = (m + 15) & ~15;  // N of the first product, K of the second
+    const uint32_t tm = c.sc->tmem;
+    const uint32_t lane_base = (uint32_t)((c.warp & 3) * 32) << 16;
+    float* st = c.tcs;
+    float* ahi = st;
+    float* alo = st + TC_TILE * TC_KC;
+    float* bhi = st + 2 * TC_TILE * TC_KC;
+    float* blo = st + 3 * TC_TILE * TC_KC;
+    // snapshot of the window's rows of B^T before the update
+    for (int l = c.warp; l < m; l += NWARP)
+      for (int j = c.lane; j < n; j += 32) c.snap[l * n + j] = c.B[(size_t)c.wP[l] * bs + j];
+    // ---- X = B^T Phi^T - P (per 128-row tile, K = n in chunks of 32)
+    const uint32_t id1 = tc_idesc_tf32((uint32_t)mp);
+    for (int r0 = 0; r0 < n; r0 += TC_TILE) {
+      float4 v[TC_PER_T];
+      tc_load_bt(c, r0, 0, v);
+      for (int k0 = 0; k0 < n; k0 += TC_KC) {
+#pragma unroll
+        for (int q = 0; q < TC_PER_T; ++q) tc_store_split(ahi, alo, c.tid + q * NT, v[q]);
+        for (int e = c.tid; e < mp * 8; e += NT) {  // Phi rows l < m, zero rows up to mp
+          int l, kk;
+          tc_slot(e, l, kk);
+          kk += k0;
+          float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (l < m) {
+            const T* vr = c.wV + (size_t)l * p.vs;
+            f.x = kk < n ? vr[kk] : 0.f;
+            f.y = kk + 1 < n ? vr[kk + 1] : 0.f;
+            f.z = kk + 2 < n ? vr[kk + 2] : 0.f;
+            f.w = kk + 3 < n ? vr[kk + 3] : 0.f;
+          }
+          tc_store_split(bhi, blo, e, f);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (c.tid == 0) tc_issue_chunk(st, tm, id1, TC_KC / 8, k0 == 0, c.bar + 1);
+        if (k0 + TC_KC < n) tc_load_bt(c, r0, k0 + TC_KC, v);  // in flight during the MMAs
+        if (!tc_wait(c)) return;
+      }
+      tc_fence_after_sync();
+      // epilogue: row r of the tile is TMEM lane r; warps of one lane quadrant split columns
+      const int r = r0 + (c.warp & 3) * 32 + c.lane;
+      for (int c0 = (c.warp >> 2) * 16; c0 < mp; c0 += (NWARP / 4) * 16) {
+        float x[16];
+        tmem_ld16(tm + lane_base + (uint32_t)c0, x);
+        if (r < n) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int l = c0 + q;
+            if (l < m) c.xb[(size_t)r * m + l] = x[q] - (r == c.wP[l] ? 1.f : 0.f);
+          }
+        }
+      }
+      tc_fence_before_sync();
+      __syncthreads();
+    }
+    // ---- Y = X S^-T (m x m on the CUDA cores)
+    for (int e = c.tid; e < n * m; e += NT) {
+      const int k = e / m, b = e - k * m;
+      const T* srow = c.wS + (size_t)b * p.ks;
+      const T* xrow = c.xb + (size_t)k * m;
+      T acc = 0;
+      for (int l = 0; l < m; ++l) acc += xrow[l] * srow[l];
+      c.yb[e] = acc;
+    }
+    __syncthreads();
+    // ---- B^T -= Y snap (per 128 x 128 output tile, K = mp in chunks of 32)
+    const uint32_t id2 = tc_idesc_tf32((uint32_t)TC_TILE);
+    for (int r0 = 0; r0 < n; r0 += TC_TILE) {
+      for (int j0 = 0; j0 < n; j0 += TC_TILE) {
+        for (int b0 = 0; b0 < mp; b0 += TC_KC) {
+          for (int e = c.tid; e < TC_SLOTS; e += NT) {
+            int r, kk;
+            tc_slot(e, r, kk);
+            const int k = r0 + r, b = b0 + kk;
+            float4 y = make_float4(0.f, 0.f, 0.f, 0.f), z = y;
+            if (k < n) {
+              const T* yr = c.yb + (size_t)k * m;
+              y.x = b < m ? yr[b] : 0.f;
+              y.y = b + 1 < m ? yr[b + 1] : 0.f;
+              y.z = b + 2 < m ? yr[b + 2] : 0.f;
+              y.w = b + 3 < m ? yr[b + 3] : 0.f;
+            }
+            const int j = j0 + r;  // the B operand's rows are output columns j
+            if (j < n) {
+              z.x = b < m ? c.snap[(size_t)b * n + j] : 0.f;
+              z.y = b + 1 < m ? c.snap[(size_t)(b + 1) * n + j] : 0.f;
+              z.z = b + 2 < m ? c.snap[(size_t)(b + 2) * n + j] : 0.f;
+              z.w = b + 3 < m ? c.snap[(size_t)(b + 3) * n + j] : 0.f;
+            }
+            tc_store_split(ahi, alo, e, y);
+            tc_store_split(bhi, blo, e, z);
+          }
+          fence_proxy_async_smem();
+          __syncthreads();
+          const int ks = (mp - b0 < TC_KC ? mp - b0 : TC_KC) / 8;
+          if (c.tid == 0) tc_issue_chunk(st, tm, id2, ks, b0 == 0, c.bar + 1);
+          if (!tc_wait(c)) return;
+        }
+        tc_fence_after_sync();
+        const int r = r0 + (c.warp & 3) * 32 + c.lane;
+        for (int c0 = (c.warp >> 2) * 16; c0 < TC_TILE; c0 += (NWARP / 4) * 16) {
+          float d[16];
+          tmem_ld16(tm + lane_base + (uint32_t)c0, d);
+          const int j = j0 + c0;
+          if (r < n && j < n) {  // n % 4 == 0: whole float4 groups in or out
+            float4* brow = reinterpret_cast<float4*>(c.B + (size_t)r * bs + j);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (j + 4 * q < n) {
+                float4 b = brow[q];
+                b.x -= d[4 * q];
+                b.y -= d[4 * q + 1];
+                b.z -= d[4 * q + 2];
+                b.w -= d[4 * q + 3];
+                brow[q] = b;
+              }
+            }
+          }
+        }
+        tc_fence_before_sync();
+        __syncthreads();
+      }
+    }
+    if (c.tid == 0) c.sc->m = 0;
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void flush_window(Ctx<T>& c) {
+  if (c.tc) flush_window_tc(c);
+  else flush_window_simt(c);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -440,7 +678,7 @@ __device__ void eval_grad(Ctx<T>& c, int i, const T* pf, bool use_pf, T* uo, T* 
     T dummy;
     if (t != i) term(t, dummy);
   }
-  block_allreduce8(v, c.red0);
+  block_allreduce8<NWARP>(v, c.red0);
   for (int k = 0; k < 3; ++k) F[k] = v[k] - v[3 + k];
 }
 
@@ -527,7 +765,7 @@ __device__ __forceinline__ void make_proposal(const Ctx<T>& c, int i, const T* F
 // on thread 0 in the FP64 path.  phi' stays in shared memory.
 template <typename T>
 __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, bool cached,
-                           Res<T>& rs, Next<T>* nx = nullptr) {
+                           Res<T>& rs) {
   const Params& p = c.p;
   const int n = p.n, n_pad = p.n_pad, GP = p.GP;
   const T* table = (const T*)p.table;
@@ -579,49 +817,6 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   }
   for (int t = t0 + c.tid + JT * NT; t < t1; t += NT)
     if (t != i) term(t, false, T(0));
-  T w[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // next-electron partials
-  if (nx) {
-    // w[0..2] a, w[3..5] b, w[6] e, w[8..10] sj, w[11..13] dj
-    const int i1 = nx->i1;
-    nx->qi = -1;
-#pragma unroll
-    for (int q = 0; q < JT; ++q) {
-      const int t = t0 + c.tid + q * NT;
-      if (t < t1 && t != i1) {
-        const T* coef; int K; T hinv, rc;
-        functor(c, i1, t, coef, K, hinv, rc);
-        T d[3], r, rinv, u, du, d2u;
-        partner_disp(c, c.R + 3 * i1, c.Rq + 3 * i1, t, d, r, rinv);
-        radial(coef, K, hinv, rc, r, u, du, d2u);
-        T f = r > T(0) ? du * rinv : T(0);
-        w[8] += f * d[0];
-        w[9] += f * d[1];
-        w[10] += f * d[2];
-        nx->uo[q] = u;
-        if (t == i) {  // the moving electron at r'
-          T dn[3], rn, rninv, un, dun, d2n;
-          if constexpr (IsMixed<T>::value) {
-            disp_fx(c.Rq + 3 * i1, pr.rq, c.k.unit, dn);
-            const T r2 = dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2];
-            rninv = rsqrtf(r2);
-            rn = r2 * rninv;
-          } else {
-            disp_f64(c.R + 3 * i1, pr.rp, c.p.L, c.p.invL, dn);
-            rn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
-            rninv = T(1) / rn;
-          }
-          radial(coef, K, hinv, rc, rn, un, dun, d2n);
-          const T fn = rn > T(0) ? dun * rninv : T(0);
-          w[11] = fn * dn[0] - f * d[0];
-          w[12] = fn * dn[1] - f * d[1];
-          w[13] = fn * dn[2] - f * d[2];
-          nx->ui_old = u;
-          nx->ui_new = un;
-          nx->qi = q;
-        }
-      }
-    }
-  }
   const T* wts;
   if constexpr (IsMixed<T>::value) {
     wts = wreg;
@@ -692,37 +887,8 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     v[1] += o5[1] * cj;
     v[2] += o5[2] * cj;
     v[3] += o5[3] * cj;
-    if (nx) {
-      const T bn = c.B[(size_t)nx->pp1 * c.bs + j];
-      // j == tid here (n <= NT on this path): the prefetched dA entries of i1
-      w[0] += nx->pf[0] * bn;
-      w[1] += nx->pf[1] * bn;
-      w[2] += nx->pf[2] * bn;
-      w[3] += nx->pf[0] * cj;
-      w[4] += nx->pf[1] * cj;
-      w[5] += nx->pf[2] * cj;
-      w[6] += o5[0] * bn;
-    }
   }
-  if (nx) {
-    T v24[24];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v24[q] = v[q];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v24[8 + q] = w[q];
-    block_allreduce24(v24, c.red1);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = v24[q];
-    for (int k = 0; k < 3; ++k) {
-      nx->a[k] = v24[8 + k];
-      nx->b[k] = v24[11 + k];
-      nx->sj[k] = v24[16 + k];
-      nx->dj[k] = v24[19 + k];
-    }
-    nx->e = v24[14];
-  } else {
-    block_allreduce8(v, c.red1);
-  }
+  block_allreduce8<NWARP>(v, c.red1);
   rs.rhoD = v[0];
   rs.dU = v[4];
   if constexpr (IsMixed<T>::value) {
@@ -976,7 +1142,7 @@ __device__ double local_energy(Ctx<T>& c) {
     }
   }
   double v2[2] = {kin, pot};
-  block_sum_to0<2>(v2, (double*)c.red0);
+  block_sum_to0<NWARP, 2>(v2, (double*)c.red0);
   return v2[0] + v2[1];  // meaningful on thread 0
 }
 
@@ -1051,6 +1217,10 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
   c.stc = (T*)((reinterpret_cast<uintptr_t>(smem + lay.stc) + 127) & ~(uintptr_t)127);
   c.tmap = &tmap;
   c.tma_phase = 0;
+  c.mma_phase = 0;
+  c.tcs = (float*)((reinterpret_cast<uintptr_t>(smem + lay.tcs) + 127) & ~(uintptr_t)127);
+  c.tc = false;
+  c.failed = false;
   c.nit = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -1081,13 +1251,21 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
     sc->sign[1] = p.sign[w * 2 + 1];
     sc->lsum[0] = sc->lsum[1] = sc->lcomp[0] = sc->lcomp[1] = 0.0f;
     sc->m = 0;
-    if (p.use_tma) {
+    if (p.use_tma || p.tc_flush) {
       mbar_init(c.bar, 1);
+      mbar_init(c.bar + 1, 1);
       mbar_fence_init();
     }
     sc->accept = 0;
   }
+  // the tensor-core flush holds TC_COLS columns of TMEM for the whole sweep
+  if constexpr (IsMixed<T>::value && UPD == 1 && BSM == 2 && MODE == MODE_SWEEP) {
+    c.tc = p.tc_flush != 0;
+    if (c.tc && c.warp == 0) tmem_alloc(&sc->tmem, TC_COLS);
+  }
+  tc_fence_before_sync();
   __syncthreads();
+  tc_fence_after_sync();
 
   int t0, t1;
   term_range(p, t0, t1);
@@ -1114,31 +1292,19 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
     if (pf_ok) prefetch_grad_rows(c, 0, pf);
     __syncthreads();
     unsigned long long nacc = 0;
-    // mixed Sherman-Morrison sweep with drift: the drift of electron i+1 is gathered
-    // during move i (Next), so a move needs no separate gradient pass
-    constexpr bool kPre = IsMixed<T>::value && UPD == 0;
-    const bool pre = kPre && p.drift && pf_ok && cache_ok;
     for (int s = 0; s < 2; ++s) {
       begin_spin(c, s);
-      bool have_F = false;
       for (int pp = 0; pp < n; ++pp) {
         const int i = s * p.n_up + pp;
         compute_column(c, pp);
-        if (p.drift && !have_F) eval_grad(c, i, pf, pf_ok, uo, F);
+        if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
         if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
         shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
-        Next<T> nx;
-        const bool use_next = pre && pp + 1 < n;
-        bool fine;
-        if (use_next) {
-          nx.i1 = i + 1;
-          nx.pp1 = pp + 1;
-          nx.pf = pf;
-          fine = ratio_grad(c, i, pr, uo, cache_ok, rs, &nx);
-        } else {
-          fine = ratio_grad(c, i, pr, uo, cache_ok, rs);
+        // false only when a stencil copy timed out (status set; uniform over the CTA)
+        if (!ratio_grad(c, i, pr, uo, cache_ok, rs)) {
+          c.failed = true;
+          break;
         }
-        if (!fine) return;  // uniform: a stencil copy timed out (status word set)
         int acc;
         if constexpr (IsMixed<T>::value) {
           acc = metropolis(p, c.k, pr, rs, c.du[i]);
@@ -1153,26 +1319,19 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
         }
         nacc += acc;
         if (acc) accept_update(c, i, s, pp, pr, rs.rhoD);
-        if constexpr (kPre) {
-          have_F = use_next;
-          if (use_next) {
-            const T f = acc ? nx.e / rs.rhoD : T(0);
-            for (int k = 0; k < 3; ++k)
-              F[k] = (nx.a[k] - f * nx.b[k]) - (nx.sj[k] + (acc ? nx.dj[k] : T(0)));
-#pragma unroll
-            for (int q = 0; q < JT; ++q) uo[q] = nx.uo[q];
-            if (nx.qi >= 0) {
-              const T ui = acc ? nx.ui_new : nx.ui_old;
-#pragma unroll
-              for (int q = 0; q < JT; ++q)
-                if (q == nx.qi) uo[q] = ui;
-            }
-          }
-        }
+        if (c.failed) break;  // a tensor-core flush timed out
       }
+      if (c.failed) break;
       flush_window(c);
+      if (c.failed) break;
       end_spin(c, s, true);
     }
+    if (c.tc) {  // every MMA has completed (each chunk was waited for)
+      tc_fence_before_sync();
+      __syncthreads();
+      if (c.warp == 0) tmem_dealloc(sc->tmem, TC_COLS);
+    }
+    if (c.failed) return;
     moved = true;
     if (!p.skip_eloc) {
       const double e = local_energy(c);
@@ -1305,22 +1464,29 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
   }
 }
 
-int max_smem_optin() {
-  int dev = 0, v = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return v;
+// Lets a kernel instantiation use up to the device's opt-in shared memory per CTA (set
+// once per process and device; crowds of any size then launch it without resetting it).
+template <typename T, int MODE, int UPD, int BSM>
+static cudaError_t allow_max_smem() {
+  static int done_for = -1;  // one per kernel instantiation
+  auto kern = move_kernel<T, MODE, UPD, BSM>;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || done_for == dev) return e;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) done_for = dev;
+  return e;
 }
 
 template <typename T, int MODE, int UPD, int BSM>
 static cudaError_t launch_upd(const Params& p, size_t bytes, const CUtensorMap& tm,
                               cudaStream_t s) {
-  static size_t configured = 0;
-  if (bytes > 48 * 1024 && configured < bytes) {
-    cudaError_t e = cudaFuncSetAttribute(move_kernel<T, MODE, UPD, BSM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (bytes > 48 * 1024) {
+    const cudaError_t e = allow_max_smem<T, MODE, UPD, BSM>();
     if (e != cudaSuccess) return e;
-    configured = bytes;
   }
   move_kernel<T, MODE, UPD, BSM><<<p.W, NT, bytes, s>>>(p, tm);
   return cudaGetLastError();
@@ -1364,7 +1530,27 @@ cudaError_t launch_move(const Params& p_in, int mode, const void* tmap, cudaStre
   }
 }
 
+// Resident CTAs per SM of the mixed delayed sweep with the inverse in global memory (the
+// kernel that may hold TMEM), at the crowd's dynamic shared memory.
+int sweep_ctas_per_sm(const Params& p_in) {
+  Params p = p_in;
+  p.stencil_bytes = 64 * p.n_pad * 4;
+  const size_t bytes = make_lay<float>(p).total;
+  auto kern = move_kernel<float, MODE_SWEEP, 1, 2>;
+  if (allow_max_smem<float, MODE_SWEEP, 1, 2>() != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int nb = -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return nb;
+}
+
 template cudaError_t launch_move<double>(const Params&, int, const void*, cudaStream_t);
 template cudaError_t launch_move<float>(const Params&, int, const void*, cudaStream_t);
 
+}  // namespace QMCGB_MOVE_NS
 }  // namespace qmcgb

@@ -1,0 +1,4 @@
+// The particle-by-particle move kernel for CTAs of 256 threads (qmc_move_impl.cuh).
+#define QMCGB_MOVE_NT 256
+#define QMCGB_MOVE_NS nt256
+#include "qmc_move_impl.cuh"

@@ -22,6 +22,7 @@ QMC_UPDATE_SM, QMC_UPDATE_DELAYED = 0, 1
 QMC_J1, QMC_J2_UU, QMC_J2_UD = 0, 1, 2
 QMC_DTYPE_F64, QMC_DTYPE_F32 = 0, 1
 QMC_STAGING_AUTO, QMC_STAGING_LDG = 0, 1
+QMC_ENGINE_AUTO, QMC_ENGINE_SIMT = 0, 1
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA",
                 4: "QMC_ERR_SINGULAR", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_NAN",
                 7: "QMC_ERR_STATE", 8: "QMC_ERR_UNSUPPORTED"}
@@ -34,6 +35,7 @@ EXPORTS = [
     "qmc_get_positions", "qmc_get_logpsi", "qmc_get_inverse", "qmc_get_slater_matrix",
     "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
+    "qmc_last_cuda_error",
 ]
 
 
@@ -46,7 +48,7 @@ class qmc_run_desc(C.Structure):
     _fields_ = [("n_walkers", C.c_int), ("precision", C.c_int), ("update", C.c_int),
                 ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("drift", C.c_int),
                 ("potential", C.c_int), ("staging", C.c_int), ("tau", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("cta_threads", C.c_int), ("engine", C.c_int)]
 
 
 class qmc_stats(C.Structure):
@@ -55,8 +57,9 @@ class qmc_stats(C.Structure):
 
 
 class QmcError(RuntimeError):
-    def __init__(self, fn: str, status: int):
-        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}")
+    def __init__(self, fn: str, status: int, detail: str = ""):
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}"
+                         + (f" ({detail})" if detail else ""))
         self.status = status
 
 
@@ -87,7 +90,7 @@ def _load():
         "qmc_get_generation": [vp, C.POINTER(C.c_uint32)],
         "qmc_set_generation": [vp, C.c_uint32],
         "qmc_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
-        "qmc_get_kernel_config": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "qmc_get_kernel_config": [vp] + [C.POINTER(C.c_int)] * 5,
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -97,6 +100,8 @@ def _load():
         f.restype = C.c_int
     lib.qmc_inverse_noalloc.argtypes = [vp, i, i, vp, vp, vp, vp]
     lib.qmc_inverse_noalloc.restype = C.c_int
+    lib.qmc_last_cuda_error.argtypes = []
+    lib.qmc_last_cuda_error.restype = C.c_char_p
     lib.qmc_status_string.argtypes = [C.c_int]
     lib.qmc_status_string.restype = C.c_char_p
     return lib
@@ -107,7 +112,8 @@ lib = _load()
 
 def _check(fn: str, st: int):
     if st != QMC_OK:
-        raise QmcError(fn, st)
+        detail = lib.qmc_last_cuda_error().decode() if st == 3 else ""
+        raise QmcError(fn, st, detail)
 
 
 def _buf(x, dtype=np.float64):
@@ -142,7 +148,7 @@ class Crowd:
 
     def __init__(self, n_up, n_dn, n_orb, n_ions, grid, L, n_walkers, tau, precision="fp64",
                  update="sm", delay_rank=1, n_recompute=0, drift=True, potential=True,
-                 seed=14487, stream=None, staging="auto"):
+                 seed=14487, stream=None, staging="auto", cta_threads=0, engine="auto"):
         self.sys = qmc_system_desc(n_up=n_up, n_dn=n_dn, n_orb=n_orb, n_ions=n_ions, grid=grid,
                                    reserved=0, L=L)
         self.run = qmc_run_desc(
@@ -151,7 +157,8 @@ class Crowd:
             update=QMC_UPDATE_DELAYED if update == "delayed" else QMC_UPDATE_SM,
             delay_rank=delay_rank, n_recompute=n_recompute, drift=int(drift),
             potential=int(potential), staging=QMC_STAGING_LDG if staging == "ldg" else QMC_STAGING_AUTO,
-            tau=tau, seed=seed)
+            tau=tau, seed=seed, cta_threads=cta_threads,
+            engine=QMC_ENGINE_SIMT if engine == "simt" else QMC_ENGINE_AUTO)
         self.W, self.N, self.n = n_walkers, n_up + n_dn, n_up
         h = C.c_void_p()
         _check("qmc_crowd_create",
@@ -160,13 +167,14 @@ class Crowd:
 
     @classmethod
     def from_workload(cls, wl, precision="fp64", update="sm", delay_rank=1, n_walkers=None,
-                      stream=None, n_recompute=None, staging="auto"):
+                      stream=None, n_recompute=None, staging="auto", cta_threads=0,
+                      engine="auto"):
         c = cls(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L,
                 wl.n_walkers if n_walkers is None else n_walkers, wl.tau, precision=precision,
                 update=update, delay_rank=delay_rank,
                 n_recompute=wl.n_recompute if n_recompute is None else n_recompute,
                 drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream,
-                staging=staging)
+                staging=staging, cta_threads=cta_threads, engine=engine)
         if wl.n_ions:
             c.qmc_load_ions(np.ascontiguousarray(wl.ions, dtype=np.float64))
         if wl.j2_uu is not None:
@@ -283,11 +291,13 @@ class Crowd:
 
     @property
     def kernel_config(self) -> dict:
-        """{'b_in_smem', 'stencil_tma', 'smem_bytes'} of this crowd's move kernel."""
-        b, t, m = C.c_int(), C.c_int(), C.c_int()
+        """{'b_in_smem', 'stencil_tma', 'smem_bytes', 'cta_threads', 'tc_flush'} of the
+        move kernel."""
+        v = [C.c_int() for _ in range(5)]
         _check("qmc_get_kernel_config",
-               lib.qmc_get_kernel_config(self.h, C.byref(b), C.byref(t), C.byref(m)))
-        return {"b_in_smem": b.value, "stencil_tma": t.value, "smem_bytes": m.value}
+               lib.qmc_get_kernel_config(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("b_in_smem", "stencil_tma", "smem_bytes", "cta_threads", "tc_flush"),
+                        (x.value for x in v)))
 
     def qmc_crowd_save(self) -> bytes:
         sz = C.c_size_t()

@@ -22,11 +22,13 @@ def Q():
     return qmcgb
 
 
-def _pair(Q, oracle_lib, wl, precision="fp64", update="sm", k=1, W=None, R=None):
+def _pair(Q, oracle_lib, wl, precision="fp64", update="sm", k=1, W=None, R=None, nt=0):
     W = wl.n_walkers if W is None else W
     R = wl.positions(n_walkers=W) if R is None else R
     gpu = Q.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
-                                n_walkers=W)
+                                n_walkers=W, cta_threads=nt)
+    if nt:
+        assert gpu.kernel_config["cta_threads"] == nt
     gpu.qmc_load_positions(np.ascontiguousarray(R))
     gpu.qmc_recompute()
     osys = oracle_lib.OracleSystem(wl)
@@ -45,11 +47,12 @@ def _ragged():
                                 n_ions=5, L=5.3, tau=0.4, j1_knots=7, j2_knots=9)
 
 
+@pytest.mark.parametrize("nt", [128, 256])
 @pytest.mark.parametrize("make", [wl_mod.pw16, _ragged])
-def test_fp64_propose_accept_sequence(Q, oracle_lib, make):
+def test_fp64_propose_accept_sequence(Q, oracle_lib, make, nt):
     wl = make()
     W = min(wl.n_walkers, 8)
-    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, W=W)
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, W=W, nt=nt)
     rng = np.random.default_rng(5)
     seq = [0, 1, 1, wl.n_up - 1, wl.n_up, wl.n_el - 1, 2, 0]
     for step, iel in enumerate(seq):
@@ -84,11 +87,11 @@ def test_fp64_propose_accept_sequence(Q, oracle_lib, make):
     assert np.all(_rel(e, orc.local_energy()) < 1e-10)
 
 
-@pytest.mark.parametrize("k", [1, 3, 4])
-def test_fp64_delayed_update_matches_oracle(Q, oracle_lib, k):
+@pytest.mark.parametrize("k,nt", [(1, 128), (3, 256), (4, 128)])
+def test_fp64_delayed_update_matches_oracle(Q, oracle_lib, k, nt):
     wl = _ragged()
     W = 5
-    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, update="delayed", k=k, W=W)
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, update="delayed", k=k, W=W, nt=nt)
     rng = np.random.default_rng(17)
     for iel in [3, 4, 3, 0, 12, 3, 13, 14, 20, 14, 1, 2, 4]:
         rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.5, size=(W, 3)), wl.L)
@@ -107,13 +110,14 @@ def test_fp64_delayed_update_matches_oracle(Q, oracle_lib, k):
             assert np.allclose(inv[w], orc.inverse(w, s), rtol=1e-9, atol=1e-10)
 
 
+@pytest.mark.parametrize("nt", [128, 256])
 @pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 4)])
-def test_fp64_sweep_trajectory_matches_oracle(Q, oracle_lib, update, k):
+def test_fp64_sweep_trajectory_matches_oracle(Q, oracle_lib, update, k, nt):
     """Internal counter-based RNG on both sides: identical proposals and decisions up to
     rounding (a decision flips only if u lands within rounding of the acceptance)."""
     wl = _ragged()
     W = 7
-    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, update=update, k=k, W=W)
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, update=update, k=k, W=W, nt=nt)
     n_gen = 3
     e_gpu = np.zeros((n_gen, W))
     st = gpu.qmc_sweep(n_gen, e_gpu)
@@ -235,9 +239,12 @@ def test_full_size_pw128_sampled_walkers(Q, oracle_lib):
         assert abs(e[-1, w] - e_ref) < 1e-9 * max(1, abs(e_ref))
 
 
-def test_full_size_pw128_mixed_sampled_walkers(Q, oracle_lib):
+@pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 16)])
+def test_full_size_pw128_mixed_sampled_walkers(Q, oracle_lib, update, k):
+    """Bench configuration in the mixed path: sampled walkers agree with the oracle's
+    FP64 recompute at the GPU's positions."""
     wl = wl_mod.pw128()
-    gpu = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=16)
+    gpu = Q.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k)
     gpu.qmc_load_positions(np.ascontiguousarray(wl.positions()))
     gpu.qmc_recompute()
     e = np.zeros((2, wl.n_walkers))
@@ -314,14 +321,15 @@ def test_checkpoint_restore_reproduces_trajectory(Q):
     assert np.allclose(a.qmc_get_positions(), b.qmc_get_positions(), atol=1e-12)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_pw512_inverse_in_global_memory(Q, oracle_lib, precision):
+@pytest.mark.parametrize("precision,nt", [("fp64", 256), ("mixed", 256), ("mixed", 128),
+                                          ("fp64", 128)])
+def test_pw512_inverse_in_global_memory(Q, oracle_lib, precision, nt):
     """n = 256 per spin: the 256 KB (FP32) inverse block does not fit in shared memory,
     so the kernel works on the global-memory inverse; 4 stencil items per thread and
     two Jastrow partner passes per thread."""
     wl = wl_mod.pw512()
     W = 3
-    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision=precision, W=W)
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision=precision, W=W, nt=nt)
     rng = np.random.default_rng(12)
     for iel in [0, 255, 256, 511, 17]:
         rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.4, size=(W, 3)), wl.L)
@@ -338,7 +346,7 @@ def test_pw512_inverse_in_global_memory(Q, oracle_lib, precision):
         # a whole generation without drift (r' = r + sqrt(tau) chi): nothing amplifies
         # rounding differences, so trajectories agree to rounding unless a decision flips
         wl.drift = False
-        gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision=precision, W=W)
+        gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision=precision, W=W, nt=nt)
         e = np.zeros((1, W))
         st = gpu.qmc_sweep(1, e)
         e_or, na = orc.sweep(1)
@@ -372,3 +380,46 @@ def test_tma_staged_stencil_matches_plain_loads(Q, make, precision, W):
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[1], b[1])
     assert np.array_equal(a[3], b[3])
+
+
+@pytest.mark.parametrize("nt", [256, 128])
+def test_tensor_core_flush_matches_simt_flush(Q, oracle_lib, nt):
+    """n = 256, inverse in global memory, delayed rank 16: windows flushed by tcgen05
+    3xTF32 MMAs give the same trajectories as the CUDA-core flush, an inverse as accurate
+    (max|A^-1 A - I| and ||A^-1 A - I||_F within twice the CUDA-core flush's: at n = 256
+    an FP32 inverse updated in place over a generation sits at 1e-4..5e-4 element-wise
+    with either engine), and log|Psi| equal to the oracle's FP64 recompute."""
+    wl = wl_mod.pw512()
+    wl.drift = False  # trajectories depend on decisions only, not on rounding of the drift
+    W = 4
+    R = np.ascontiguousarray(wl.positions(n_walkers=W))
+    res = {}
+    for engine in ("auto", "simt"):
+        c = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=16,
+                                  n_walkers=W, n_recompute=0, cta_threads=nt, engine=engine)
+        assert c.kernel_config["tc_flush"] == (1 if engine == "auto" else 0), c.kernel_config
+        assert c.kernel_config["b_in_smem"] == 0
+        c.qmc_load_positions(R)
+        c.qmc_recompute()
+        c.qmc_sweep(2)
+        res[engine] = (c.qmc_get_positions(), [c.qmc_get_inverse(s) for s in range(2)],
+                       [c.qmc_get_slater_matrix(s) for s in range(2)], c.qmc_get_logpsi()[0])
+        c.close()
+    Rt, Bt, At, lt = res["auto"]
+    Rs, Bs, As, ls = res["simt"]
+    same = np.all(np.abs(Rt - Rs) < 1e-6, axis=(1, 2))
+    assert same.sum() >= W - 1, same
+    mt = ms = ft = fs = 0.0
+    eye = np.eye(wl.n_up)
+    for s in range(2):
+        for w in np.nonzero(same)[0]:
+            Et = Bt[s][w] @ At[s][w] - eye
+            Es = Bs[s][w] @ As[s][w] - eye
+            mt, ms = max(mt, np.abs(Et).max()), max(ms, np.abs(Es).max())
+            ft, fs = max(ft, np.linalg.norm(Et)), max(fs, np.linalg.norm(Es))
+    assert mt < 2 * ms and ft < 2 * fs, (mt, ms, ft, fs)
+    assert mt < 1e-3
+    osys = oracle_lib.OracleSystem(wl)
+    for w in np.nonzero(same)[0][:2]:
+        ref, _ = osys.logpsi(Rt[w])
+        assert abs(lt[w] - ref) < 1e-4 * max(1, abs(ref))
