@@ -164,11 +164,18 @@ __device__ __forceinline__ void basis12(T t, T* w) {
 
 // Radial functor u(r) with K free coefficients c[0..K-1] followed by three zeros:
 // i = floor(r h^-1) (at most K-1), u = sum_m c[i+m] b_m(t); zero for r >= rc.
+// FP32: branch-free; the knot index is clamped (every read stays inside the K + 3
+// coefficients, also for r = NaN or inf) and the result is selected to zero outside
+// [0, rc), so the terms of neighbouring partners can be evaluated interleaved.
 template <typename T>
 __device__ __forceinline__ void radial(const T* __restrict__ c, int K, T hinv, T rc, T r, T& u,
                                        T& du, T& d2u) {
-  u = du = d2u = T(0);
-  if (!(r < rc)) return;
+  if constexpr (sizeof(T) == 8) {  // FP64 arithmetic is scarce: skip partners beyond rc
+    if (!(r < rc)) {
+      u = du = d2u = T(0);
+      return;
+    }
+  }
   const T x = r * hinv;
   int i;
   if constexpr (sizeof(T) == 4) i = __float2int_rd(x);
@@ -178,11 +185,15 @@ __device__ __forceinline__ void radial(const T* __restrict__ c, int K, T hinv, T
   const T t2 = t * t, t3 = t2 * t, s = T(1) - t;
   const T sixth = T(1) / T(6);
   const T c0 = c[i], c1 = c[i + 1], c2 = c[i + 2], c3 = c[i + 3];
-  u = (c0 * s * s * s + c1 * (T(3) * t3 - T(6) * t2 + T(4)) +
-       c2 * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + c3 * t3) * sixth;
-  du = (c0 * (T(-0.5) * s * s) + c1 * (T(1.5) * t2 - T(2) * t) +
-        c2 * (T(-1.5) * t2 + t + T(0.5)) + c3 * (T(0.5) * t2)) * hinv;
-  d2u = (c0 * s + c1 * (T(3) * t - T(2)) + c2 * (T(-3) * t + T(1)) + c3 * t) * hinv * hinv;
+  const T uu = (c0 * s * s * s + c1 * (T(3) * t3 - T(6) * t2 + T(4)) +
+                c2 * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + c3 * t3) * sixth;
+  const T dd = (c0 * (T(-0.5) * s * s) + c1 * (T(1.5) * t2 - T(2) * t) +
+                c2 * (T(-1.5) * t2 + t + T(0.5)) + c3 * (T(0.5) * t2)) * hinv;
+  const T d2 = (c0 * s + c1 * (T(3) * t - T(2)) + c2 * (T(-3) * t + T(1)) + c3 * t) * hinv * hinv;
+  const bool in = r < rc;
+  u = in ? uu : T(0);
+  du = in ? dd : T(0);
+  d2u = in ? d2 : T(0);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -654,7 +654,8 @@ __device__ void eval_grad(Ctx<T>& c, int i, const T* pf, bool use_pf, T* uo, T* 
   }
   int t0, t1;
   term_range(p, t0, t1);
-  auto term = [&](int t, T& u_out) {
+  // partner t (use = false: a placeholder partner in range whose term is discarded)
+  auto term = [&](int t, bool use, T& u_out) {
     T d[3], r, rinv;
     partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r, rinv);
     const T* coef; int K; T hinv, rc;
@@ -662,21 +663,21 @@ __device__ void eval_grad(Ctx<T>& c, int i, const T* pf, bool use_pf, T* uo, T* 
     T u, du, d2u;
     radial(coef, K, hinv, rc, r, u, du, d2u);
     u_out = u;
-    if (r > T(0)) {
-      const T f = du * rinv;
-      v[3] += f * d[0];
-      v[4] += f * d[1];
-      v[5] += f * d[2];
-    }
+    const T f = (use && r > T(0)) ? du * rinv : T(0);
+    v[3] += f * d[0];
+    v[4] += f * d[1];
+    v[5] += f * d[2];
   };
 #pragma unroll
   for (int q = 0; q < JT; ++q) {
-    const int t = t0 + c.tid + q * NT;
-    if (t < t1 && t != i) term(t, uo[q]);
+    if (t0 + q * NT < t1) {
+      const int t = t0 + c.tid + q * NT;
+      term(t < t1 ? t : t1 - 1, t < t1 && t != i, uo[q]);
+    }
   }
   for (int t = t0 + c.tid + JT * NT; t < t1; t += NT) {
     T dummy;
-    if (t != i) term(t, dummy);
+    term(t, t != i, dummy);
   }
   block_allreduce8<NWARP>(v, c.red0);
   for (int k = 0; k < 3; ++k) F[k] = v[k] - v[3 + k];
@@ -790,7 +791,8 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int t0, t1;
   term_range(p, t0, t1);
-  auto term = [&](int t, bool have_old, T uold) {
+  // partner t (use = false: a placeholder partner in range whose term is discarded)
+  auto term = [&](int t, bool use, bool have_old, T uold) {
     T dn[3], rn, rninv;
     partner_disp(c, pr.rp, pr.rq, t, dn, rn, rninv);
     const T* coef; int K; T hinv, rc;
@@ -802,21 +804,21 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
       partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro, roinv);
       radial(coef, K, hinv, rc, ro, uold, duo, d2o);
     }
-    v[4] += un - uold;
-    if (rn > T(0)) {
-      const T f = dun * rninv;
-      v[5] += f * dn[0];
-      v[6] += f * dn[1];
-      v[7] += f * dn[2];
-    }
+    const T f = (use && rn > T(0)) ? dun * rninv : T(0);
+    v[4] += use ? un - uold : T(0);
+    v[5] += f * dn[0];
+    v[6] += f * dn[1];
+    v[7] += f * dn[2];
   };
+  // the cached terms: a slot q is skipped only when no thread has a partner in it
 #pragma unroll
   for (int q = 0; q < JT; ++q) {
-    const int t = t0 + c.tid + q * NT;
-    if (t < t1 && t != i) term(t, cached, uo[q]);
+    if (t0 + q * NT < t1) {
+      const int t = t0 + c.tid + q * NT;
+      term(t < t1 ? t : t1 - 1, t < t1 && t != i, cached, uo[q]);
+    }
   }
-  for (int t = t0 + c.tid + JT * NT; t < t1; t += NT)
-    if (t != i) term(t, false, T(0));
+  for (int t = t0 + c.tid + JT * NT; t < t1; t += NT) term(t, t != i, false, T(0));
   const T* wts;
   if constexpr (IsMixed<T>::value) {
     wts = wreg;
@@ -829,9 +831,28 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     ok = mbar_wait_bounded(c.bar, c.tma_phase);
     c.tma_phase ^= 1u;
   }
+  // with TMA staging, the shared-memory reads of the first two items are issued together
+  if (tma && c.nit >= 2) {
+    T cg[16];
+    const T* sa = c.stc + (size_t)(c.ita[0] * 16) * n_pad + c.itj[0];
+    const T* sb = c.stc + (size_t)(c.ita[1] * 16) * n_pad + c.itj[1];
+#pragma unroll
+    for (int bc = 0; bc < 16; ++bc) {
+      cf[bc] = sa[(size_t)bc * n_pad];
+      cg[bc] = sb[(size_t)bc * n_pad];
+    }
+    T o4[4], o4b[4];
+    stencil_reduce(cf, wts, o4);
+    stencil_reduce(cg, wts, o4b);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      c.part[(c.ita[0] * 4 + r) * n_pad + c.itj[0]] = o4[r];
+      c.part[(c.ita[1] * 4 + r) * n_pad + c.itj[1]] = o4b[r];
+    }
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (q < c.nit) {
+    if (q < c.nit && !(tma && c.nit >= 2 && q < 2)) {
       if (tma) {
         const T* sb = c.stc + (size_t)(c.ita[q] * 16) * n_pad + c.itj[q];
 #pragma unroll
@@ -935,12 +956,18 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
     // B^T[k] -= col (v_k - delta_k,pp) / rhoD (one warp per row); f_k reuses `part`.
     const T invr = T(1) / rhoD;
     T* fk = c.part;
-    bool vec = false;
-    if constexpr (sizeof(T) == 4) vec = (n % 16 == 0) && (bs % 4 == 0) && (4 * n <= NT);
-    if (vec) {
-      // four threads per row, each a quarter of the row in float4 reads, two shuffles
+    // threads per row: 4 or 2 when the CTA covers the rows that way (float4 reads of a
+    // part of the row each, combined by shuffles), else one thread per row
+    int tpr = 0;
+    if constexpr (sizeof(T) == 4) {
+      if (bs % 4 == 0) {
+        if (4 * n <= NT && n % 16 == 0) tpr = 4;
+        else if (2 * n <= NT && n % 8 == 0) tpr = 2;
+      }
+    }
+    if (tpr) {
       if constexpr (sizeof(T) == 4) {
-        const int k = c.tid >> 2, qd = c.tid & 3, nq = n >> 2;  // nq floats per quarter
+        const int k = c.tid / tpr, qd = c.tid % tpr, nq = n / tpr;  // nq floats per part
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
         if (k < n) {
           const float4* r4 = reinterpret_cast<const float4*>(c.B + (size_t)k * bs + qd * nq);
@@ -955,7 +982,7 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
         }
         float acc = (a0 + a1) + (a2 + a3);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (tpr == 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (k < n && qd == 0) fk[k] = (acc - (k == pp ? 1.f : 0.f)) * invr;
       }
     } else {
