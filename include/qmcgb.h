@@ -190,6 +190,30 @@ int qmc_crowd_save(qmc_crowd* crowd, void* buf, size_t* size);
 int qmc_crowd_restore(qmc_crowd* crowd, const void* buf, size_t size);
 
 const char* qmc_status_string(int status);
+/* ---------------------------------------------------------------------------------------
+ * Batches: crowds of different systems (electron counts, grids, ions) swept together,
+ * one kernel launch per generation whose CTAs cover every walker of every crowd (the
+ * crowd concept of Sec. III applied across systems of different sizes).  Each crowd keeps
+ * its own state, RNG key, generation counter and FP64 recompute cadence; the result of a
+ * batch sweep equals that of qmc_sweep on each crowd.  Generations without a recompute
+ * replay a captured CUDA graph (move launch + counter advance).
+ * --------------------------------------------------------------------------------------- */
+typedef struct qmc_batch qmc_batch;
+
+/* 1..8 distinct crowds on the current device with the same precision, update kind and
+ * cta_threads (UNSUPPORTED otherwise).  The batch launches on crowds[0]'s stream and
+ * orders the other crowds' streams around each sweep.  The crowds must outlive the batch.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM. */
+int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out);
+int qmc_batch_destroy(qmc_batch* batch);
+/* n_gen generations of every crowd.  eloc: NULL, or n_crowds pointers (entries may be
+ * NULL) to host buffers double [n_gen][W_c] for crowd c's E_L; stats: NULL or n_crowds
+ * entries.  Delayed windows are flushed on the CUDA cores in a batch.  Synchronous.
+ * Errors: as qmc_sweep. */
+int qmc_batch_sweep(qmc_batch* batch, int n_gen, double* const* eloc, qmc_stats* stats);
+/* Kernel launches (graph replays count their nodes) issued by the batch so far. */
+int qmc_batch_get_launch_count(const qmc_batch* batch, unsigned long long* count);
+
 /* Text of the CUDA error behind the calling thread's last QMC_ERR_CUDA ("no error" if none). */
 const char* qmc_last_cuda_error(void);
 

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -25,6 +26,18 @@ size_t move_smem_bytes(const Params& p, int elem_bytes) {
 template <typename T>
 cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s) {
   return p.nt == 128 ? nt128::launch_move<T>(p, mode, tmap, s) : nt256::launch_move<T>(p, mode, tmap, s);
+}
+
+template <typename T>
+cudaError_t launch_batch(int nt, const Params* d_plist, const BatchArgs& a, int update,
+                         size_t bytes, cudaStream_t s) {
+  return nt == 128 ? nt128::launch_batch<T>(d_plist, a, update, bytes, s)
+                   : nt256::launch_batch<T>(d_plist, a, update, bytes, s);
+}
+
+// Advances the generation counter of every crowd of a batch (after its move launch).
+__global__ void batch_advance_kernel(Params* plist, int n) {
+  if ((int)threadIdx.x < n) plist[threadIdx.x].gen += 1u;
 }
 
 int sweep_ctas_per_sm(const Params& p) {
@@ -843,6 +856,269 @@ int qmc_crowd_save(qmc_crowd* c, void* buf, size_t* size) {
   int st = qmc_get_positions(c, (double*)((char*)buf + sizeof(h)), QMC_MEM_HOST);
   *size = need;
   return st;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batches: several crowds (systems of different sizes) swept by one launch per generation.
+// ---------------------------------------------------------------------------------------
+struct qmc_batch {
+  std::vector<qmc_crowd*> crowds;  // caller's order
+  std::vector<int> order;          // launch order: largest systems first
+  int update = 0, nt = 256;
+  bool mixed = false;
+  size_t smem = 0;
+  qmcgb::BatchArgs args{};
+  std::vector<Params> hp;          // launch order
+  Params* d_params = nullptr;
+  std::vector<double*> ring;       // per crowd (caller's order): E_L [cap][W]
+  int ring_cap = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t graph = nullptr;  // one plain generation: batch move launch + advance
+  bool eager_done = false;
+  unsigned long long launches = 0;
+};
+
+namespace {
+
+void batch_free(qmc_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->d_params) cudaFree(b->d_params);
+  for (double* r : b->ring)
+    if (r) cudaFree(r);
+  if (b->ev) cudaEventDestroy(b->ev);
+}
+
+int batch_launch_move(qmc_batch* b) {
+  ++b->launches;
+  cudaError_t e = b->mixed ? qmcgb::launch_batch<float>(b->nt, b->d_params, b->args, b->update,
+                                                         b->smem, b->stream)
+                           : qmcgb::launch_batch<double>(b->nt, b->d_params, b->args, b->update,
+                                                          b->smem, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  ++b->launches;
+  qmcgb::batch_advance_kernel<<<1, 32, 0, b->stream>>>(b->d_params, (int)b->order.size());
+  e = cudaGetLastError();
+  return e == cudaSuccess ? QMC_OK : cuda_fail(e);
+}
+
+// Every crowd's stream waits for the batch stream (or the other way round).
+int batch_join(qmc_batch* b, bool into_batch) {
+  for (qmc_crowd* c : b->crowds) {
+    if (c->stream == b->stream) continue;
+    cudaStream_t from = into_batch ? c->stream : b->stream;
+    cudaStream_t to = into_batch ? b->stream : c->stream;
+    CK(cudaEventRecord(b->ev, from));
+    CK(cudaStreamWaitEvent(to, b->ev, 0));
+  }
+  return QMC_OK;
+}
+
+}  // namespace
+
+int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out) {
+  if (!crowds || !out || n_crowds < 1 || n_crowds > qmcgb::MAX_BATCH) return QMC_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n_crowds; ++i) {
+    if (!crowds[i]) return QMC_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (crowds[j] == crowds[i]) return QMC_ERR_INVALID_ARG;
+    const qmc_crowd* c = crowds[i];
+    const qmc_crowd* c0 = crowds[0];
+    if (c->run.precision != c0->run.precision || c->run.update != c0->run.update ||
+        c->p.nt != c0->p.nt)
+      return QMC_ERR_UNSUPPORTED;
+  }
+  qmc_batch* b = new qmc_batch();
+  b->crowds.assign(crowds, crowds + n_crowds);
+  b->update = crowds[0]->run.update;
+  b->nt = crowds[0]->p.nt;
+  b->mixed = is_mixed(crowds[0]);
+  b->stream = crowds[0]->stream;
+  b->order.resize(n_crowds);
+  for (int i = 0; i < n_crowds; ++i) b->order[i] = i;
+  // longest walkers first: their CTAs start in the first wave
+  std::sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    return crowds[x]->p.N > crowds[y]->p.N || (crowds[x]->p.N == crowds[y]->p.N && x < y);
+  });
+  b->args.n = n_crowds;
+  b->args.base[0] = 0;
+  for (int q = 0; q < n_crowds; ++q) {
+    qmc_crowd* c = crowds[b->order[q]];
+    b->args.base[q + 1] = b->args.base[q] + c->p.W;
+    std::memcpy(&b->args.maps[q], &c->tmap, sizeof(CUtensorMap));
+    b->smem = std::max(b->smem, c->smem);
+  }
+  b->hp.resize(n_crowds);
+  b->ring.assign(n_crowds, nullptr);
+  if (dmalloc((void**)&b->d_params, sizeof(Params) * n_crowds) ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    delete b;
+    return QMC_ERR_OOM;
+  }
+  *out = b;
+  return QMC_OK;
+}
+
+int qmc_batch_destroy(qmc_batch* b) {
+  if (!b) return QMC_ERR_INVALID_ARG;
+  cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  delete b;
+  return QMC_OK;
+}
+
+int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* stats) {
+  if (!b || n_gen < 0) return QMC_ERR_INVALID_ARG;
+  const int nc = (int)b->crowds.size();
+  for (qmc_crowd* c : b->crowds) {
+    const int st = ensure_ready(c);
+    if (st) return st;
+  }
+  if (n_gen == 0) return QMC_OK;
+  int st = batch_join(b, true);
+  if (st) return st;
+  if (b->ring_cap < n_gen) {
+    for (double*& r : b->ring) {
+      if (r) cudaFree(r);
+      r = nullptr;
+    }
+    b->ring_cap = 0;
+    for (int i = 0; i < nc; ++i)
+      if (dmalloc((void**)&b->ring[i], sizeof(double) * (size_t)n_gen * b->crowds[i]->p.W))
+        return QMC_ERR_OOM;
+    b->ring_cap = n_gen;
+    if (b->graph) {  // the graph holds the old parameters' addresses only, but rebuild anyway
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  // parameters of every crowd (launch order), E_L rows indexed by generation
+  auto fill = [&](int g) {
+    for (int q = 0; q < nc; ++q) {
+      const int ci = b->order[q];
+      qmc_crowd* c = b->crowds[ci];
+      sync_params(c);
+      Params p = c->p;
+      p.gen = c->gen + (uint32_t)g;
+      p.eloc_out = b->ring[ci];
+      p.eloc_by_gen = 1;
+      p.eloc_gen0 = c->gen;
+      p.n_accept = stats ? c->d_nacc : nullptr;
+      p.stencil_bytes = qmcgb::stencil_tma_bytes(p, c->es);
+      p.skip_eloc = 0;
+      p.tc_flush = 0;  // the batch kernel keeps delayed flushes on the CUDA cores
+      b->hp[q] = p;
+    }
+  };
+  if (stats)
+    for (qmc_crowd* c : b->crowds)
+      CK(cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), b->stream));
+  auto due = [&](qmc_crowd* c, int g) {
+    return c->run.n_recompute > 0 && ((c->gen + (uint32_t)g + 1) % (uint32_t)c->run.n_recompute) == 0;
+  };
+  fill(0);
+  for (int q = 0; q < nc; ++q)  // layouts as launched (the kernel checks this too)
+    if (qmcgb::move_smem_bytes(b->hp[q], b->crowds[b->order[q]]->es) > b->smem)
+      return QMC_ERR_STATE;
+  CK(cudaMemcpyAsync(b->d_params, b->hp.data(), sizeof(Params) * nc, cudaMemcpyHostToDevice,
+                     b->stream));
+  for (int g = 0; g < n_gen; ++g) {
+    bool any_due = false;
+    for (qmc_crowd* c : b->crowds) any_due |= due(c, g);
+    if (!any_due && !b->graph && !b->eager_done) {
+      // the first plain generation runs eagerly (it configures the kernel's shared memory
+      // limit, which a stream capture must not do); later ones replay a captured graph
+      st = batch_launch_move(b);
+      if (st) return st;
+      b->eager_done = true;
+      continue;
+    }
+    if (!any_due) {
+      // a plain generation: replay the captured graph (batch launch + advance)
+      if (!b->graph) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const int ls = batch_launch_move(b);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+        if (ls) {
+          if (graph) cudaGraphDestroy(graph);
+          return ls;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce);
+        ce = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ce);
+        b->launches -= 2;  // counted at replay
+      }
+      CK(cudaGraphLaunch(b->graph, b->stream));
+      b->launches += 2;
+      continue;
+    }
+    // a generation with an FP64 recompute for some crowds: their E_L follows the recompute
+    fill(g);
+    for (int q = 0; q < nc; ++q) b->hp[q].skip_eloc = due(b->crowds[b->order[q]], g) ? 1 : 0;
+    CK(cudaMemcpyAsync(b->d_params, b->hp.data(), sizeof(Params) * nc, cudaMemcpyHostToDevice,
+                       b->stream));
+    st = batch_launch_move(b);
+    if (st) return st;
+    for (int q = 0; q < nc; ++q) {
+      const int ci = b->order[q];
+      qmc_crowd* c = b->crowds[ci];
+      if (!due(c, g)) continue;
+      Params p = b->hp[q];
+      cudaError_t e = is_mixed(c) ? qmcgb::launch_recompute<float>(p, c->d_ws, b->stream)
+                                  : qmcgb::launch_recompute<double>(p, c->d_ws, b->stream);
+      ++b->launches;
+      if (e != cudaSuccess) return cuda_fail(e);
+      p.skip_eloc = 0;
+      const void* tm = p.use_tma ? (const void*)&c->tmap : nullptr;
+      e = is_mixed(c) ? qmcgb::launch_move<float>(p, qmcgb::MODE_ELOC, tm, b->stream)
+                      : qmcgb::launch_move<double>(p, qmcgb::MODE_ELOC, tm, b->stream);
+      ++b->launches;
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
+    // back to plain parameters for the following generations (generation g + 1)
+    fill(g + 1);
+    CK(cudaMemcpyAsync(b->d_params, b->hp.data(), sizeof(Params) * nc, cudaMemcpyHostToDevice,
+                       b->stream));
+  }
+  for (qmc_crowd* c : b->crowds) c->gen += (uint32_t)n_gen;
+  st = batch_join(b, false);
+  if (st) return st;
+  CK(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < nc; ++i) {
+    qmc_crowd* c = b->crowds[i];
+    const size_t cnt = (size_t)n_gen * c->p.W;
+    std::vector<double> h(cnt);
+    CK(cudaMemcpy(h.data(), b->ring[i], sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    if (eloc && eloc[i]) std::memcpy(eloc[i], h.data(), sizeof(double) * cnt);
+    if (stats) {
+      double s1 = 0.0, s2 = 0.0;
+      for (double e : h) {
+        s1 += e;
+        s2 += e * e;
+      }
+      unsigned long long na = 0;
+      CK(cudaMemcpy(&na, c->d_nacc, sizeof(na), cudaMemcpyDeviceToHost));
+      stats[i].e_sum = s1;
+      stats[i].e2_sum = s2;
+      stats[i].n_samples = (long long)cnt;
+      stats[i].n_accept = (long long)na;
+      stats[i].n_moves = (long long)n_gen * c->p.W * c->p.N;
+    }
+    st = read_status(c);
+    if (st) return st;
+  }
+  return QMC_OK;
+}
+
+int qmc_batch_get_launch_count(const qmc_batch* b, unsigned long long* count) {
+  if (!b || !count) return QMC_ERR_INVALID_ARG;
+  *count = b->launches;
+  return QMC_OK;
 }
 
 int qmc_crowd_restore(qmc_crowd* c, const void* buf, size_t size) {

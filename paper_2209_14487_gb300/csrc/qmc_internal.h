@@ -3,6 +3,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace qmcgb {
@@ -43,6 +44,8 @@ struct Params {
   int nt;                   // threads per CTA of the move kernel: 128 or 256
   int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
+  int eloc_by_gen;          // E_L of generation g goes to eloc_out[(g - eloc_gen0) W + w]
+  uint32_t eloc_gen0;
   int stencil_bytes;        // bytes of that copy
   int vs, ks;               // padded strides of the window's V rows and S^-1 rows
   uint32_t gen;
@@ -86,10 +89,21 @@ int sweep_ctas_per_sm(const Params& p);
 template <typename T>
 cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s);
 int stencil_tma_bytes(const Params& p, int elem_bytes);
+// Several crowds in one launch: crowd c owns CTAs [base[c], base[c+1]).
+constexpr int MAX_BATCH = 8;
+struct BatchArgs {
+  CUtensorMap maps[MAX_BATCH];  // each crowd's table map (unused where use_tma == 0)
+  int base[MAX_BATCH + 1];
+  int n;
+};
+
 #define QMCGB_DECLARE_MOVE_WIDTH(NS)                                                      \
   namespace NS {                                                                        \
   template <typename T>                                                                 \
   cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s); \
+  template <typename T>                                                                 \
+  cudaError_t launch_batch(const Params* d_plist, const BatchArgs& a, int update,       \
+                           size_t bytes, cudaStream_t s);                              \
   size_t move_smem_bytes(const Params& p, int elem_bytes);                              \
   int sweep_ctas_per_sm(const Params& p);                                               \
   }

@@ -129,7 +129,7 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.Rq = o; o += al16((size_t)p.N * 3 * 4);
   L.ion = o; o += al16((size_t)p.n_ions * 3 * 8);
   L.ionq = o; o += al16((size_t)p.n_ions * 3 * 4);
-  L.jc = o; o += al16((size_t)(2 * (p.K2 + 3) + p.K1 + 3) * es);
+  L.jc = o; o += al16((size_t)3 * (MAX_KNOTS + 3) * es);  // any Jastrow the crowd loads later
   L.phi = o; o += al16((size_t)5 * p.n_pad * es);
   L.part = o; o += al16((size_t)16 * p.n_pad * es);
   L.col = o; o += al16((size_t)p.n_pad * es);
@@ -1197,12 +1197,18 @@ __device__ __forceinline__ void shared_proposal(Ctx<T>& c, int i, const T* F, co
   }
 }
 
+// Offset of this generation's E_L in p.eloc_out: a batch sweep keeps one row per
+// generation ([gen - eloc_gen0][W]); single-crowd calls write row 0.
+__device__ __forceinline__ size_t eloc_slot(const Params& p) {
+  return p.eloc_by_gen ? (size_t)(p.gen - p.eloc_gen0) * p.W : 0;
+}
+
+// The body of one walker's CTA (walker w of the crowd described by p); smem is the CTA's
+// dynamic shared memory, tmap the crowd's table tensor map.
 template <typename T, int MODE, int UPD, int BSM>
-__global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
-                                                     const __grid_constant__ CUtensorMap tmap) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void move_body(const Params& p, const int w, const CUtensorMap* tmap,
+                                          unsigned char* smem) {
   const Lay lay = make_lay<T>(p);
-  const int w = blockIdx.x;
   const int N = p.N, n = p.n, n_pad = p.n_pad;
   Ctx<T> c{p};
   c.k = make_cst<T>(p);
@@ -1242,7 +1248,7 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
   c.rows = (T*)p.rows + (size_t)w * N * 5 * n_pad;
   c.bar = (uint64_t*)(smem + lay.bar);
   c.stc = (T*)((reinterpret_cast<uintptr_t>(smem + lay.stc) + 127) & ~(uintptr_t)127);
-  c.tmap = &tmap;
+  c.tmap = tmap;
   c.tma_phase = 0;
   c.mma_phase = 0;
   c.tcs = (float*)((reinterpret_cast<uintptr_t>(smem + lay.tcs) + 127) & ~(uintptr_t)127);
@@ -1363,7 +1369,7 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
     if (!p.skip_eloc) {
       const double e = local_energy(c);
       if (c.tid == 0) {
-        if (p.eloc_out) p.eloc_out[w] = e;
+        if (p.eloc_out) p.eloc_out[eloc_slot(p) + w] = e;
         if (!isfinite(e)) atomicOr(p.status, ST_NAN);
       }
     }
@@ -1470,7 +1476,7 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
     if (!p.skip_eloc) {
       const double e = local_energy(c);
       if (c.tid == 0) {
-        p.eloc_out[w] = e;
+        p.eloc_out[eloc_slot(p) + w] = e;
         if (!isfinite(e)) atomicOr(p.status, ST_NAN);
       }
     }
@@ -1489,6 +1495,38 @@ __global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
       p.sign[w * 2 + 1] = sc->sign[1];
     }
   }
+}
+
+template <typename T, int MODE, int UPD, int BSM>
+__global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
+                                                     const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  move_body<T, MODE, UPD, BSM>(p, blockIdx.x, &tmap, smem);
+}
+
+// One generation of several crowds in one launch (the mixed-size batch): CTA b runs walker
+// b - base[c] of crowd c, with the crowd's parameters copied from global memory into
+// shared memory.  Where the inverse lives is decided per crowd at run time.
+template <typename T, int UPD>
+__global__ void __launch_bounds__(NT, 2) move_kernel_batch(const Params* __restrict__ plist,
+                                                           const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) Params sp;
+  int cr = 0;
+  while (cr + 1 < a.n && (int)blockIdx.x >= a.base[cr + 1]) ++cr;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(plist + cr);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
+  for (int e = threadIdx.x; e < (int)(sizeof(Params) / 4); e += NT) dst[e] = src[e];
+  __syncthreads();
+  // the crowd's layout must fit the launch's dynamic shared memory (uniform per CTA)
+  uint32_t dyn;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const int w = (int)blockIdx.x - a.base[cr];
+  if (make_lay<T>(sp).total > dyn || w >= sp.W) {
+    if (threadIdx.x == 0) atomicOr(sp.status, ST_STATE);
+    return;
+  }
+  move_body<T, MODE_SWEEP, UPD, 0>(sp, w, &a.maps[cr], smem);
 }
 
 // Lets a kernel instantiation use up to the device's opt-in shared memory per CTA (set
@@ -1575,6 +1613,39 @@ int sweep_ctas_per_sm(const Params& p_in) {
   }
   return nb;
 }
+
+template <typename T, int UPD>
+static cudaError_t launch_batch_upd(const Params* d_plist, const BatchArgs& a, size_t bytes,
+                                    cudaStream_t s) {
+  static int done_for = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (done_for != dev) {
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int avail = optin - (int)sizeof(Params) - 16;  // the static Params copy
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(move_kernel_batch<T, UPD>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
+    if (e != cudaSuccess) return e;
+    done_for = dev;
+  }
+  move_kernel_batch<T, UPD><<<a.base[a.n], NT, bytes, s>>>(d_plist, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch(const Params* d_plist, const BatchArgs& a, int update, size_t bytes,
+                         cudaStream_t s) {
+  return update == 1 ? launch_batch_upd<T, 1>(d_plist, a, bytes, s)
+                     : launch_batch_upd<T, 0>(d_plist, a, bytes, s);
+}
+
+template cudaError_t launch_batch<float>(const Params*, const BatchArgs&, int, size_t,
+                                         cudaStream_t);
+template cudaError_t launch_batch<double>(const Params*, const BatchArgs&, int, size_t,
+                                          cudaStream_t);
 
 template cudaError_t launch_move<double>(const Params&, int, const void*, cudaStream_t);
 template cudaError_t launch_move<float>(const Params&, int, const void*, cudaStream_t);

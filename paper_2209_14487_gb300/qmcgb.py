@@ -35,7 +35,8 @@ EXPORTS = [
     "qmc_get_positions", "qmc_get_logpsi", "qmc_get_inverse", "qmc_get_slater_matrix",
     "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
-    "qmc_last_cuda_error",
+    "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
+    "qmc_batch_get_launch_count",
 ]
 
 
@@ -91,6 +92,10 @@ def _load():
         "qmc_set_generation": [vp, C.c_uint32],
         "qmc_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
         "qmc_get_kernel_config": [vp] + [C.POINTER(C.c_int)] * 5,
+        "qmc_batch_create": [C.POINTER(vp), i, C.POINTER(vp)],
+        "qmc_batch_destroy": [vp],
+        "qmc_batch_sweep": [vp, i, vp, vp],
+        "qmc_batch_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -309,6 +314,43 @@ class Crowd:
     def qmc_crowd_restore(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         _check("qmc_crowd_restore", lib.qmc_crowd_restore(self.h, buf, len(data)))
+
+
+class Batch:
+    """Crowds of different systems swept together: one launch per generation covers every
+    walker of every crowd (qmc_batch_* in include/qmcgb.h).  Keeps the crowds alive."""
+
+    def __init__(self, crowds):
+        self.crowds = list(crowds)
+        arr = (C.c_void_p * len(self.crowds))(*[c.h.value for c in self.crowds])
+        h = C.c_void_p()
+        _check("qmc_batch_create", lib.qmc_batch_create(arr, len(self.crowds), C.byref(h)))
+        self.h = h
+
+    def qmc_batch_sweep(self, n_gen: int, eloc=True, stats=True):
+        """(list of E_L arrays [n_gen][W_c] or None, list of qmc_stats or None)."""
+        out = [np.zeros((n_gen, c.W)) for c in self.crowds] if eloc else None
+        ptrs = (C.c_void_p * len(self.crowds))(*[o.ctypes.data for o in out]) if eloc else None
+        st = (qmc_stats * len(self.crowds))() if stats else None
+        _check("qmc_batch_sweep", lib.qmc_batch_sweep(self.h, n_gen, ptrs, st))
+        return out, (list(st) if stats else None)
+
+    @property
+    def launch_count(self) -> int:
+        v = C.c_ulonglong()
+        _check("qmc_batch_get_launch_count", lib.qmc_batch_get_launch_count(self.h, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.qmc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def qmc_inverse_noalloc(a, inv, logdet, sign, stream=None):

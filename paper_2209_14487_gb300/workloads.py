@@ -229,7 +229,32 @@ def pw512() -> Workload:
                          tau=0.5, n_recompute=128, j2_knots=10)
 
 
-WORKLOADS = {"pw16": pw16, "pw128": pw128, "pw512": pw512}
+def _mixed_size(n_el: int, n_orb: int, grid: int, n_walkers: int, offset: int) -> Workload:
+    # the density of pw16/pw128 (L = 5 (N/16)^(1/3)), N/4 ions, J1 (8 knots) + J2 (10)
+    return make_workload(f"mix{n_el}", n_el=n_el, n_orb=n_orb, grid=grid, n_walkers=n_walkers,
+                         n_gen=200, n_ions=n_el // 4, tau=0.5, n_recompute=64, j1_knots=8,
+                         j2_knots=10, crowd_seed_offset=offset)
+
+
+def mix64() -> Workload:
+    """64 electrons (32/32), 32 orbitals on 32^3, 16 ions, L = 7.94, 512 walkers."""
+    return _mixed_size(64, 32, 32, 512, 0)
+
+
+def mix192() -> Workload:
+    """192 electrons (96/96), 96 orbitals on 48^3, 48 ions, L = 11.45, 256 walkers."""
+    return _mixed_size(192, 96, 48, 256, 1)
+
+
+def mix384() -> Workload:
+    """384 electrons (192/192), 192 orbitals on 64^3, 96 ions, L = 14.42, 128 walkers."""
+    return _mixed_size(384, 192, 64, 128, 2)
+
+
+MIXED_BATCH = (mix64, mix192, mix384)
+
+WORKLOADS = {"pw16": pw16, "pw128": pw128, "pw512": pw512, "mix64": mix64, "mix192": mix192,
+             "mix384": mix384}
 
 
 def tiny(n_el: int = 8, n_orb: int | None = None, grid: int = 12, n_walkers: int = 4,
