@@ -162,21 +162,21 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def make_crowd(wl, precision, update, k, stream, crowd_id):
+def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0):
     from paper_2209_14487_gb300 import qmcgb
     c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
-                                  stream=stream)
+                                  stream=stream, cta_threads=nt)
     c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=crowd_id)))
     c.qmc_recompute()
     return c
 
 
-def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf):
+def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0):
     """Per-step CUDA-event timing of qmc_sweep(1) on torch's current stream."""
     import torch
     stream = torch.cuda.Stream()  # a real stream: torch's default is the legacy NULL stream
     torch.cuda.set_stream(stream)
-    c = make_crowd(wl, precision, update, k, stream.cuda_stream, crowd_id)
+    c = make_crowd(wl, precision, update, k, stream.cuda_stream, crowd_id, nt)
     eloc = torch.zeros((warmup + steps, wl.n_walkers), dtype=torch.float64, device="cuda")
     for g in range(warmup):
         c.qmc_sweep(1, eloc[g], stats=False)
@@ -213,7 +213,7 @@ def energy_stats(e: np.ndarray, n_blocks: int = 10):
     return float(b.mean()), float(b.std(ddof=1) / math.sqrt(nb)) if nb > 1 else float("nan")
 
 
-def e2e_run(wl, precision, update, k, steps, crowd_id):
+def e2e_run(wl, precision, update, k, steps, crowd_id, nt=0):
     """Through the public API from pinned host buffers: create, load table, ions, Jastrow
     and positions, recompute, then `steps` sweeps each returning E_L to the host."""
     import torch
@@ -227,7 +227,7 @@ def e2e_run(wl, precision, update, k, steps, crowd_id):
     c = qmcgb.Crowd(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L, wl.n_walkers, wl.tau,
                     precision=precision, update=update, delay_rank=k,
                     n_recompute=wl.n_recompute, drift=wl.drift, potential=wl.potential,
-                    seed=wl.seed)
+                    seed=wl.seed, cta_threads=nt)
     if wl.n_ions:
         c.qmc_load_ions(wl.ions)
     if wl.j2_uu is not None:
@@ -286,8 +286,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="pw128")
+    ap.add_argument("--walkers", type=int, default=None,
+                    help="walkers per GPU (default: the workload's)")
     ap.add_argument("--delay-rank", type=int, default=None)
     ap.add_argument("--update", default="auto", choices=["auto", "sm", "delayed"])
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 128, 256],
+                    help="threads per walker CTA (0: tuned with --update auto, else the "
+                         "library's choice)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -296,6 +301,8 @@ def main():
 
     from paper_2209_14487_gb300 import workloads
     wl = workloads.WORKLOADS[args.workload]()
+    if args.walkers:
+        wl.n_walkers = args.walkers
     ws, rank, local = dist_env()
     update = args.update
     k = args.delay_rank or (1 if update == "sm" else 8)
@@ -365,14 +372,18 @@ def main():
     tune_table = None
     if update == "auto":
         from paper_2209_14487_gb300 import autotune
-        update, k, tune_table = autotune.tune(wl, "mixed")
+        update, k, tuned_nt, tune_table = autotune.tune(wl, "mixed")
+        if not args.cta_threads:
+            args.cta_threads = tuned_nt
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(uuid) as clk:
-        mixed = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush)
+        mixed = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush,
+                          args.cta_threads)
         fp64 = None
         if not args.no_fp64:
-            fp64 = time_path(wl, "fp64", "sm", 1, args.steps, args.warmup, rank, flush)
+            fp64 = time_path(wl, "fp64", "sm", 1, args.steps, args.warmup, rank, flush,
+                             args.cta_threads)
     torch.cuda.synchronize()
     barrier(ws)
 
@@ -385,9 +396,11 @@ def main():
            "data": "synthetic", "config": dict(cfg, precision="mixed: fp32 orbitals, Jastrow, "
                                                "ratios and inverse; fp64 recompute and energy",
                                                update=f"{update} k={k}",
+                                               cta_threads=args.cta_threads or "library",
                                                parallelism=f"replicas x{ws}")}
     if tune_table is not None:
-        out["autotune"] = {"ms_per_generation": tune_table, "chosen": f"{update}:{k}"}
+        out["autotune"] = {"ms_per_generation": tune_table,
+                           "chosen": f"{update}:{k}:{args.cta_threads}"}
     e_m, s_m = energy_stats(mixed["eloc"])
     out["energy"] = {"mixed": {"mean": e_m, "sigma": s_m}}
     if fp64 is not None:
@@ -413,7 +426,7 @@ def main():
     out["gpu_launches"] = mixed["launches"]
     out["clocks"] = clk.summary()
     if not args.no_e2e:
-        rate, h2d, d2h = e2e_run(wl, "mixed", update, k, args.steps, rank)
+        rate, h2d, d2h = e2e_run(wl, "mixed", update, k, args.steps, rank, args.cta_threads)
         rate = aggregate_value(moves_step * args.steps, moves_step * args.steps / rate, ws)
         out["e2e"] = {"value": rate, "unit": UNIT, "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h,

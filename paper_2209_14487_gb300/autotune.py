@@ -1,7 +1,7 @@
-"""Autotuner for the inverse-update scheme of a crowd: Sherman-Morrison or a delayed
-(Woodbury) window of rank k, chosen by timing a few generations of each candidate on the
-current GPU.  Results are cached in a JSON file keyed by system size, crowd size,
-precision and GPU name.
+"""Autotuner for the inverse-update scheme of a crowd and its CTA width: Sherman-Morrison
+or a delayed (Woodbury) window of rank k, with 128 or 256 threads per walker, chosen by
+timing a few generations of each candidate on the current GPU.  Results are cached in a
+JSON file keyed by system size, crowd size, precision and GPU name.
 
 The timing uses CUDA events on a dedicated stream around qmc_sweep(1) calls; the crowd
 under test is built from the same workload the caller will run.
@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 DEFAULT_CANDIDATES = (("sm", 1), ("delayed", 2), ("delayed", 4), ("delayed", 8),
-                      ("delayed", 16), ("delayed", 32))
+                      ("delayed", 16), ("delayed", 32), ("delayed", 64))
+WIDTHS = (128, 256)
 
 
 def cache_path() -> str:
@@ -25,12 +26,13 @@ def cache_path() -> str:
 
 def _key(wl, precision: str, gpu: str) -> str:
     return (f"{gpu}|N={wl.n_el}|n={wl.n_up}|G={wl.grid}|W={wl.n_walkers}|NI={wl.n_ions}|"
-            f"{precision}")
+            f"{precision}|v2")
 
 
 def time_candidate(wl, precision: str, update: str, k: int, gens: int = 4,
-                   warmup: int = 2) -> float:
-    """Median milliseconds of one generation of the crowd with this update scheme."""
+                   warmup: int = 2, cta_threads: int = 0) -> float:
+    """Median milliseconds of one generation of the crowd with this update scheme (inf
+    when the configuration does not fit the GPU)."""
     import torch
 
     from . import qmcgb
@@ -38,8 +40,13 @@ def time_candidate(wl, precision: str, update: str, k: int, gens: int = 4,
     s = torch.cuda.Stream()
     torch.cuda.set_stream(s)
     try:
-        c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
-                                      stream=s.cuda_stream)
+        try:
+            c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
+                                          stream=s.cuda_stream, cta_threads=cta_threads)
+        except qmcgb.QmcError as e:
+            if e.status == qmcgb.QMC_ERR_UNSUPPORTED:
+                return float("inf")
+            raise
         c.qmc_load_positions(np.ascontiguousarray(wl.positions()))
         c.qmc_recompute()
         for _ in range(warmup):
@@ -59,8 +66,9 @@ def time_candidate(wl, precision: str, update: str, k: int, gens: int = 4,
 
 
 def tune(wl, precision: str = "mixed", candidates=DEFAULT_CANDIDATES, gens: int = 4,
-         use_cache: bool = True):
-    """(update, k, {candidate: ms}) for the fastest candidate; cached per GPU and shape."""
+         use_cache: bool = True, widths=WIDTHS):
+    """(update, k, cta_threads, {candidate: ms}) for the fastest candidate; cached per GPU
+    and shape."""
     import torch
     gpu = torch.cuda.get_device_name()
     key = _key(wl, precision, gpu)
@@ -73,17 +81,19 @@ def tune(wl, precision: str = "mixed", candidates=DEFAULT_CANDIDATES, gens: int 
             cache = {}
         if key in cache:
             e = cache[key]
-            return e["update"], e["k"], e["table"]
+            return e["update"], e["k"], e["nt"], e["table"]
     table = {}
-    for update, k in candidates:
-        table[f"{update}:{k}"] = time_candidate(wl, precision, update, k, gens=gens)
+    for nt in widths:
+        for update, k in candidates:
+            table[f"{update}:{k}:{nt}"] = time_candidate(wl, precision, update, k, gens=gens,
+                                                         cta_threads=nt)
     best = min(table, key=table.get)
-    update, k = best.split(":")[0], int(best.split(":")[1])
-    cache[key] = {"update": update, "k": k, "table": table}
+    update, k, nt = best.split(":")[0], int(best.split(":")[1]), int(best.split(":")[2])
+    cache[key] = {"update": update, "k": k, "nt": nt, "table": table}
     try:
         with open(path + ".tmp", "w") as fh:
             json.dump(cache, fh, indent=1)
         os.replace(path + ".tmp", path)
     except OSError:
         pass
-    return update, k, table
+    return update, k, nt, table

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqmcgb.so")
 
 QMC_OK = 0
+QMC_ERR_UNSUPPORTED = 8
 QMC_MEM_HOST, QMC_MEM_DEVICE = 0, 1
 QMC_PREC_FP64, QMC_PREC_MIXED = 0, 1
 QMC_UPDATE_SM, QMC_UPDATE_DELAYED = 0, 1
