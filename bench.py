@@ -290,7 +290,7 @@ def main():
                     help="walkers per GPU (default: the workload's)")
     ap.add_argument("--delay-rank", type=int, default=None)
     ap.add_argument("--update", default="auto", choices=["auto", "sm", "delayed"])
-    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 128, 256],
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 128, 160, 256],
                     help="threads per walker CTA (0: tuned with --update auto, else the "
                          "library's choice)")
     ap.add_argument("--no-fp64", action="store_true")

@@ -86,8 +86,9 @@ typedef struct qmc_run_desc {
                      * QMC_STAGING_LDG: the stencil is read with per-thread loads      */
   double tau;       /* time step                                                      */
   uint64_t seed;    /* Philox key: (low 32 bits, walker ^ high 32 bits)               */
-  int cta_threads;  /* threads per walker CTA of the move kernel: 128, 256, or 0 for  *
-                     * the library's choice (128 up to 128 electrons per spin)         */
+  int cta_threads;  /* threads per walker CTA of the move kernel: 128, 160, 256, or 0 *
+                     * for the library's choice (128 up to 128 electrons per spin,     *
+                     * else 256); the tensor-core flush needs 128 or 256               */
   int engine;       /* QMC_ENGINE_AUTO (0): in the mixed path with the delayed update   *
                      * and the inverse in global memory, windows are flushed on the    *
                      * tensor cores (tcgen05, 3xTF32); QMC_ENGINE_SIMT: CUDA cores     */

@@ -1,5 +1,5 @@
 """Autotuner for the inverse-update scheme of a crowd and its CTA width: Sherman-Morrison
-or a delayed (Woodbury) window of rank k, with 128 or 256 threads per walker, chosen by
+or a delayed (Woodbury) window of rank k, with 128, 160 or 256 threads per walker, chosen by
 timing a few generations of each candidate on the current GPU.  Results are cached in a
 JSON file keyed by system size, crowd size, precision and GPU name.
 
@@ -15,7 +15,7 @@ import numpy as np
 
 DEFAULT_CANDIDATES = (("sm", 1), ("delayed", 2), ("delayed", 4), ("delayed", 8),
                       ("delayed", 16), ("delayed", 32), ("delayed", 64))
-WIDTHS = (128, 256)
+WIDTHS = (128, 160, 256)
 
 
 def cache_path() -> str:
@@ -26,7 +26,7 @@ def cache_path() -> str:
 
 def _key(wl, precision: str, gpu: str) -> str:
     return (f"{gpu}|N={wl.n_el}|n={wl.n_up}|G={wl.grid}|W={wl.n_walkers}|NI={wl.n_ions}|"
-            f"{precision}|v2")
+            f"{precision}|v3")
 
 
 def time_candidate(wl, precision: str, update: str, k: int, gens: int = 4,

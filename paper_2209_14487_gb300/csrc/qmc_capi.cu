@@ -20,19 +20,24 @@ namespace qmcgb {
 int stencil_tma_bytes(const Params& p, int elem_bytes) { return 64 * p.n_pad * elem_bytes; }
 
 size_t move_smem_bytes(const Params& p, int elem_bytes) {
-  return p.nt == 128 ? nt128::move_smem_bytes(p, elem_bytes) : nt256::move_smem_bytes(p, elem_bytes);
+  if (p.nt == 128) return nt128::move_smem_bytes(p, elem_bytes);
+  if (p.nt == 160) return nt160::move_smem_bytes(p, elem_bytes);
+  return nt256::move_smem_bytes(p, elem_bytes);
 }
 
 template <typename T>
 cudaError_t launch_move(const Params& p, int mode, const void* tmap, cudaStream_t s) {
-  return p.nt == 128 ? nt128::launch_move<T>(p, mode, tmap, s) : nt256::launch_move<T>(p, mode, tmap, s);
+  if (p.nt == 128) return nt128::launch_move<T>(p, mode, tmap, s);
+  if (p.nt == 160) return nt160::launch_move<T>(p, mode, tmap, s);
+  return nt256::launch_move<T>(p, mode, tmap, s);
 }
 
 template <typename T>
 cudaError_t launch_batch(int nt, const Params* d_plist, const BatchArgs& a, int update,
                          size_t bytes, cudaStream_t s) {
-  return nt == 128 ? nt128::launch_batch<T>(d_plist, a, update, bytes, s)
-                   : nt256::launch_batch<T>(d_plist, a, update, bytes, s);
+  if (nt == 128) return nt128::launch_batch<T>(d_plist, a, update, bytes, s);
+  if (nt == 160) return nt160::launch_batch<T>(d_plist, a, update, bytes, s);
+  return nt256::launch_batch<T>(d_plist, a, update, bytes, s);
 }
 
 // Advances the generation counter of every crowd of a batch (after its move launch).
@@ -41,7 +46,9 @@ __global__ void batch_advance_kernel(Params* plist, int n) {
 }
 
 int sweep_ctas_per_sm(const Params& p) {
-  return p.nt == 128 ? nt128::sweep_ctas_per_sm(p) : nt256::sweep_ctas_per_sm(p);
+  if (p.nt == 128) return nt128::sweep_ctas_per_sm(p);
+  if (p.nt == 160) return nt160::sweep_ctas_per_sm(p);
+  return nt256::sweep_ctas_per_sm(p);
 }
 
 int max_smem_optin() {
@@ -308,7 +315,8 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   if (run->n_recompute < 0) return QMC_ERR_INVALID_ARG;
   if (run->staging != QMC_STAGING_AUTO && run->staging != QMC_STAGING_LDG)
     return QMC_ERR_INVALID_ARG;
-  if (run->cta_threads != 0 && run->cta_threads != 128 && run->cta_threads != 256)
+  if (run->cta_threads != 0 && run->cta_threads != 128 && run->cta_threads != 160 &&
+      run->cta_threads != 256)
     return QMC_ERR_INVALID_ARG;
   if (run->engine != QMC_ENGINE_AUTO && run->engine != QMC_ENGINE_SIMT) return QMC_ERR_INVALID_ARG;
   if (sys->n_dn != sys->n_up) return QMC_ERR_UNSUPPORTED;
@@ -361,8 +369,11 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   const bool tma_ok = run->staging == QMC_STAGING_AUTO && p.n_pad <= 256;
   // The tensor-core flush (mixed delayed path, inverse in global memory, n % 4 == 0) adds
   // a 64 KB operand stage unless it can share the stencil buffer.
+  // (its epilogue splits the four TMEM lane quadrants over groups of four warps, and
+  // its operand stages over 128 or 256 threads)
   const bool tc_ok = run->engine == QMC_ENGINE_AUTO && run->precision == QMC_PREC_MIXED &&
-                     run->update == QMC_UPDATE_DELAYED && n % 4 == 0;
+                     run->update == QMC_UPDATE_DELAYED && n % 4 == 0 &&
+                     (p.nt == 128 || p.nt == 256);
   const int plans[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   size_t smem = 0;
   bool placed = false;

@@ -41,7 +41,7 @@ struct Params {
   int K2, K1;               // free radial coefficients (0 = term absent)
   int b_in_smem;            // inverse of the moving spin staged in shared memory
   int skip_eloc;            // sweep without the local energy (a recompute comes first)
-  int nt;                   // threads per CTA of the move kernel: 128 or 256
+  int nt;                   // threads per CTA of the move kernel: 128, 160 or 256
   int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
   int eloc_by_gen;          // E_L of generation g goes to eloc_out[(g - eloc_gen0) W + w]
@@ -108,6 +108,7 @@ struct BatchArgs {
   int sweep_ctas_per_sm(const Params& p);                                               \
   }
 QMCGB_DECLARE_MOVE_WIDTH(nt128)
+QMCGB_DECLARE_MOVE_WIDTH(nt160)
 QMCGB_DECLARE_MOVE_WIDTH(nt256)
 #undef QMCGB_DECLARE_MOVE_WIDTH
 template <typename T>

@@ -14,12 +14,12 @@
 // reduction, so the move needs three barriers plus one per accepted move; the FP64 path,
 // where GB300's FP64 rate makes redundant scalar work expensive, lets thread 0 do it.
 //
-// This file is the kernel's implementation, compiled once per CTA width: a translation
-// unit defines QMCGB_MOVE_NT (threads per CTA) and QMCGB_MOVE_NS (the namespace of that
-// width) and includes it.  Narrow CTAs suit small determinants: a move is a chain of short
+// This file is the kernel's implementation, compiled once per CTA width and precision: a
+// translation unit defines QMCGB_MOVE_NT (threads per CTA), QMCGB_MOVE_NS (the namespace
+// of that width) and QMCGB_MOVE_ELEM (4: the mixed path, 8: the FP64 path) and includes it.  Narrow CTAs suit small determinants: a move is a chain of short
 // block reductions, and fewer warps make each barrier and each reduction cheaper.
-#ifndef QMCGB_MOVE_NT
-#error "define QMCGB_MOVE_NT and QMCGB_MOVE_NS before including qmc_move_impl.cuh"
+#if !defined(QMCGB_MOVE_NT) || !defined(QMCGB_MOVE_ELEM)
+#error "define QMCGB_MOVE_NT, QMCGB_MOVE_NS and QMCGB_MOVE_ELEM before including qmc_move_impl.cuh"
 #endif
 #include <cuda.h>
 
@@ -154,9 +154,11 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   return L;
 }
 
+#if QMCGB_MOVE_ELEM == 4  // host functions shared by both precisions: in the FP32 unit
 size_t move_smem_bytes(const Params& p, int elem_bytes) {
   return elem_bytes == 4 ? make_lay<float>(p).total : make_lay<double>(p).total;
 }
+#endif
 
 template <typename T>
 struct Ctx {
@@ -1595,6 +1597,7 @@ cudaError_t launch_move(const Params& p_in, int mode, const void* tmap, cudaStre
   }
 }
 
+#if QMCGB_MOVE_ELEM == 4
 // Resident CTAs per SM of the mixed delayed sweep with the inverse in global memory (the
 // kernel that may hold TMEM), at the crowd's dynamic shared memory.
 int sweep_ctas_per_sm(const Params& p_in) {
@@ -1613,6 +1616,7 @@ int sweep_ctas_per_sm(const Params& p_in) {
   }
   return nb;
 }
+#endif
 
 template <typename T, int UPD>
 static cudaError_t launch_batch_upd(const Params* d_plist, const BatchArgs& a, size_t bytes,
@@ -1642,13 +1646,17 @@ cudaError_t launch_batch(const Params* d_plist, const BatchArgs& a, int update, 
                      : launch_batch_upd<T, 0>(d_plist, a, bytes, s);
 }
 
+// one precision per translation unit (QMCGB_MOVE_ELEM = 4 or 8), so the units compile in
+// parallel
+#if QMCGB_MOVE_ELEM == 4
 template cudaError_t launch_batch<float>(const Params*, const BatchArgs&, int, size_t,
                                          cudaStream_t);
+template cudaError_t launch_move<float>(const Params&, int, const void*, cudaStream_t);
+#else
 template cudaError_t launch_batch<double>(const Params*, const BatchArgs&, int, size_t,
                                           cudaStream_t);
-
 template cudaError_t launch_move<double>(const Params&, int, const void*, cudaStream_t);
-template cudaError_t launch_move<float>(const Params&, int, const void*, cudaStream_t);
+#endif
 
 }  // namespace QMCGB_MOVE_NS
 }  // namespace qmcgb

@@ -1,0 +1,6 @@
+// The particle-by-particle move kernel for CTAs of 128 threads, FP64 path
+// (qmc_move_impl.cuh).
+#define QMCGB_MOVE_NT 128
+#define QMCGB_MOVE_NS nt128
+#define QMCGB_MOVE_ELEM 8
+#include "qmc_move_impl.cuh"

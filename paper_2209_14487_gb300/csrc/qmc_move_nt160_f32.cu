@@ -1,0 +1,6 @@
+// The particle-by-particle move kernel for CTAs of 160 threads, mixed path
+// (qmc_move_impl.cuh).
+#define QMCGB_MOVE_NT 160
+#define QMCGB_MOVE_NS nt160
+#define QMCGB_MOVE_ELEM 4
+#include "qmc_move_impl.cuh"

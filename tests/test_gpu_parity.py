@@ -47,7 +47,7 @@ def _ragged():
                                 n_ions=5, L=5.3, tau=0.4, j1_knots=7, j2_knots=9)
 
 
-@pytest.mark.parametrize("nt", [128, 256])
+@pytest.mark.parametrize("nt", [128, 160, 256])
 @pytest.mark.parametrize("make", [wl_mod.pw16, _ragged])
 def test_fp64_propose_accept_sequence(Q, oracle_lib, make, nt):
     wl = make()
@@ -110,7 +110,7 @@ def test_fp64_delayed_update_matches_oracle(Q, oracle_lib, k, nt):
             assert np.allclose(inv[w], orc.inverse(w, s), rtol=1e-9, atol=1e-10)
 
 
-@pytest.mark.parametrize("nt", [128, 256])
+@pytest.mark.parametrize("nt", [128, 160, 256])
 @pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 4)])
 def test_fp64_sweep_trajectory_matches_oracle(Q, oracle_lib, update, k, nt):
     """Internal counter-based RNG on both sides: identical proposals and decisions up to
@@ -239,12 +239,13 @@ def test_full_size_pw128_sampled_walkers(Q, oracle_lib):
         assert abs(e[-1, w] - e_ref) < 1e-9 * max(1, abs(e_ref))
 
 
-@pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 16)])
-def test_full_size_pw128_mixed_sampled_walkers(Q, oracle_lib, update, k):
+@pytest.mark.parametrize("update,k,nt", [("sm", 1, 128), ("sm", 1, 160), ("delayed", 16, 0)])
+def test_full_size_pw128_mixed_sampled_walkers(Q, oracle_lib, update, k, nt):
     """Bench configuration in the mixed path: sampled walkers agree with the oracle's
     FP64 recompute at the GPU's positions."""
     wl = wl_mod.pw128()
-    gpu = Q.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k)
+    gpu = Q.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
+                                cta_threads=nt)
     gpu.qmc_load_positions(np.ascontiguousarray(wl.positions()))
     gpu.qmc_recompute()
     e = np.zeros((2, wl.n_walkers))
