@@ -81,6 +81,8 @@ struct qmc_crowd {
   void* d_win_V = nullptr;
   void* d_win_S = nullptr;
   void* d_pend_phi = nullptr;
+  void* d_jgl = nullptr;        // [W][N][4] incremental Jastrow grad/lap, carried over sweeps
+  int* d_jvalid = nullptr;      // [W]
   double* d_pend = nullptr;
   double* d_ws = nullptr;
   double* d_eloc = nullptr;     // [eloc_cap][W]
@@ -132,7 +134,7 @@ void free_all(qmc_crowd* c) {
   void* ptrs[] = {c->d_R, c->d_rows, c->d_binv, c->d_logdet, c->d_sign, c->d_table,
                   c->d_jc, c->d_ions, c->d_win_m, c->d_win_P, c->d_win_V, c->d_win_S,
                   c->d_pend_phi, c->d_pend, c->d_ws, c->d_eloc, c->d_nacc, c->d_status,
-                  c->d_io, c->d_io8};
+                  c->d_io, c->d_io8, c->d_jgl, c->d_jvalid};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -152,6 +154,8 @@ void sync_params(qmc_crowd* c) {
   p.win_V = c->d_win_V;
   p.win_S = c->d_win_S;
   p.pend_phi = c->d_pend_phi;
+  p.jgl = c->d_jgl;
+  p.jvalid = c->d_jvalid;
   p.pend = c->d_pend;
   p.status = c->d_status;
   p.n_accept = c->d_nacc;
@@ -259,6 +263,7 @@ int rebuild(qmc_crowd* c) {
   if (st) return st;
   CK(cudaMemsetAsync(c->d_pend, 0, sizeof(double) * c->run.n_walkers * qmcgb::PEND_STRIDE,
                      c->stream));
+  CK(cudaMemsetAsync(c->d_jvalid, 0, sizeof(int) * c->run.n_walkers, c->stream));
   c->stale = false;
   return QMC_OK;
 }
@@ -343,6 +348,9 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.n = n;
   p.n_pad = (n + 7) & ~7;
   p.nt = run->cta_threads ? run->cta_threads : (n <= 128 ? 128 : 256);
+  // incremental Jastrow gradients and Laplacians in the mixed Sherman-Morrison sweep
+  p.inc_jastrow = (run->precision == QMC_PREC_MIXED && run->update == QMC_UPDATE_SM &&
+                   n <= p.nt) ? 1 : 0;
   p.n_ions = sys->n_ions;
   p.G = sys->grid;
   p.GP = sys->grid + 3;
@@ -434,6 +442,8 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     st |= dmalloc(&c->d_win_S, (size_t)es * W * 2 * p.k * p.ks);
   }
   st |= dmalloc(&c->d_pend_phi, (size_t)es * W * 5 * p.n_pad);
+  st |= dmalloc(&c->d_jgl, (size_t)es * W * N * 4);
+  st |= dmalloc((void**)&c->d_jvalid, sizeof(int) * W);
   st |= dmalloc((void**)&c->d_pend, sizeof(double) * W * qmcgb::PEND_STRIDE);
   st |= dmalloc((void**)&c->d_ws, sizeof(double) * W * 2 * 2 * n * n);
   st |= dmalloc((void**)&c->d_nacc, sizeof(unsigned long long));
@@ -447,6 +457,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     return QMC_ERR_OOM;
   }
   cudaMemsetAsync(c->d_win_m, 0, sizeof(int) * W * 2, c->stream);
+  cudaMemsetAsync(c->d_jvalid, 0, sizeof(int) * W, c->stream);
   cudaMemsetAsync(c->d_pend, 0, sizeof(double) * W * qmcgb::PEND_STRIDE, c->stream);
   cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), c->stream);
   cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);

@@ -300,6 +300,27 @@ __device__ __forceinline__ void block_allreduce8(R* v, R* red) {
   for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
 }
 
+// Sixteen values summed over a CTA of NW warps, every thread receives all totals (one
+// barrier).  `red` holds NW * 16 values.
+template <int NW, typename R>
+__device__ __forceinline__ void block_allreduce16(R* v, R* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const R c0 = warp_sum8_transposed(v);
+  const R c1 = warp_sum8_transposed(v + 8);
+  if ((lane & 3) == 0) {
+    red[warp * 16 + (lane >> 2)] = c0;
+    red[warp * 16 + 8 + (lane >> 2)] = c1;
+  }
+  __syncthreads();
+  R t = R(0);
+  if (lane < 16) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t += red[w * 16 + lane];
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __shfl_sync(0xffffffffu, t, q);
+}
+
 // ---------------------------------------------------------------------------------------
 // TMA and mbarrier helpers (inline PTX, sm_90+ forms available on sm_103a).
 // ---------------------------------------------------------------------------------------

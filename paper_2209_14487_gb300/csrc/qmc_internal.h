@@ -44,6 +44,7 @@ struct Params {
   int nt;                   // threads per CTA of the move kernel: 128, 160 or 256
   int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
+  int inc_jastrow;          // mixed Sherman-Morrison sweep: incremental Jastrow grad/lap
   int eloc_by_gen;          // E_L of generation g goes to eloc_out[(g - eloc_gen0) W + w]
   uint32_t eloc_gen0;
   int stencil_bytes;        // bytes of that copy
@@ -66,6 +67,8 @@ struct Params {
   void* win_V;              // [W][2][k][vs] T
   void* win_S;              // [W][2][k][ks] T  (S^-1)
   void* pend_phi;           // [W][5][n_pad] T
+  void* jgl;                // [W][N][4] T: Jastrow grad U (3) and lap U of every electron
+  int* jvalid;              // [W]: jgl holds the walker's current values
   double* pend;             // [W][PEND_STRIDE]
   int iel;
   const double* rnew_in;    // [W][3] or null

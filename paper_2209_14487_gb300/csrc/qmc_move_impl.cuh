@@ -96,7 +96,7 @@ __device__ __forceinline__ Cst<T> make_cst(const Params& p) {
 }
 
 struct Lay {
-  size_t scal, bar, stc, tcs, B, R, Rq, ion, ionq, jc, phi, part, col, dchi, du, red0, red1;
+  size_t scal, bar, stc, tcs, B, R, Rq, ion, ionq, jc, jgl, phi, part, col, dchi, du, red0, red1;
   size_t wP, wV, wS, wy, wz, wc, wb, snap, xb, yb, total;
 };
 
@@ -130,6 +130,7 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.ion = o; o += al16((size_t)p.n_ions * 3 * 8);
   L.ionq = o; o += al16((size_t)p.n_ions * 3 * 4);
   L.jc = o; o += al16((size_t)3 * (MAX_KNOTS + 3) * es);  // any Jastrow the crowd loads later
+  L.jgl = o; o += p.inc_jastrow ? al16((size_t)p.N * 4 * es) : 0;
   L.phi = o; o += al16((size_t)5 * p.n_pad * es);
   L.part = o; o += al16((size_t)16 * p.n_pad * es);
   L.col = o; o += al16((size_t)p.n_pad * es);
@@ -177,6 +178,7 @@ struct Ctx {
   double* ion;
   uint32_t* ionq;
   T* jc;
+  T* jgl;   // incremental sweep: grad U (3) and lap U of every electron [N][4]
   T* phi;
   T* part;
   T* col;
@@ -1175,6 +1177,315 @@ __device__ double local_energy(Ctx<T>& c) {
   return v2[0] + v2[1];  // meaningful on thread 0
 }
 
+// ---------------------------------------------------------------------------------------
+// Incremental Jastrow (mixed Sherman-Morrison sweep).  c.jgl[i] holds grad_i U and lap_i U
+// of every electron at the current positions; an accepted move of electron i replaces
+// c.jgl[i] by the values at r' (summed afresh over all partners in the ratio) and adds
+// each electron partner's change of its pair term.  The drift then needs no Jastrow pass,
+// and E_L no pair derivatives.  Between sweeps the values stay in global memory (p.jgl,
+// valid while p.jvalid[w] is set: a recompute, new positions or a fine-grained accept
+// clear it); every electron's entry is recomputed whenever its own move is accepted.
+// ---------------------------------------------------------------------------------------
+
+// grad U and lap U of every electron over all partners (one warp per electron).
+template <typename T>
+__device__ void jastrow_gl_all(Ctx<T>& c) {
+  const Params& p = c.p;
+  const int N = p.N, NI = p.n_ions;
+  for (int i = c.warp; i < N; i += NWARP) {
+    T g0 = 0, g1 = 0, g2 = 0, l = 0;
+    for (int t = c.lane; t < N + NI; t += 32) {
+      const bool jas = t < N ? p.K2 > 0 : p.K1 > 0;
+      if (t == i || !jas) continue;
+      T d[3], r, rinv;
+      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r, rinv);
+      if (r > T(0)) {
+        const T* coef; int K; T hinv, rc;
+        functor(c, i, t, coef, K, hinv, rc);
+        T u, du, d2u;
+        radial(coef, K, hinv, rc, r, u, du, d2u);
+        const T f = du * rinv;
+        g0 += f * d[0];
+        g1 += f * d[1];
+        g2 += f * d[2];
+        l += d2u + T(2) * f;
+      }
+    }
+    g0 = warp_sum(g0);
+    g1 = warp_sum(g1);
+    g2 = warp_sum(g2);
+    l = warp_sum(l);
+    if (c.lane == 0) {
+      c.jgl[4 * i] = g0;
+      c.jgl[4 * i + 1] = g1;
+      c.jgl[4 * i + 2] = g2;
+      c.jgl[4 * i + 3] = l;
+    }
+  }
+}
+
+// Determinant part of electron i's drift, dA_i . B[:,p] (col), by one all-reduce.
+template <typename T>
+__device__ void det_grad(Ctx<T>& c, int i, T* det) {
+  const int n = c.p.n, n_pad = c.p.n_pad;
+  T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const T* rw = c.rows + (size_t)i * 5 * n_pad;
+  for (int j = c.tid; j < n; j += NT) {
+    const T cj = c.col[j];
+    v[0] += rw[n_pad + j] * cj;
+    v[1] += rw[2 * n_pad + j] * cj;
+    v[2] += rw[3 * n_pad + j] * cj;
+  }
+  block_allreduce8<NWARP>(v, c.red0);
+  det[0] = v[0];
+  det[1] = v[1];
+  det[2] = v[2];
+}
+
+// What a move leaves for the accept and the next electron's drift (incremental sweep).
+template <typename T>
+struct IncOut {
+  T dg[JT][4];    // per cached partner slot: change of the partner's grad U (3) and lap U
+  T g[4];         // grad U and lap U of the moving electron at r'
+  T a[3], b[3];   // dA_{i+1} . B[:,p+1] and dA_{i+1} . B[:,p]
+  T e;            // phi' . B[:,p+1]
+};
+
+// The ratio of the incremental sweep: as ratio_grad, with u, u', u'' of every partner
+// term at r and at r' (no cached u(r)), the moving electron's fresh grad U and lap U at
+// r', the partner changes for an accept, and, when `nxt`, the sums a, b, e from which the
+// next electron's determinant drift follows after this move (`pf`: that electron's dA
+// entries for orbital j = tid).  False when the stencil copy timed out (uniform).
+template <typename T>
+__device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& rs, bool nxt,
+                          const T* pf, IncOut<T>& io) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad, GP = p.GP;
+  const T* table = (const T*)p.table;
+  T cf[16];
+  const bool tma = p.use_tma;
+  if (tma) {
+    if (c.tid == 0) {  // the whole 4x4x4 x n_pad stencil in one copy
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(c.bar, (uint32_t)p.stencil_bytes);
+      tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
+    }
+  } else if (c.nit > 0) {
+    stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[0], c.ita[0], cf);
+  }
+  T wreg[36];
+  basis12(pr.t[1], wreg + 12);
+  basis12(pr.t[2], wreg + 24);
+  T v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = T(0);
+  int t0, t1;
+  term_range(p, t0, t1);
+#pragma unroll
+  for (int q = 0; q < JT; ++q) {
+    io.dg[q][0] = io.dg[q][1] = io.dg[q][2] = io.dg[q][3] = T(0);
+    if (t0 + q * NT < t1) {  // slot q has partners for some thread (uniform)
+      const int tq = t0 + c.tid + q * NT;
+      const bool use = tq < t1 && tq != i;
+      const int t = tq < t1 ? tq : t1 - 1;
+      T dn[3], rn, rninv, dol[3], ro, roinv;
+      partner_disp(c, pr.rp, pr.rq, t, dn, rn, rninv);
+      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro, roinv);
+      const T* coef; int K; T hinv, rc;
+      functor(c, i, t, coef, K, hinv, rc);
+      T un, dun, d2n, uo, duo, d2o;
+      radial(coef, K, hinv, rc, rn, un, dun, d2n);
+      radial(coef, K, hinv, rc, ro, uo, duo, d2o);
+      const bool un_ok = use && rn > T(0), uo_ok = use && ro > T(0);
+      const T fn = un_ok ? dun * rninv : T(0), fo = uo_ok ? duo * roinv : T(0);
+      const T ln = un_ok ? d2n + T(2) * fn : T(0), lo = uo_ok ? d2o + T(2) * fo : T(0);
+      v[4] += use ? un - uo : T(0);
+      v[5] += fn * dn[0];
+      v[6] += fn * dn[1];
+      v[7] += fn * dn[2];
+      v[8] += ln;
+      // partner t's pair term: grad_t u = -(u'/r) d, lap_t u = u'' + 2 u'/r
+      io.dg[q][0] = fo * dol[0] - fn * dn[0];
+      io.dg[q][1] = fo * dol[1] - fn * dn[1];
+      io.dg[q][2] = fo * dol[2] - fn * dn[2];
+      io.dg[q][3] = ln - lo;
+    }
+  }
+  const T* wts = wreg;
+  bool ok = true;
+  if (tma) {
+    ok = mbar_wait_bounded(c.bar, c.tma_phase);
+    c.tma_phase ^= 1u;
+  }
+  if (tma && c.nit >= 2) {
+    T cg[16];
+    const T* sa = c.stc + (size_t)(c.ita[0] * 16) * n_pad + c.itj[0];
+    const T* sb = c.stc + (size_t)(c.ita[1] * 16) * n_pad + c.itj[1];
+#pragma unroll
+    for (int bc = 0; bc < 16; ++bc) {
+      cf[bc] = sa[(size_t)bc * n_pad];
+      cg[bc] = sb[(size_t)bc * n_pad];
+    }
+    T o4[4], o4b[4];
+    stencil_reduce(cf, wts, o4);
+    stencil_reduce(cg, wts, o4b);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      c.part[(c.ita[0] * 4 + r) * n_pad + c.itj[0]] = o4[r];
+      c.part[(c.ita[1] * 4 + r) * n_pad + c.itj[1]] = o4b[r];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < c.nit && !(tma && c.nit >= 2 && q < 2)) {
+      if (tma) {
+        const T* sb = c.stc + (size_t)(c.ita[q] * 16) * n_pad + c.itj[q];
+#pragma unroll
+        for (int bc = 0; bc < 16; ++bc) cf[bc] = sb[(size_t)bc * n_pad];
+      } else if (q > 0) {
+        stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[q], c.ita[q], cf);
+      }
+      T o4[4];
+      stencil_reduce(cf, wts, o4);
+      const int j = c.itj[q], a = c.ita[q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
+    }
+  }
+  for (int it = c.tid + 4 * NT; it < 4 * n; it += NT) {  // items beyond four per thread
+    const int j = it % n, a = it / n;
+    if (tma) {
+      const T* sb = c.stc + (size_t)(a * 16) * n_pad + j;
+      for (int bc = 0; bc < 16; ++bc) cf[bc] = sb[(size_t)bc * n_pad];
+    } else {
+      stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], j, a, cf);
+    }
+    T o4[4];
+    stencil_reduce(cf, wts, o4);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
+  }
+  if (tma) {
+    if (__syncthreads_or(!ok)) {
+      if (c.tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      if (!ok) mbar_wait_bounded(c.bar, c.tma_phase ^ 1u);
+      return false;
+    }
+  } else {
+    __syncthreads();
+  }
+  const T dinv = c.k.dgrid;
+  const T* bnext = c.B + (size_t)(pp + 1) * c.bs;  // read only when nxt (pp + 1 < n)
+  for (int j = c.tid; j < n; j += NT) {  // n <= NT on this path: j == tid
+    T wx[12];
+    basis12(pr.t[0], wx);
+    T o5[5];
+    stencil_combine(c.part, n_pad, j, wx, dinv, o5);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) c.phi[q * n_pad + j] = o5[q];
+    const T cj = c.col[j];
+    v[0] += o5[0] * cj;
+    v[1] += o5[1] * cj;
+    v[2] += o5[2] * cj;
+    v[3] += o5[3] * cj;
+    if (nxt) {
+      const T bn = bnext[j];
+      v[9] += pf[0] * bn;
+      v[10] += pf[1] * bn;
+      v[11] += pf[2] * bn;
+      v[12] += pf[0] * cj;
+      v[13] += pf[1] * cj;
+      v[14] += pf[2] * cj;
+      v[15] += o5[0] * bn;
+    }
+  }
+  block_allreduce16<NWARP>(v, c.red1);
+  rs.rhoD = v[0];
+  rs.dU = v[4];
+  rs.rho = v[0] * __expf(-v[4]);
+  const T ir = T(1) / v[0];
+  for (int k = 0; k < 3; ++k) rs.Fp[k] = v[1 + k] * ir - v[5 + k];
+  io.g[0] = v[5];
+  io.g[1] = v[6];
+  io.g[2] = v[7];
+  io.g[3] = v[8];
+  for (int k = 0; k < 3; ++k) {
+    io.a[k] = v[9 + k];
+    io.b[k] = v[12 + k];
+  }
+  io.e = v[15];
+  return true;
+}
+
+// Accepted move of electron i: partners' accumulators change by their pair term's
+// difference, the electron's own become the fresh sums at r' (the caller's barrier in
+// the inverse update publishes them).
+template <typename T>
+__device__ __forceinline__ void accept_inc(Ctx<T>& c, int i, const IncOut<T>& io) {
+  const Params& p = c.p;
+  int t0, t1;
+  term_range(p, t0, t1);
+#pragma unroll
+  for (int q = 0; q < JT; ++q) {
+    const int t = t0 + c.tid + q * NT;
+    if (t0 + q * NT < t1 && t < t1 && t < p.N && t != i) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c.jgl[4 * t + k] += io.dg[q][k];
+    }
+  }
+  if (c.tid == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.jgl[4 * i + k] = io.g[k];
+  }
+}
+
+// E_L of the incremental sweep: the Jastrow derivatives come from c.jgl; the determinant
+// part and the potential as in local_energy.
+template <typename T>
+__device__ double local_energy_inc(Ctx<T>& c) {
+  const Params& p = c.p;
+  const int N = p.N, n = p.n, n_pad = p.n_pad, NI = p.n_ions;
+  double kin = 0.0;
+  T pot = 0;
+  for (int i = c.warp; i < N; i += NWARP) {
+    T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int s = i < p.n_up ? 0 : 1;
+    const int pp = i - s * p.n_up;
+    const T* brow = c.Bg + ((size_t)s * n + pp) * n;
+    const T* rw = c.rows + (size_t)i * 5 * n_pad;
+    for (int j = c.lane; j < n; j += 32) {
+      const T b = brow[j];
+      v[4] += rw[n_pad + j] * b;
+      v[5] += rw[2 * n_pad + j] * b;
+      v[6] += rw[3 * n_pad + j] * b;
+      v[7] += rw[4 * n_pad + j] * b;
+    }
+    if (p.potential) {
+      for (int t = c.lane; t < N + NI; t += 32) {
+        if (t == i || (t < N && t < i)) continue;  // each electron pair once
+        T d[3], r, rinv;
+        partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r, rinv);
+        if (r < c.k.halfL) pot += t < N ? exp(-r * r) : T(-2) * exp(T(-0.5) * r * r);
+      }
+    }
+    const T t8 = warp_sum8_transposed(v);  // lane 4q holds the total of value q
+#pragma unroll
+    for (int q = 4; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t8, 4 * q);
+    if (c.lane == 0) {
+      T gd2 = 0, gg = 0;
+      for (int k = 0; k < 3; ++k) {
+        gd2 += v[4 + k] * v[4 + k];
+        const T g = v[4 + k] - c.jgl[4 * i + k];
+        gg += g * g;
+      }
+      kin += (double)(T(-0.5) * ((v[7] - gd2) - c.jgl[4 * i + 3] + gg));
+    }
+  }
+  double v2[2] = {kin, (double)pot};
+  block_sum_to0<NWARP, 2>(v2, (double*)c.red0);
+  return v2[0] + v2[1];  // meaningful on thread 0
+}
+
 template <typename T>
 __device__ __forceinline__ void prefetch_grad_rows(const Ctx<T>& c, int i, T* pf) {
   if (i < c.p.N && c.tid < c.p.n) {
@@ -1230,6 +1541,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
   c.ion = (double*)(smem + lay.ion);
   c.ionq = (uint32_t*)(smem + lay.ionq);
   c.jc = (T*)(smem + lay.jc);
+  c.jgl = (T*)(smem + lay.jgl);
   c.phi = (T*)(smem + lay.phi);
   c.part = (T*)(smem + lay.part);
   c.col = (T*)(smem + lay.col);
@@ -1325,13 +1637,58 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     }
     T pf[3] = {0, 0, 0};
     if (pf_ok) prefetch_grad_rows(c, 0, pf);
+    // incremental Jastrow (mixed Sherman-Morrison): the accumulators come from the previous
+    // sweep when still valid, else from one pass over all pairs
+    bool inc = false;
+    if constexpr (IsMixed<T>::value && UPD == 0)
+      inc = p.inc_jastrow && pf_ok && (t1 - t0) <= JT * NT;
+    if (inc) {
+      if (p.jvalid[w]) {
+        const T* gsrc = (const T*)p.jgl + (size_t)w * N * 4;
+        for (int e = c.tid; e < N * 4; e += NT) c.jgl[e] = gsrc[e];
+      } else {
+        jastrow_gl_all(c);
+      }
+    }
     __syncthreads();
     unsigned long long nacc = 0;
     for (int s = 0; s < 2; ++s) {
       begin_spin(c, s);
+      bool have_det = false;
+      T det[3] = {0, 0, 0};
       for (int pp = 0; pp < n; ++pp) {
         const int i = s * p.n_up + pp;
         compute_column(c, pp);
+        if constexpr (IsMixed<T>::value && UPD == 0) {
+          if (inc) {
+            // drift: determinant part (from the previous move's sums, or one all-reduce at
+            // a spin's first electron) minus the accumulated grad U
+            if (p.drift) {
+              if (!have_det) det_grad(c, i, det);
+              for (int k = 0; k < 3; ++k) F[k] = det[k] - c.jgl[4 * i + k];
+            }
+            const bool nxt = p.drift && pp + 1 < n;
+            if (nxt) prefetch_grad_rows(c, i + 1, pf);
+            shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
+            IncOut<T> io;
+            if (!ratio_inc(c, i, pp, pr, rs, nxt, pf, io)) {
+              c.failed = true;
+              break;
+            }
+            const int acc = metropolis(p, c.k, pr, rs, c.du[i]);
+            nacc += acc;
+            if (acc) {
+              accept_inc(c, i, io);
+              accept_update(c, i, s, pp, pr, rs.rhoD);  // its barriers publish c.jgl
+            }
+            if (nxt) {
+              const T f = acc ? io.e / rs.rhoD : T(0);
+              for (int k = 0; k < 3; ++k) det[k] = io.a[k] - f * io.b[k];
+            }
+            have_det = nxt;
+            continue;
+          }
+        }
         if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
         if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
         shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
@@ -1369,11 +1726,20 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     if (c.failed) return;
     moved = true;
     if (!p.skip_eloc) {
-      const double e = local_energy(c);
+      double e;
+      if constexpr (IsMixed<T>::value && UPD == 0)
+        e = inc ? local_energy_inc(c) : local_energy(c);
+      else
+        e = local_energy(c);
       if (c.tid == 0) {
         if (p.eloc_out) p.eloc_out[eloc_slot(p) + w] = e;
         if (!isfinite(e)) atomicOr(p.status, ST_NAN);
       }
+    }
+    if (inc) {  // carried to the next sweep
+      T* gdst = (T*)p.jgl + (size_t)w * N * 4;
+      for (int e = c.tid; e < N * 4; e += NT) gdst[e] = c.jgl[e];
+      if (c.tid == 0) p.jvalid[w] = 1;
     }
     if (c.tid == 0 && p.n_accept) atomicAdd(p.n_accept, nacc);
   } else if constexpr (MODE == MODE_GRAD || MODE == MODE_PROPOSE) {
@@ -1464,6 +1830,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
       sc->accept = acc;
       if (p.accept_out) p.accept_out[w] = (uint8_t)acc;
       pd[P_VALID] = 0.0;
+      if (p.jvalid) p.jvalid[w] = 0;  // the incremental sweep's accumulators are stale
     }
     __syncthreads();
     if (sc->accept) accept_update(c, i, s, pp, pr, rs.rhoD);

@@ -424,3 +424,34 @@ def test_tensor_core_flush_matches_simt_flush(Q, oracle_lib, nt):
     for w in np.nonzero(same)[0][:2]:
         ref, _ = osys.logpsi(Rt[w])
         assert abs(lt[w] - ref) < 1e-4 * max(1, abs(ref))
+
+
+@pytest.mark.parametrize("nt", [128, 160])
+def test_incremental_jastrow_matches_full_pass(Q, nt):
+    """Mixed Sherman-Morrison sweeps keep every electron's grad U and lap U up to date
+    move by move and carry them from one sweep to the next: E_L after the sweeps equals
+    the fine-grained local energy, which sums all pair terms afresh; a fine-grained accept
+    in between makes the next sweep start from a fresh pass."""
+    wl = wl_mod.pw128()
+    W = 16
+    c = Q.Crowd.from_workload(wl, precision="mixed", update="sm", n_walkers=W, cta_threads=nt,
+                              n_recompute=0)
+    c.qmc_load_positions(np.ascontiguousarray(wl.positions(n_walkers=W)))
+    c.qmc_recompute()
+    e = np.zeros((3, W))
+    c.qmc_sweep(3, e)
+    e2 = np.zeros((2, W))
+    c.qmc_sweep(2, e2)  # starts from the accumulators the first call left
+    ref = np.zeros(W)
+    c.qmc_local_energy_batch(ref)
+    assert np.allclose(e2[-1], ref, rtol=1e-4, atol=1e-3), np.abs(e2[-1] - ref).max()
+    R = c.qmc_get_positions()
+    rng = np.random.default_rng(3)
+    rnew = np.mod(R[:, 5, :] + rng.normal(0, 0.3, size=(W, 3)), wl.L)
+    c.qmc_propose_move_batch(5, np.ascontiguousarray(rnew))
+    c.qmc_accept_reject_batch(5, np.ones(W, dtype=np.uint8))
+    e3 = np.zeros((1, W))
+    c.qmc_sweep(1, e3)
+    ref3 = np.zeros(W)
+    c.qmc_local_energy_batch(ref3)
+    assert np.allclose(e3[0], ref3, rtol=1e-4, atol=1e-3), np.abs(e3[0] - ref3).max()
