@@ -956,8 +956,9 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
   const int n = p.n, n_pad = p.n_pad, bs = c.bs;
   T* rw = c.rows + (size_t)i * 5 * n_pad;
   if (c.upd == 0) {
-    // Sherman-Morrison: v_k = phi'.B^T[k] (one thread per row), then
-    // B^T[k] -= col (v_k - delta_k,pp) / rhoD (one warp per row); f_k reuses `part`.
+    // Sherman-Morrison: v_k = phi'.B^T[k], then B^T[k] -= col (v_k - delta_k,pp) / rhoD:
+    // by row owners (2 or 4 threads per row) in FP32, else one thread per row for v
+    // (f_k in `part`) and one warp per row for the update.
     const T invr = T(1) / rhoD;
     T* fk = c.part;
     // threads per row: 4 or 2 when the CTA covers the rows that way (float4 reads of a
@@ -971,11 +972,15 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
     }
     if (tpr) {
       if constexpr (sizeof(T) == 4) {
+        // row owners: the tpr threads of row k dot phi' with their parts of the row
+        // (float4 reads), combine by shuffles and update the same parts, so the two passes
+        // need no barrier between them
         const int k = c.tid / tpr, qd = c.tid % tpr, nq = n / tpr;  // nq floats per part
+        float4* r4 = reinterpret_cast<float4*>(c.B + (size_t)(k < n ? k : 0) * bs + qd * nq);
+        const float4* p4 = reinterpret_cast<const float4*>(c.phi + qd * nq);
+        const float4* c4 = reinterpret_cast<const float4*>(c.col + qd * nq);
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
         if (k < n) {
-          const float4* r4 = reinterpret_cast<const float4*>(c.B + (size_t)k * bs + qd * nq);
-          const float4* p4 = reinterpret_cast<const float4*>(c.phi + qd * nq);
           for (int q = 0; q < nq / 4; ++q) {
             const float4 b = r4[q], f = p4[q];
             a0 += b.x * f.x;
@@ -987,7 +992,18 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
         float acc = (a0 + a1) + (a2 + a3);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         if (tpr == 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (k < n && qd == 0) fk[k] = (acc - (k == pp ? 1.f : 0.f)) * invr;
+        if (k < n) {
+          const float f = (acc - (k == pp ? 1.f : 0.f)) * invr;
+          for (int q = 0; q < nq / 4; ++q) {
+            float4 b = r4[q];
+            const float4 cv = c4[q];
+            b.x -= cv.x * f;
+            b.y -= cv.y * f;
+            b.z -= cv.z * f;
+            b.w -= cv.w * f;
+            r4[q] = b;
+          }
+        }
       }
     } else {
       for (int k = c.tid; k < n; k += NT) {
@@ -1003,35 +1019,35 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
         for (; j < n; ++j) a0 += row[j] * c.phi[j];
         fk[k] = ((a0 + a1) + (a2 + a3) - (k == pp ? T(1) : T(0))) * invr;
       }
-    }
-    __syncthreads();
-    // B^T[k][j] -= col[j] f_k: each warp takes rows warp, warp + NWARP, ...; four rows at a
-    // time with every load issued before the stores (the compiler cannot prove that the
-    // row, col and f pointers do not alias)
-    for (int k0 = c.warp; k0 < n; k0 += 4 * NWARP) {
-      T f[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int k = k0 + r * NWARP;
-        f[r] = k < n ? fk[k] : T(0);
-      }
-      for (int j0 = 0; j0 < n; j0 += 64) {
-        const int ja = j0 + c.lane, jb = j0 + 32 + c.lane;
-        const T ca = ja < n ? c.col[ja] : T(0), cb = jb < n ? c.col[jb] : T(0);
-        T va[4], vb[4];
+      __syncthreads();
+      // B^T[k][j] -= col[j] f_k: each warp takes rows warp, warp + NWARP, ...; four rows at
+      // a time with every load issued before the stores (the compiler cannot prove that
+      // the row, col and f pointers do not alias)
+      for (int k0 = c.warp; k0 < n; k0 += 4 * NWARP) {
+        T f[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int k = k0 + r * NWARP;
-          const T* row = c.B + (size_t)k * bs;
-          va[r] = (k < n && ja < n) ? row[ja] : T(0);
-          vb[r] = (k < n && jb < n) ? row[jb] : T(0);
+          f[r] = k < n ? fk[k] : T(0);
         }
+        for (int j0 = 0; j0 < n; j0 += 64) {
+          const int ja = j0 + c.lane, jb = j0 + 32 + c.lane;
+          const T ca = ja < n ? c.col[ja] : T(0), cb = jb < n ? c.col[jb] : T(0);
+          T va[4], vb[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int k = k0 + r * NWARP;
-          T* row = c.B + (size_t)k * bs;
-          if (k < n && ja < n) row[ja] = va[r] - ca * f[r];
-          if (k < n && jb < n) row[jb] = vb[r] - cb * f[r];
+          for (int r = 0; r < 4; ++r) {
+            const int k = k0 + r * NWARP;
+            const T* row = c.B + (size_t)k * bs;
+            va[r] = (k < n && ja < n) ? row[ja] : T(0);
+            vb[r] = (k < n && jb < n) ? row[jb] : T(0);
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int k = k0 + r * NWARP;
+            T* row = c.B + (size_t)k * bs;
+            if (k < n && ja < n) row[ja] = va[r] - ca * f[r];
+            if (k < n && jb < n) row[jb] = vb[r] - cb * f[r];
+          }
         }
       }
     }
