@@ -1455,46 +1455,75 @@ __device__ __forceinline__ void accept_inc(Ctx<T>& c, int i, const IncOut<T>& io
   }
 }
 
-// E_L of the incremental sweep: the Jastrow derivatives come from c.jgl; the determinant
-// part and the potential as in local_energy.
+// E_L of the incremental sweep.  The Jastrow derivatives come from c.jgl, so what is left
+// is independent per electron: one thread per electron forms its determinant gradient and
+// Laplacian (four dots with its rows and the inverse column, float4 reads when aligned);
+// the potential's electron pairs are split evenly, two threads per folded row of the pair
+// triangle (row r holds (r, col + 1) for col >= r and (N - 1 - r, N - 1 - col) for
+// col < r), and every thread takes its electron's ion terms.  FP64 accumulation.
 template <typename T>
 __device__ double local_energy_inc(Ctx<T>& c) {
   const Params& p = c.p;
   const int N = p.N, n = p.n, n_pad = p.n_pad, NI = p.n_ions;
   double kin = 0.0;
   T pot = 0;
-  for (int i = c.warp; i < N; i += NWARP) {
-    T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const bool vec = (n % 4 == 0) && (n_pad % 4 == 0);
+  for (int i = c.tid; i < N; i += NT) {
     const int s = i < p.n_up ? 0 : 1;
     const int pp = i - s * p.n_up;
     const T* brow = c.Bg + ((size_t)s * n + pp) * n;
     const T* rw = c.rows + (size_t)i * 5 * n_pad;
-    for (int j = c.lane; j < n; j += 32) {
-      const T b = brow[j];
-      v[4] += rw[n_pad + j] * b;
-      v[5] += rw[2 * n_pad + j] * b;
-      v[6] += rw[3 * n_pad + j] * b;
-      v[7] += rw[4 * n_pad + j] * b;
+    T gx = 0, gy = 0, gz = 0, l = 0;
+    if constexpr (sizeof(T) == 4) {
+      if (vec) {
+        const float4* b4 = reinterpret_cast<const float4*>(brow);
+        const float4* x4 = reinterpret_cast<const float4*>(rw + n_pad);
+        const float4* y4 = reinterpret_cast<const float4*>(rw + 2 * n_pad);
+        const float4* z4 = reinterpret_cast<const float4*>(rw + 3 * n_pad);
+        const float4* l4 = reinterpret_cast<const float4*>(rw + 4 * n_pad);
+        for (int q = 0; q < n / 4; ++q) {
+          const float4 b = b4[q], x = x4[q], y = y4[q], z = z4[q], w = l4[q];
+          gx += x.x * b.x + x.y * b.y + x.z * b.z + x.w * b.w;
+          gy += y.x * b.x + y.y * b.y + y.z * b.z + y.w * b.w;
+          gz += z.x * b.x + z.y * b.y + z.z * b.z + z.w * b.w;
+          l += w.x * b.x + w.y * b.y + w.z * b.z + w.w * b.w;
+        }
+      }
     }
+    if (!(sizeof(T) == 4 && vec)) {
+      for (int j = 0; j < n; ++j) {
+        const T b = brow[j];
+        gx += rw[n_pad + j] * b;
+        gy += rw[2 * n_pad + j] * b;
+        gz += rw[3 * n_pad + j] * b;
+        l += rw[4 * n_pad + j] * b;
+      }
+    }
+    const T ux = c.jgl[4 * i], uy = c.jgl[4 * i + 1], uz = c.jgl[4 * i + 2];
+    const T gd2 = gx * gx + gy * gy + gz * gz;
+    const T gg = (gx - ux) * (gx - ux) + (gy - uy) * (gy - uy) + (gz - uz) * (gz - uz);
+    kin += (double)(T(-0.5) * ((l - gd2) - c.jgl[4 * i + 3] + gg));
     if (p.potential) {
-      for (int t = c.lane; t < N + NI; t += 32) {
-        if (t == i || (t < N && t < i)) continue;  // each electron pair once
+      for (int t = N; t < N + NI; ++t) {
         T d[3], r, rinv;
         partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, r, rinv);
-        if (r < c.k.halfL) pot += t < N ? exp(-r * r) : T(-2) * exp(T(-0.5) * r * r);
+        if (r < c.k.halfL) pot += T(-2) * exp(T(-0.5) * r * r);
       }
     }
-    const T t8 = warp_sum8_transposed(v);  // lane 4q holds the total of value q
-#pragma unroll
-    for (int q = 4; q < 8; ++q) v[q] = __shfl_sync(0xffffffffu, t8, 4 * q);
-    if (c.lane == 0) {
-      T gd2 = 0, gg = 0;
-      for (int k = 0; k < 3; ++k) {
-        gd2 += v[4 + k] * v[4 + k];
-        const T g = v[4 + k] - c.jgl[4 * i + k];
-        gg += g * g;
+  }
+  if (p.potential && N >= 2) {
+    const int half = (N - 1) / 2;
+    for (int u = c.tid; u < 2 * (N / 2); u += NT) {
+      const int r = u >> 1;
+      const int c0 = (u & 1) ? half : 0, c1 = (u & 1) ? N - 1 : half;
+      for (int col = c0; col < c1; ++col) {
+        const bool first = col >= r;
+        const int i = first ? r : N - 1 - r;
+        const int t = first ? col + 1 : N - 1 - col;
+        T d[3], rr, rinv;
+        partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, d, rr, rinv);
+        if (rr < c.k.halfL) pot += exp(-rr * rr);
       }
-      kin += (double)(T(-0.5) * ((v[7] - gd2) - c.jgl[4 * i + 3] + gg));
     }
   }
   double v2[2] = {kin, (double)pot};
