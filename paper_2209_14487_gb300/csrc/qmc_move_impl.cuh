@@ -1297,35 +1297,44 @@ __device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& r
   for (int q = 0; q < 16; ++q) v[q] = T(0);
   int t0, t1;
   term_range(p, t0, t1);
+  // partner slot q of this thread: t = t0 + tid + q NT
+  auto slot = [&](int q) {
+    const int tq = t0 + c.tid + q * NT;
+    const bool use = tq < t1 && tq != i;
+    const int t = tq < t1 ? tq : t1 - 1;
+    T dn[3], rn, rninv, dol[3], ro, roinv;
+    partner_disp(c, pr.rp, pr.rq, t, dn, rn, rninv);
+    partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro, roinv);
+    const T* coef; int K; T hinv, rc;
+    functor(c, i, t, coef, K, hinv, rc);
+    T un, dun, d2n, uo, duo, d2o;
+    radial(coef, K, hinv, rc, rn, un, dun, d2n);
+    radial(coef, K, hinv, rc, ro, uo, duo, d2o);
+    const bool un_ok = use && rn > T(0), uo_ok = use && ro > T(0);
+    const T fn = un_ok ? dun * rninv : T(0), fo = uo_ok ? duo * roinv : T(0);
+    const T ln = un_ok ? d2n + T(2) * fn : T(0), lo = uo_ok ? d2o + T(2) * fo : T(0);
+    v[4] += use ? un - uo : T(0);
+    v[5] += fn * dn[0];
+    v[6] += fn * dn[1];
+    v[7] += fn * dn[2];
+    v[8] += ln;
+    // partner t's pair term: grad_t u = -(u'/r) d, lap_t u = u'' + 2 u'/r
+    io.dg[q][0] = fo * dol[0] - fn * dn[0];
+    io.dg[q][1] = fo * dol[1] - fn * dn[1];
+    io.dg[q][2] = fo * dol[2] - fn * dn[2];
+    io.dg[q][3] = ln - lo;
+  };
 #pragma unroll
-  for (int q = 0; q < JT; ++q) {
-    io.dg[q][0] = io.dg[q][1] = io.dg[q][2] = io.dg[q][3] = T(0);
-    if (t0 + q * NT < t1) {  // slot q has partners for some thread (uniform)
-      const int tq = t0 + c.tid + q * NT;
-      const bool use = tq < t1 && tq != i;
-      const int t = tq < t1 ? tq : t1 - 1;
-      T dn[3], rn, rninv, dol[3], ro, roinv;
-      partner_disp(c, pr.rp, pr.rq, t, dn, rn, rninv);
-      partner_disp(c, c.R + 3 * i, c.Rq + 3 * i, t, dol, ro, roinv);
-      const T* coef; int K; T hinv, rc;
-      functor(c, i, t, coef, K, hinv, rc);
-      T un, dun, d2n, uo, duo, d2o;
-      radial(coef, K, hinv, rc, rn, un, dun, d2n);
-      radial(coef, K, hinv, rc, ro, uo, duo, d2o);
-      const bool un_ok = use && rn > T(0), uo_ok = use && ro > T(0);
-      const T fn = un_ok ? dun * rninv : T(0), fo = uo_ok ? duo * roinv : T(0);
-      const T ln = un_ok ? d2n + T(2) * fn : T(0), lo = uo_ok ? d2o + T(2) * fo : T(0);
-      v[4] += use ? un - uo : T(0);
-      v[5] += fn * dn[0];
-      v[6] += fn * dn[1];
-      v[7] += fn * dn[2];
-      v[8] += ln;
-      // partner t's pair term: grad_t u = -(u'/r) d, lap_t u = u'' + 2 u'/r
-      io.dg[q][0] = fo * dol[0] - fn * dn[0];
-      io.dg[q][1] = fo * dol[1] - fn * dn[1];
-      io.dg[q][2] = fo * dol[2] - fn * dn[2];
-      io.dg[q][3] = ln - lo;
-    }
+  for (int q = 0; q < JT; ++q) io.dg[q][0] = io.dg[q][1] = io.dg[q][2] = io.dg[q][3] = T(0);
+  if (t1 - t0 > NT && t1 - t0 <= 2 * NT) {
+    // two slots in one block, so their independent chains interleave (the common case:
+    // a little more than one partner per thread)
+    slot(0);
+    slot(1);
+  } else {
+#pragma unroll
+    for (int q = 0; q < JT; ++q)
+      if (t0 + q * NT < t1) slot(q);  // slot q has partners for some thread (uniform)
   }
   const T* wts = wreg;
   bool ok = true;
