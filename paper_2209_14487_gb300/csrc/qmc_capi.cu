@@ -350,7 +350,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.nt = run->cta_threads ? run->cta_threads : (n <= 128 ? 128 : 256);
   // incremental Jastrow gradients and Laplacians in the mixed Sherman-Morrison sweep
   p.inc_jastrow = (run->precision == QMC_PREC_MIXED && run->update == QMC_UPDATE_SM &&
-                   n <= p.nt) ? 1 : 0;
+                   2 * n <= p.nt && n % 8 == 0) ? 1 : 0;
   p.n_ions = sys->n_ions;
   p.G = sys->grid;
   p.GP = sys->grid + 3;

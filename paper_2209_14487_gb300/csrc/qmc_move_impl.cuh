@@ -1267,36 +1267,31 @@ struct IncOut {
   T e;            // phi' . B[:,p+1]
 };
 
-// The ratio of the incremental sweep: as ratio_grad, with u, u', u'' of every partner
-// term at r and at r' (no cached u(r)), the moving electron's fresh grad U and lap U at
-// r', the partner changes for an accept, and, when `nxt`, the sums a, b, e from which the
-// next electron's determinant drift follows after this move (`pf`: that electron's dA
-// entries for orbital j = tid).  False when the stencil copy timed out (uniform).
+// The ratio of the incremental sweep, in three parts so that the sweep can start a move
+// before the previous move's inverse update: stencil_issue (the TMA copy of the stencil),
+// jas_inc (the Jastrow terms) and spo_inc (the spline, the determinant sums and the
+// all-reduce).  Every partner term is evaluated at r and at r' (u, u', u''), giving the
+// moving electron's fresh grad U and lap U at r' and the partners' changes for an accept;
+// when `nxt`, the sums a, b, e from which the next electron's determinant drift follows
+// after this move (`pf`: that electron's dA entries for orbital j = tid).
 template <typename T>
-__device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& rs, bool nxt,
-                          const T* pf, IncOut<T>& io) {
-  const Params& p = c.p;
-  const int n = p.n, n_pad = p.n_pad, GP = p.GP;
-  const T* table = (const T*)p.table;
-  T cf[16];
-  const bool tma = p.use_tma;
-  if (tma) {
-    if (c.tid == 0) {  // the whole 4x4x4 x n_pad stencil in one copy
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(c.bar, (uint32_t)p.stencil_bytes);
-      tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
-    }
-  } else if (c.nit > 0) {
-    stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[0], c.ita[0], cf);
+__device__ __forceinline__ void stencil_issue(Ctx<T>& c, const Prop<T>& pr) {
+  if (c.p.use_tma && c.tid == 0) {  // the whole 4x4x4 x n_pad stencil in one copy
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(c.bar, (uint32_t)c.p.stencil_bytes);
+    tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
   }
-  T wreg[36];
-  basis12(pr.t[1], wreg + 12);
-  basis12(pr.t[2], wreg + 24);
-  T v[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = T(0);
+}
+
+// jv: dU, grad U (3) and lap U partial sums of this thread's partner slots.
+template <typename T>
+__device__ __forceinline__ void jas_inc(Ctx<T>& c, int i, const Prop<T>& pr, T* jv,
+                                        IncOut<T>& io) {
+  const Params& p = c.p;
   int t0, t1;
   term_range(p, t0, t1);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) jv[q] = T(0);
   // partner slot q of this thread: t = t0 + tid + q NT
   auto slot = [&](int q) {
     const int tq = t0 + c.tid + q * NT;
@@ -1313,11 +1308,11 @@ __device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& r
     const bool un_ok = use && rn > T(0), uo_ok = use && ro > T(0);
     const T fn = un_ok ? dun * rninv : T(0), fo = uo_ok ? duo * roinv : T(0);
     const T ln = un_ok ? d2n + T(2) * fn : T(0), lo = uo_ok ? d2o + T(2) * fo : T(0);
-    v[4] += use ? un - uo : T(0);
-    v[5] += fn * dn[0];
-    v[6] += fn * dn[1];
-    v[7] += fn * dn[2];
-    v[8] += ln;
+    jv[0] += use ? un - uo : T(0);
+    jv[1] += fn * dn[0];
+    jv[2] += fn * dn[1];
+    jv[3] += fn * dn[2];
+    jv[4] += ln;
     // partner t's pair term: grad_t u = -(u'/r) d, lap_t u = u'' + 2 u'/r
     io.dg[q][0] = fo * dol[0] - fn * dn[0];
     io.dg[q][1] = fo * dol[1] - fn * dn[1];
@@ -1336,6 +1331,25 @@ __device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& r
     for (int q = 0; q < JT; ++q)
       if (t0 + q * NT < t1) slot(q);  // slot q has partners for some thread (uniform)
   }
+}
+
+// False when the stencil copy timed out (uniform).
+template <typename T>
+__device__ bool spo_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& rs, bool nxt,
+                        const T* pf, const T* jv, IncOut<T>& io) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad, GP = p.GP;
+  const T* table = (const T*)p.table;
+  const bool tma = p.use_tma;
+  T cf[16];
+  T wreg[36];
+  basis12(pr.t[1], wreg + 12);
+  basis12(pr.t[2], wreg + 24);
+  T v[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) v[4 + q] = jv[q];
   const T* wts = wreg;
   bool ok = true;
   if (tma) {
@@ -1367,7 +1381,7 @@ __device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& r
         const T* sb = c.stc + (size_t)(c.ita[q] * 16) * n_pad + c.itj[q];
 #pragma unroll
         for (int bc = 0; bc < 16; ++bc) cf[bc] = sb[(size_t)bc * n_pad];
-      } else if (q > 0) {
+      } else {
         stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[q], c.ita[q], cf);
       }
       T o4[4];
@@ -1440,6 +1454,60 @@ __device__ bool ratio_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& r
   }
   io.e = v[15];
   return true;
+}
+
+// The Sherman-Morrison update of an accepted move by row owners (2 or 4 threads per row,
+// n <= NT / 2) with the new rows of A written to HBM and log|det| advanced; no barrier
+// (the caller's publishes it).  The caller has already moved the electron.
+template <typename T>
+__device__ __forceinline__ void sm_rows_update(Ctx<T>& c, int i, int s, int pp, T rhoD) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad, bs = c.bs;
+  if constexpr (sizeof(T) == 4) {
+    const int tpr = (4 * n <= NT && n % 16 == 0) ? 4 : 2;
+    const float invr = 1.f / rhoD;
+    const int k = c.tid / tpr, qd = c.tid % tpr, nq = n / tpr;
+    float4* r4 = reinterpret_cast<float4*>(c.B + (size_t)(k < n ? k : 0) * bs + qd * nq);
+    const float4* p4 = reinterpret_cast<const float4*>(c.phi + qd * nq);
+    const float4* c4 = reinterpret_cast<const float4*>(c.col + qd * nq);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (k < n) {
+      for (int q = 0; q < nq / 4; ++q) {
+        const float4 b = r4[q], f = p4[q];
+        a0 += b.x * f.x;
+        a1 += b.y * f.y;
+        a2 += b.z * f.z;
+        a3 += b.w * f.w;
+      }
+    }
+    float acc = (a0 + a1) + (a2 + a3);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (tpr == 4) acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (k < n) {
+      const float f = (acc - (k == pp ? 1.f : 0.f)) * invr;
+      for (int q = 0; q < nq / 4; ++q) {
+        float4 b = r4[q];
+        const float4 cv = c4[q];
+        b.x -= cv.x * f;
+        b.y -= cv.y * f;
+        b.z -= cv.z * f;
+        b.w -= cv.w * f;
+        r4[q] = b;
+      }
+    }
+    T* rw = c.rows + (size_t)i * 5 * n_pad;
+    for (int j = c.tid; j < n; j += NT) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = c.phi[q * n_pad + j];
+    }
+    if (c.tid == 0) {
+      const float y = logf(fabsf(rhoD)) - c.sc->lcomp[s];
+      const float t = c.sc->lsum[s] + y;
+      c.sc->lcomp[s] = (t - c.sc->lsum[s]) - y;
+      c.sc->lsum[s] = t;
+      if (rhoD < 0.f) c.sc->sign[s] = -c.sc->sign[s];
+    }
+  }
 }
 
 // Accepted move of electron i: partners' accumulators change by their pair term's
@@ -1695,7 +1763,8 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     // sweep when still valid, else from one pass over all pairs
     bool inc = false;
     if constexpr (IsMixed<T>::value && UPD == 0)
-      inc = p.inc_jastrow && pf_ok && (t1 - t0) <= JT * NT;
+      inc = p.inc_jastrow && 2 * n <= NT && n % 8 == 0 && b_stride<T>(p) % 4 == 0 &&
+            (t1 - t0) <= JT * NT;
     if (inc) {
       if (p.jvalid[w]) {
         const T* gsrc = (const T*)p.jgl + (size_t)w * N * 4;
@@ -1706,26 +1775,31 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     }
     __syncthreads();
     unsigned long long nacc = 0;
-    for (int s = 0; s < 2; ++s) {
-      begin_spin(c, s);
-      bool have_det = false;
-      T det[3] = {0, 0, 0};
-      for (int pp = 0; pp < n; ++pp) {
-        const int i = s * p.n_up + pp;
-        compute_column(c, pp);
-        if constexpr (IsMixed<T>::value && UPD == 0) {
-          if (inc) {
-            // drift: determinant part (from the previous move's sums, or one all-reduce at
-            // a spin's first electron) minus the accumulated grad U
-            if (p.drift) {
-              if (!have_det) det_grad(c, i, det);
-              for (int k = 0; k < 3; ++k) F[k] = det[k] - c.jgl[4 * i + k];
-            }
-            const bool nxt = p.drift && pp + 1 < n;
-            if (nxt) prefetch_grad_rows(c, i + 1, pf);
-            shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
-            IncOut<T> io;
-            if (!ratio_inc(c, i, pp, pr, rs, nxt, pf, io)) {
+    if constexpr (IsMixed<T>::value && UPD == 0) {
+      if (inc) {
+        // Software-pipelined: once move i is decided (and its accumulators and position
+        // published), move i+1's drift, proposal, stencil copy and Jastrow terms are issued
+        // before move i's inverse update, so their latencies overlap it.
+        for (int s = 0; s < 2 && !c.failed; ++s) {
+          begin_spin(c, s);
+          T det[3] = {0, 0, 0};
+          T jv[5];
+          IncOut<T> io;
+          int i = s * p.n_up;
+          compute_column(c, 0);
+          if (p.drift) {
+            det_grad(c, i, det);
+            for (int k = 0; k < 3; ++k) F[k] = det[k] - c.jgl[4 * i + k];
+          }
+          bool nxt = p.drift && n > 1;
+          if (nxt) prefetch_grad_rows(c, i + 1, pf);
+          shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
+          stencil_issue(c, pr);
+          jas_inc(c, i, pr, jv, io);
+          for (int pp = 0; pp < n; ++pp) {
+            i = s * p.n_up + pp;
+            // false only when a stencil copy timed out (status set; uniform over the CTA)
+            if (!spo_inc(c, i, pp, pr, rs, nxt, pf, jv, io)) {
               c.failed = true;
               break;
             }
@@ -1733,16 +1807,40 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
             nacc += acc;
             if (acc) {
               accept_inc(c, i, io);
-              accept_update(c, i, s, pp, pr, rs.rhoD);  // its barriers publish c.jgl
+              if (c.tid == 0)
+                for (int k = 0; k < 3; ++k) c.Rq[3 * i + k] = pr.rq[k];
             }
-            if (nxt) {
+            if (nxt) {  // the next electron's determinant drift after this move
               const T f = acc ? io.e / rs.rhoD : T(0);
               for (int k = 0; k < 3; ++k) det[k] = io.a[k] - f * io.b[k];
             }
-            have_det = nxt;
-            continue;
+            const T rhoD = rs.rhoD;
+            __syncthreads();  // accumulators and the moved position are visible
+            const bool more = pp + 1 < n;
+            if (more) {
+              const int i1 = i + 1;
+              if (p.drift)
+                for (int k = 0; k < 3; ++k) F[k] = det[k] - c.jgl[4 * i1 + k];
+              nxt = p.drift && pp + 2 < n;
+              if (nxt) prefetch_grad_rows(c, i1 + 1, pf);
+              shared_proposal(c, i1, F, c.dchi + 3 * i1, nullptr, pr);
+              stencil_issue(c, pr);
+              jas_inc(c, i1, pr, jv, io);
+            }
+            if (acc) sm_rows_update(c, i, s, pp, rhoD);
+            __syncthreads();  // the updated inverse is visible
+            if (more) compute_column(c, pp + 1);
           }
+          if (c.failed) break;
+          end_spin(c, s, true);
         }
+      }
+    }
+    for (int s = 0; s < 2 && !inc; ++s) {
+      begin_spin(c, s);
+      for (int pp = 0; pp < n; ++pp) {
+        const int i = s * p.n_up + pp;
+        compute_column(c, pp);
         if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
         if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
         shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
