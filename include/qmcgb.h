@@ -209,7 +209,7 @@ int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out);
 int qmc_batch_destroy(qmc_batch* batch);
 /* n_gen generations of every crowd.  eloc: NULL, or n_crowds pointers (entries may be
  * NULL) to host buffers double [n_gen][W_c] for crowd c's E_L; stats: NULL or n_crowds
- * entries.  Delayed windows are flushed on the CUDA cores in a batch.  Synchronous.
+ * entries.  Synchronous.
  * Errors: as qmc_sweep. */
 int qmc_batch_sweep(qmc_batch* batch, int n_gen, double* const* eloc, qmc_stats* stats);
 /* Kernel launches (graph replays count their nodes) issued by the batch so far. */

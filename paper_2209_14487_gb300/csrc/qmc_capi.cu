@@ -45,12 +45,6 @@ __global__ void batch_advance_kernel(Params* plist, int n) {
   if ((int)threadIdx.x < n) plist[threadIdx.x].gen += 1u;
 }
 
-int sweep_ctas_per_sm(const Params& p) {
-  if (p.nt == 128) return nt128::sweep_ctas_per_sm(p);
-  if (p.nt == 160) return nt160::sweep_ctas_per_sm(p);
-  return nt256::sweep_ctas_per_sm(p);
-}
-
 int max_smem_optin() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -82,6 +76,7 @@ struct qmc_crowd {
   void* d_win_S = nullptr;
   void* d_pend_phi = nullptr;
   void* d_jgl = nullptr;        // [W][N][4] incremental Jastrow grad/lap, carried over sweeps
+  void* d_flush = nullptr;      // [W][3][k][n] tensor-core flush scratch
   int* d_jvalid = nullptr;      // [W]
   double* d_pend = nullptr;
   double* d_ws = nullptr;
@@ -134,7 +129,7 @@ void free_all(qmc_crowd* c) {
   void* ptrs[] = {c->d_R, c->d_rows, c->d_binv, c->d_logdet, c->d_sign, c->d_table,
                   c->d_jc, c->d_ions, c->d_win_m, c->d_win_P, c->d_win_V, c->d_win_S,
                   c->d_pend_phi, c->d_pend, c->d_ws, c->d_eloc, c->d_nacc, c->d_status,
-                  c->d_io, c->d_io8, c->d_jgl, c->d_jvalid};
+                  c->d_io, c->d_io8, c->d_jgl, c->d_jvalid, c->d_flush};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -155,6 +150,7 @@ void sync_params(qmc_crowd* c) {
   p.win_S = c->d_win_S;
   p.pend_phi = c->d_pend_phi;
   p.jgl = c->d_jgl;
+  p.flush_scratch = c->d_flush;
   p.jvalid = c->d_jvalid;
   p.pend = c->d_pend;
   p.status = c->d_status;
@@ -415,14 +411,8 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     delete c;
     return QMC_ERR_UNSUPPORTED;
   }
-  // TMEM: every resident CTA of the sweep holds 128 of the SM's 512 columns
-  if (p.tc_flush) {
-    const int per_sm = qmcgb::sweep_ctas_per_sm(p);
-    if (per_sm < 1 || per_sm > 4) {
-      p.tc_flush = 0;
-      smem = qmcgb::move_smem_bytes(p, es);
-    }
-  }
+  // TMEM: a flush holds 128 of the SM's 512 columns while it runs; a CTA whose
+  // allocation finds them taken waits for another CTA's flush to end
   c->smem = smem;
 
   const size_t GP = (size_t)p.GP;
@@ -443,6 +433,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   }
   st |= dmalloc(&c->d_pend_phi, (size_t)es * W * 5 * p.n_pad);
   st |= dmalloc(&c->d_jgl, (size_t)es * W * N * 4);
+  if (p.tc_flush) st |= dmalloc(&c->d_flush, (size_t)es * W * 3 * p.k * n);
   st |= dmalloc((void**)&c->d_jvalid, sizeof(int) * W);
   st |= dmalloc((void**)&c->d_pend, sizeof(double) * W * qmcgb::PEND_STRIDE);
   st |= dmalloc((void**)&c->d_ws, sizeof(double) * W * 2 * 2 * n * n);
@@ -1031,7 +1022,6 @@ int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* sta
       p.n_accept = stats ? c->d_nacc : nullptr;
       p.stencil_bytes = qmcgb::stencil_tma_bytes(p, c->es);
       p.skip_eloc = 0;
-      p.tc_flush = 0;  // the batch kernel keeps delayed flushes on the CUDA cores
       b->hp[q] = p;
     }
   };

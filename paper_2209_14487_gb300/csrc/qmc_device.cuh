@@ -396,13 +396,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // ---------------------------------------------------------------------------------------
 
 // Allocates `ncols` TMEM columns (a power of two, 32..512) for the CTA; the base address
-// is written to *dst.  Executed by one whole warp.
+// is written to *dst.  Executed by one whole warp.  The CTA keeps its permit to allocate
+// again (an allocation lives for one flush).
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                    smem_addr(dst)),
                "r"(ncols)
                : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
 // Frees a TMEM allocation; by the warp that allocated it.

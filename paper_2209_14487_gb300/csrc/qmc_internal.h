@@ -67,6 +67,7 @@ struct Params {
   void* win_V;              // [W][2][k][vs] T
   void* win_S;              // [W][2][k][ks] T  (S^-1)
   void* pend_phi;           // [W][5][n_pad] T
+  void* flush_scratch;      // [W][2][k][n] T: tensor-core flush, snapshot rows and Y^T
   void* jgl;                // [W][N][4] T: Jastrow grad U (3) and lap U of every electron
   int* jvalid;              // [W]: jgl holds the walker's current values
   double* pend;             // [W][PEND_STRIDE]
@@ -85,7 +86,6 @@ struct Params {
 
 size_t move_smem_bytes(const Params& p, int elem_bytes);
 int max_smem_optin();
-int sweep_ctas_per_sm(const Params& p);
 
 // tmap: host copy of the table's CUtensorMap (128 bytes), or null when p.use_tma == 0.
 // The move kernel is compiled once per CTA width (p.nt); these dispatch on it.
@@ -108,7 +108,6 @@ struct BatchArgs {
   cudaError_t launch_batch(const Params* d_plist, const BatchArgs& a, int update,       \
                            size_t bytes, cudaStream_t s);                              \
   size_t move_smem_bytes(const Params& p, int elem_bytes);                              \
-  int sweep_ctas_per_sm(const Params& p);                                               \
   }
 QMCGB_DECLARE_MOVE_WIDTH(nt128)
 QMCGB_DECLARE_MOVE_WIDTH(nt160)

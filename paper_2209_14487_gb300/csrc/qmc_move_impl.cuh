@@ -125,7 +125,7 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
     o += al16((size_t)TC_STAGE_BYTES + 128);
   }
   L.B = o; o += al16(p.b_in_smem ? (size_t)p.n * b_stride<T>(p) * es : 0);
-  L.R = o; o += al16((size_t)p.N * 3 * 8);
+  L.R = o; o += es == 8 ? al16((size_t)p.N * 3 * 8) : 0;  // the mixed path moves fixed point
   L.Rq = o; o += al16((size_t)p.N * 3 * 4);
   L.ion = o; o += al16((size_t)p.n_ions * 3 * 8);
   L.ionq = o; o += al16((size_t)p.n_ions * 3 * 4);
@@ -147,9 +147,11 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
     L.wz = o; o += al16((size_t)(MAX_K + 1) * es);
     L.wc = o; o += al16((size_t)(MAX_K + 1) * es);
     L.wb = o; o += al16((size_t)(MAX_K + 1) * es);
-    L.snap = o; o += al16((size_t)p.k * p.n * es);
-    L.xb = o; o += al16((size_t)p.n * p.k * es);
-    L.yb = o; o += al16((size_t)p.n * p.k * es);
+    if (!p.tc_flush) {  // the tensor-core flush keeps them in global memory
+      L.snap = o; o += al16((size_t)p.k * p.n * es);
+      L.xb = o; o += al16((size_t)p.n * p.k * es);
+      L.yb = o; o += al16((size_t)p.n * p.k * es);
+    }
   }
   L.total = o;
   return L;
@@ -485,6 +487,17 @@ __device__ __forceinline__ void tc_load_bt(const Ctx<T>& c, int r0, int k0, floa
   }
 }
 
+// Releases the flush's TMEM (every MMA has completed or its wait ran out twice).
+template <typename T>
+__device__ __forceinline__ void tc_release(Ctx<T>& c) {
+  tc_fence_before_sync();
+  __syncthreads();
+  if (c.warp == 0) tmem_dealloc(c.sc->tmem, TC_COLS);
+}
+
+// The window's rows of B^T before the update (snap), X^T and Y^T live in the walker's
+// global scratch [3][k][n] (L2-resident), which keeps the flush's shared memory to the
+// operand stages: delay ranks up to 64 fit next to the staged stencil.
 template <typename T>
 __device__ void flush_window_tc(Ctx<T>& c) {
   if constexpr (IsMixed<T>::value) {
@@ -493,6 +506,19 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     if (m == 0) return;
     const int n = p.n, bs = c.bs;
     const int mp = (m + 15) & ~15;  // N of the first product, K of the second
+    float* scr = (float*)p.flush_scratch + (size_t)c.w * 3 * p.k * n;
+    float* snapg = scr;                      // [m][n]: B^T[p_b][j]
+    float* xt = scr + (size_t)p.k * n;       // [m][n]: X^T[l][r]
+    float* yt = scr + (size_t)2 * p.k * n;   // [m][n]: Y^T[b][r]
+    if (c.warp == 0) tmem_alloc(&c.sc->tmem, TC_COLS);
+    // snapshot of the window's rows of B^T before the update
+    for (int e = c.tid; e < m * n; e += NT) {
+      const int l = e / n, j = e - l * n;
+      snapg[e] = c.B[(size_t)c.wP[l] * bs + j];
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
     const uint32_t tm = c.sc->tmem;
     const uint32_t lane_base = (uint32_t)((c.warp & 3) * 32) << 16;
     float* st = c.tcs;
@@ -500,9 +526,6 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     float* alo = st + TC_TILE * TC_KC;
     float* bhi = st + 2 * TC_TILE * TC_KC;
     float* blo = st + 3 * TC_TILE * TC_KC;
-    // snapshot of the window's rows of B^T before the update
-    for (int l = c.warp; l < m; l += NWARP)
-      for (int j = c.lane; j < n; j += 32) c.snap[l * n + j] = c.B[(size_t)c.wP[l] * bs + j];
     // ---- X = B^T Phi^T - P (per 128-row tile, K = n in chunks of 32)
     const uint32_t id1 = tc_idesc_tf32((uint32_t)mp);
     for (int r0 = 0; r0 < n; r0 += TC_TILE) {
@@ -529,7 +552,10 @@ __device__ void flush_window_tc(Ctx<T>& c) {
         __syncthreads();
         if (c.tid == 0) tc_issue_chunk(st, tm, id1, TC_KC / 8, k0 == 0, c.bar + 1);
         if (k0 + TC_KC < n) tc_load_bt(c, r0, k0 + TC_KC, v);  // in flight during the MMAs
-        if (!tc_wait(c)) return;
+        if (!tc_wait(c)) {
+          tc_release(c);
+          return;
+        }
       }
       tc_fence_after_sync();
       // epilogue: row r of the tile is TMEM lane r; warps of one lane quadrant split columns
@@ -541,21 +567,20 @@ __device__ void flush_window_tc(Ctx<T>& c) {
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int l = c0 + q;
-            if (l < m) c.xb[(size_t)r * m + l] = x[q] - (r == c.wP[l] ? 1.f : 0.f);
+            if (l < m) xt[(size_t)l * n + r] = x[q] - (r == c.wP[l] ? 1.f : 0.f);
           }
         }
       }
       tc_fence_before_sync();
       __syncthreads();
     }
-    // ---- Y = X S^-T (m x m on the CUDA cores)
+    // ---- Y = X S^-T (m x m on the CUDA cores; X^T rows from the L2-resident scratch)
     for (int e = c.tid; e < n * m; e += NT) {
-      const int k = e / m, b = e - k * m;
+      const int b = e / n, r = e - b * n;
       const T* srow = c.wS + (size_t)b * p.ks;
-      const T* xrow = c.xb + (size_t)k * m;
-      T acc = 0;
-      for (int l = 0; l < m; ++l) acc += xrow[l] * srow[l];
-      c.yb[e] = acc;
+      float acc = 0.f;
+      for (int l = 0; l < m; ++l) acc += xt[(size_t)l * n + r] * srow[l];
+      yt[e] = acc;
     }
     __syncthreads();
     // ---- B^T -= Y snap (per 128 x 128 output tile, K = mp in chunks of 32)
@@ -564,23 +589,22 @@ __device__ void flush_window_tc(Ctx<T>& c) {
       for (int j0 = 0; j0 < n; j0 += TC_TILE) {
         for (int b0 = 0; b0 < mp; b0 += TC_KC) {
           for (int e = c.tid; e < TC_SLOTS; e += NT) {
-            int r, kk;
-            tc_slot(e, r, kk);
-            const int k = r0 + r, b = b0 + kk;
+            int rr, kk;
+            tc_slot(e, rr, kk);
+            const int k = r0 + rr, b = b0 + kk;
             float4 y = make_float4(0.f, 0.f, 0.f, 0.f), z = y;
             if (k < n) {
-              const T* yr = c.yb + (size_t)k * m;
-              y.x = b < m ? yr[b] : 0.f;
-              y.y = b + 1 < m ? yr[b + 1] : 0.f;
-              y.z = b + 2 < m ? yr[b + 2] : 0.f;
-              y.w = b + 3 < m ? yr[b + 3] : 0.f;
+              y.x = b < m ? yt[(size_t)b * n + k] : 0.f;
+              y.y = b + 1 < m ? yt[(size_t)(b + 1) * n + k] : 0.f;
+              y.z = b + 2 < m ? yt[(size_t)(b + 2) * n + k] : 0.f;
+              y.w = b + 3 < m ? yt[(size_t)(b + 3) * n + k] : 0.f;
             }
-            const int j = j0 + r;  // the B operand's rows are output columns j
+            const int j = j0 + rr;  // the B operand's rows are output columns j
             if (j < n) {
-              z.x = b < m ? c.snap[(size_t)b * n + j] : 0.f;
-              z.y = b + 1 < m ? c.snap[(size_t)(b + 1) * n + j] : 0.f;
-              z.z = b + 2 < m ? c.snap[(size_t)(b + 2) * n + j] : 0.f;
-              z.w = b + 3 < m ? c.snap[(size_t)(b + 3) * n + j] : 0.f;
+              z.x = b < m ? snapg[(size_t)b * n + j] : 0.f;
+              z.y = b + 1 < m ? snapg[(size_t)(b + 1) * n + j] : 0.f;
+              z.z = b + 2 < m ? snapg[(size_t)(b + 2) * n + j] : 0.f;
+              z.w = b + 3 < m ? snapg[(size_t)(b + 3) * n + j] : 0.f;
             }
             tc_store_split(ahi, alo, e, y);
             tc_store_split(bhi, blo, e, z);
@@ -589,7 +613,10 @@ __device__ void flush_window_tc(Ctx<T>& c) {
           __syncthreads();
           const int ks = (mp - b0 < TC_KC ? mp - b0 : TC_KC) / 8;
           if (c.tid == 0) tc_issue_chunk(st, tm, id2, ks, b0 == 0, c.bar + 1);
-          if (!tc_wait(c)) return;
+          if (!tc_wait(c)) {
+            tc_release(c);
+            return;
+          }
         }
         tc_fence_after_sync();
         const int r = r0 + (c.warp & 3) * 32 + c.lane;
@@ -602,12 +629,12 @@ __device__ void flush_window_tc(Ctx<T>& c) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               if (j + 4 * q < n) {
-                float4 b = brow[q];
-                b.x -= d[4 * q];
-                b.y -= d[4 * q + 1];
-                b.z -= d[4 * q + 2];
-                b.w -= d[4 * q + 3];
-                brow[q] = b;
+                float4 bv = brow[q];
+                bv.x -= d[4 * q];
+                bv.y -= d[4 * q + 1];
+                bv.z -= d[4 * q + 2];
+                bv.w -= d[4 * q + 3];
+                brow[q] = bv;
               }
             }
           }
@@ -616,6 +643,7 @@ __device__ void flush_window_tc(Ctx<T>& c) {
         __syncthreads();
       }
     }
+    tc_release(c);
     if (c.tid == 0) c.sc->m = 0;
     __syncthreads();
   }
@@ -1703,8 +1731,8 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
   const double* Rg = p.R + (size_t)w * N * 3;
   for (int e = c.tid; e < N * 3; e += NT) {
     const double x = Rg[e];
-    c.R[e] = x;
     if constexpr (IsMixed<T>::value) c.Rq[e] = to_fixed(x, p.fx_scale);
+    else c.R[e] = x;
   }
   for (int e = c.tid; e < p.n_ions * 3; e += NT) {
     const double x = p.ions[e];
@@ -1727,14 +1755,10 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     }
     sc->accept = 0;
   }
-  // the tensor-core flush holds TC_COLS columns of TMEM for the whole sweep
-  if constexpr (IsMixed<T>::value && UPD == 1 && BSM == 2 && MODE == MODE_SWEEP) {
-    c.tc = p.tc_flush != 0;
-    if (c.tc && c.warp == 0) tmem_alloc(&sc->tmem, TC_COLS);
-  }
-  tc_fence_before_sync();
+  // delayed windows of the mixed path with the inverse in global memory are flushed on
+  // the tensor cores (TMEM is allocated for each flush)
+  if constexpr (IsMixed<T>::value && UPD == 1 && BSM != 1) c.tc = p.tc_flush && !p.b_in_smem;
   __syncthreads();
-  tc_fence_after_sync();
 
   int t0, t1;
   term_range(p, t0, t1);
@@ -1869,11 +1893,6 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
       flush_window(c);
       if (c.failed) break;
       end_spin(c, s, true);
-    }
-    if (c.tc) {  // every MMA has completed (each chunk was waited for)
-      tc_fence_before_sync();
-      __syncthreads();
-      if (c.warp == 0) tmem_dealloc(sc->tmem, TC_COLS);
     }
     if (c.failed) return;
     moved = true;
@@ -2116,26 +2135,6 @@ cudaError_t launch_move(const Params& p_in, int mode, const void* tmap, cudaStre
   }
 }
 
-#if QMCGB_MOVE_ELEM == 4
-// Resident CTAs per SM of the mixed delayed sweep with the inverse in global memory (the
-// kernel that may hold TMEM), at the crowd's dynamic shared memory.
-int sweep_ctas_per_sm(const Params& p_in) {
-  Params p = p_in;
-  p.stencil_bytes = 64 * p.n_pad * 4;
-  const size_t bytes = make_lay<float>(p).total;
-  auto kern = move_kernel<float, MODE_SWEEP, 1, 2>;
-  if (allow_max_smem<float, MODE_SWEEP, 1, 2>() != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  int nb = -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  return nb;
-}
-#endif
 
 template <typename T, int UPD>
 static cudaError_t launch_batch_upd(const Params* d_plist, const BatchArgs& a, size_t bytes,

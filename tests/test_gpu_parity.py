@@ -455,3 +455,38 @@ def test_incremental_jastrow_matches_full_pass(Q, nt):
     ref3 = np.zeros(W)
     c.qmc_local_energy_batch(ref3)
     assert np.allclose(e3[0], ref3, rtol=1e-4, atol=1e-3), np.abs(e3[0] - ref3).max()
+
+
+@pytest.mark.parametrize("k", [4, 64])
+def test_pw512_tensor_flush_fine_grained_and_rank_64(Q, oracle_lib, k):
+    """Mixed delayed update on n = 256 with the tensor-core flush in every mode: windows
+    flushed when full during fine-grained accepts (k = 4) and before the local energy,
+    then a whole sweep; delay rank 64 fits beside the staged stencil."""
+    wl = wl_mod.pw512()
+    W = 3
+    gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision="mixed", update="delayed", k=k, W=W,
+                              nt=128)
+    cfg = gpu.kernel_config
+    assert cfg["tc_flush"] == 1 and cfg["stencil_tma"] == 1, cfg
+    rng = np.random.default_rng(21)
+    for iel in [0, 9, 255, 300, 17, 511, 256, 40, 77, 300]:
+        rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.3, size=(W, 3)), wl.L)
+        lr = np.zeros(W)
+        gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, None, lr)
+        _, _, o_lr, _ = orc.propose(iel, rnew)
+        assert np.all(np.abs(lr - o_lr) <= 2e-4 * np.maximum(1.0, np.abs(o_lr))), (iel, lr, o_lr)
+        acc = np.ones(W, dtype=np.uint8)
+        gpu.qmc_accept_reject_batch(iel, acc)
+        orc.accept(iel, acc)
+        R = orc.positions()
+    e = np.zeros(W)
+    gpu.qmc_local_energy_batch(e)
+    e_ref = orc.local_energy()
+    assert np.all(np.abs(e - e_ref) < 1e-3 * np.maximum(1.0, np.abs(e_ref))), (e, e_ref)
+    gpu.qmc_sweep(1)
+    Rg = gpu.qmc_get_positions()
+    la, sg = gpu.qmc_get_logpsi()
+    for w in range(W):
+        ref, rsg = osys.logpsi(Rg[w])
+        assert abs(la[w] - ref) < 1e-4 * max(1.0, abs(ref)), (w, la[w], ref)
+        assert sg[w] == rsg
