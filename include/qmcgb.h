@@ -92,6 +92,10 @@ typedef struct qmc_run_desc {
   int engine;       /* QMC_ENGINE_AUTO (0): in the mixed path with the delayed update   *
                      * and the inverse in global memory, windows are flushed on the    *
                      * tensor cores (tcgen05, 3xTF32); QMC_ENGINE_SIMT: CUDA cores     */
+  int dmc;          /* 1: diffusion Monte Carlo: fixed-node acceptance (a move that     *
+                     * changes the sign of the determinant is rejected) and population *
+                     * branching by qmc_dmc_branch; n_walkers is then the capacity     */
+  int reserved;     /* 0                                                              */
 } qmc_run_desc;
 
 /* Per-call statistics of qmc_sweep, accumulated in FP64 over walkers and generations. */
@@ -214,6 +218,32 @@ int qmc_batch_destroy(qmc_batch* batch);
 int qmc_batch_sweep(qmc_batch* batch, int n_gen, double* const* eloc, qmc_stats* stats);
 /* Kernel launches (graph replays count their nodes) issued by the batch so far. */
 int qmc_batch_get_launch_count(const qmc_batch* batch, unsigned long long* count);
+
+/* ---------------------------------------------------------------------------------------
+ * DMC branching (Alg. 1 lines 13-14; the paper gives no formulas, the readings are):
+ * after a generation, walker w's weight is exp(-tau ((E_prev[w] + E_new[w]) / 2 - e_trial))
+ * and its multiplicity floor(weight + u) with u the walker's Philox uniform from counter
+ * (generation just completed, N, 3, 0); the new population lists walker 0 M_0 times,
+ * walker 1 M_1 times, ... (each copy carries the walker's full state: positions, orbital
+ * rows, inverses, log|det|), cut at the crowd's capacity (run.n_walkers).  Pending delayed
+ * windows are applied first.  The crowd's active walker count becomes n_after.
+ * e_prev: double [W] (mem); e_new: double [capacity] (mem) holding the W walkers' E_L
+ * after the generation; on return e_new[0..n_after) holds the new population's E_L (the
+ * next generation's e_prev).  Needs run.dmc.  Errors: INVALID_ARG; STATE (no
+ * DMC crowd, or every multiplicity zero: the crowd is then left unchanged).
+ * --------------------------------------------------------------------------------------- */
+typedef struct qmc_dmc_stats {
+  int n_before;       /* walkers before branching                                     */
+  int n_after;        /* walkers after (at most the capacity)                         */
+  long long n_wanted; /* sum of multiplicities before the capacity cut                 */
+  double w_sum;       /* sum of weights                                               */
+  double we_sum;      /* sum of weight x E_new (the mixed estimator's numerator)       */
+} qmc_dmc_stats;
+
+int qmc_dmc_branch(qmc_crowd* crowd, const double* e_prev, double* e_new, int mem,
+                   double e_trial, qmc_dmc_stats* out);
+/* Active walkers of the crowd (n_walkers unless DMC branching changed it). */
+int qmc_get_walker_count(const qmc_crowd* crowd, int* count);
 
 /* Text of the CUDA error behind the calling thread's last QMC_ERR_CUDA ("no error" if none). */
 const char* qmc_last_cuda_error(void);

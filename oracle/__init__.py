@@ -33,7 +33,7 @@ class System(C.Structure):
         ("n_up", C.c_int), ("n_dn", C.c_int), ("n_orb", C.c_int), ("n_ions", C.c_int),
         ("grid", C.c_int), ("drift", C.c_int), ("potential", C.c_int), ("update", C.c_int),
         ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("j2_K", C.c_int),
-        ("j1_K", C.c_int), ("analytic", C.c_int), ("pad0", C.c_int),
+        ("j1_K", C.c_int), ("analytic", C.c_int), ("dmc", C.c_int),
         ("L", C.c_double), ("tau", C.c_double), ("j2_rc", C.c_double), ("j1_rc", C.c_double),
         ("seed", C.c_uint64),
         ("table", C.c_void_p), ("ions", C.c_void_p), ("j2_uu", C.c_void_p),
@@ -83,6 +83,10 @@ def lib():
         L.or_crowd_get_generation.restype = C.c_uint32
         L.or_crowd_set_generation.argtypes = [C.c_void_p, C.c_uint32]
         L.or_num_threads.restype = C.c_int
+        L.or_dmc_branch.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
+                                    C.c_double, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p,
+                                    C.c_void_p]
+        L.or_dmc_branch.restype = C.c_int
         del dp
         _lib = L
     return _lib
@@ -308,6 +312,20 @@ class OracleCrowd:
     @generation.setter
     def generation(self, g):
         lib().or_crowd_set_generation(self.h, g)
+
+
+def dmc_branch(e_prev, e_new, n_el: int, tau: float, e_trial: float, seed: int, gen: int,
+               cap: int):
+    """DMC reweighting and branching (or_dmc_branch): (src walker of every new slot,
+    weights)."""
+    e_prev = np.ascontiguousarray(e_prev, dtype=np.float64)
+    e_new = np.ascontiguousarray(e_new, dtype=np.float64)
+    W = e_prev.size
+    src = np.zeros(max(cap, 1), dtype=np.int32)
+    wt = np.zeros(W)
+    n = lib().or_dmc_branch(_p(e_prev), _p(e_new), W, n_el, tau, e_trial, seed, gen, cap,
+                            _p(src), _p(wt))
+    return src[:n].copy(), wt
 
 
 def num_threads() -> int:

@@ -41,7 +41,8 @@ typedef struct or_system {
   int n_recompute;  /* generations between full recomputes; 0 = never                       */
   int j2_K, j1_K;   /* number of free radial coefficients; 0 = term absent                  */
   int analytic;     /* test mode: phi_j = single real plane wave pw_m[j], pw_kind[j]        */
-  int pad0;
+  int dmc;          /* 1: fixed node (DMC): a move that changes the determinant's sign is   *
+                     * rejected                                                             */
   double L, tau, j2_rc, j1_rc;
   uint64_t seed;
   const double* table;  /* [G][G][G][n_orb] periodic cubic B-spline coefficients */
@@ -744,6 +745,7 @@ static void walker_accept(or_crowd* c, or_walker* wk, int w, int i) {
 static int metropolis(const or_system* s, const or_walker* wk, double u) {
   double rho = wk->rho;
   if (!(rho != 0.0) || !isfinite(rho)) return 0;
+  if (s->dmc && wk->rhoD < 0.0) return 0;  /* fixed node: no crossing of a nodal surface */
   double A;
   if (s->drift) {
     double gb = 0.0;
@@ -952,4 +954,31 @@ int or_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+
+/* ------------------------------------------------------------------------------------ */
+/* DMC reweighting and branching (Alg. 1 lines 13-14; the paper gives no formulas, the     */
+/* readings are): weight w = exp(-tau ((E_prev + E_new) / 2 - E_T)); multiplicity          */
+/* M = floor(w + u) with u the walker's uniform from Philox counter (gen, N, 3, 0) and the */
+/* walker's usual key; the new population lists walker 0 M_0 times, then walker 1 M_1     */
+/* times, and so on, cut at `cap` entries.  Writes src[d] (the walker copied into slot d)  */
+/* and the weights; returns the new population size.                                       */
+/* ------------------------------------------------------------------------------------ */
+int or_dmc_branch(const double* e_prev, const double* e_new, int W, int N, double tau,
+                  double e_trial, uint64_t seed, uint32_t gen, int cap, int* src,
+                  double* weight) {
+  int d = 0;
+  for (int w = 0; w < W; ++w) {
+    const double wt = exp(-tau * (0.5 * (e_prev[w] + e_new[w]) - e_trial));
+    weight[w] = wt;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)w ^ (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {gen, (uint32_t)N, 3u, 0u};
+    uint32_t x[4];
+    or_philox4x32_10(ctr, key, x);
+    const double u = u53(x[0], x[1]);
+    const int M = (int)floor(wt + u);
+    for (int j = 0; j < M && d < cap; ++j) src[d++] = w;
+  }
+  return d;
 }

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "../../include/qmcgb.h"
@@ -77,6 +78,19 @@ struct qmc_crowd {
   void* d_pend_phi = nullptr;
   void* d_jgl = nullptr;        // [W][N][4] incremental Jastrow grad/lap, carried over sweeps
   void* d_flush = nullptr;      // [W][3][k][n] tensor-core flush scratch
+  // DMC: the other half of the walker-state double buffer and the branching scratch
+  double* d_R2 = nullptr;
+  void* d_rows2 = nullptr;
+  void* d_binv2 = nullptr;
+  void* d_jgl2 = nullptr;
+  double* d_logdet2 = nullptr;
+  int* d_sign2 = nullptr;
+  int* d_jvalid2 = nullptr;
+  int* d_mult = nullptr;        // [cap]
+  int* d_src = nullptr;         // [cap]
+  int* d_bout = nullptr;        // [2]
+  double* d_bsums = nullptr;    // [2]
+  double* d_e = nullptr;        // [3][cap]: E_prev, E_new staging, gathered E
   int* d_jvalid = nullptr;      // [W]
   double* d_pend = nullptr;
   double* d_ws = nullptr;
@@ -129,7 +143,9 @@ void free_all(qmc_crowd* c) {
   void* ptrs[] = {c->d_R, c->d_rows, c->d_binv, c->d_logdet, c->d_sign, c->d_table,
                   c->d_jc, c->d_ions, c->d_win_m, c->d_win_P, c->d_win_V, c->d_win_S,
                   c->d_pend_phi, c->d_pend, c->d_ws, c->d_eloc, c->d_nacc, c->d_status,
-                  c->d_io, c->d_io8, c->d_jgl, c->d_jvalid, c->d_flush};
+                  c->d_io, c->d_io8, c->d_jgl, c->d_jvalid, c->d_flush, c->d_R2,
+                  c->d_rows2, c->d_binv2, c->d_jgl2, c->d_logdet2, c->d_sign2, c->d_jvalid2,
+                  c->d_mult, c->d_src, c->d_bout, c->d_bsums, c->d_e};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -351,6 +367,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.G = sys->grid;
   p.GP = sys->grid + 3;
   p.drift = run->drift ? 1 : 0;
+  p.dmc = run->dmc ? 1 : 0;
   p.potential = run->potential ? 1 : 0;
   p.update = run->update;
   p.k = run->update == QMC_UPDATE_DELAYED ? run->delay_rank : 1;
@@ -434,6 +451,20 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   st |= dmalloc(&c->d_pend_phi, (size_t)es * W * 5 * p.n_pad);
   st |= dmalloc(&c->d_jgl, (size_t)es * W * N * 4);
   if (p.tc_flush) st |= dmalloc(&c->d_flush, (size_t)es * W * 3 * p.k * n);
+  if (run->dmc) {
+    st |= dmalloc((void**)&c->d_R2, sizeof(double) * W * N * 3);
+    st |= dmalloc(&c->d_rows2, (size_t)es * W * N * 5 * p.n_pad);
+    st |= dmalloc(&c->d_binv2, (size_t)es * W * 2 * n * n);
+    st |= dmalloc(&c->d_jgl2, (size_t)es * W * N * 4);
+    st |= dmalloc((void**)&c->d_logdet2, sizeof(double) * W * 2);
+    st |= dmalloc((void**)&c->d_sign2, sizeof(int) * W * 2);
+    st |= dmalloc((void**)&c->d_jvalid2, sizeof(int) * W);
+    st |= dmalloc((void**)&c->d_mult, sizeof(int) * W);
+    st |= dmalloc((void**)&c->d_src, sizeof(int) * W);
+    st |= dmalloc((void**)&c->d_bout, sizeof(int) * 2);
+    st |= dmalloc((void**)&c->d_bsums, sizeof(double) * 2);
+    st |= dmalloc((void**)&c->d_e, sizeof(double) * 3 * W);
+  }
   st |= dmalloc((void**)&c->d_jvalid, sizeof(int) * W);
   st |= dmalloc((void**)&c->d_pend, sizeof(double) * W * qmcgb::PEND_STRIDE);
   st |= dmalloc((void**)&c->d_ws, sizeof(double) * W * 2 * 2 * n * n);
@@ -837,6 +868,83 @@ int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, 
   if (b_in_smem) *b_in_smem = c->p.b_in_smem;
   if (stencil_tma) *stencil_tma = c->p.use_tma;
   if (smem_bytes) *smem_bytes = (int)c->smem;
+  return QMC_OK;
+}
+
+int qmc_get_walker_count(const qmc_crowd* c, int* count) {
+  if (!c || !count) return QMC_ERR_INVALID_ARG;
+  *count = c->p.W;
+  return QMC_OK;
+}
+
+int qmc_dmc_branch(qmc_crowd* c, const double* e_prev, double* e_new, int mem, double e_trial,
+                   qmc_dmc_stats* out) {
+  if (!c || !e_prev || !e_new) return QMC_ERR_INVALID_ARG;
+  if (!c->run.dmc) return QMC_ERR_STATE;
+  int st = ensure_ready(c);
+  if (st) return st;
+  const int W = c->p.W, N = c->p.N, cap = c->run.n_walkers, es = c->es;
+  if (c->run.update == QMC_UPDATE_DELAYED) {  // apply pending windows before copying walkers
+    st = move(c, qmcgb::MODE_FLUSH);
+    if (st) return st;
+  }
+  const double* ep = e_prev;
+  const double* en = e_new;
+  if (mem == QMC_MEM_HOST) {
+    CK(cudaMemcpyAsync(c->d_e, e_prev, sizeof(double) * W, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_e + cap, e_new, sizeof(double) * W, cudaMemcpyHostToDevice,
+                       c->stream));
+    ep = c->d_e;
+    en = c->d_e + cap;
+  }
+  const uint32_t gen = c->gen > 0 ? c->gen - 1 : 0;  // the generation just completed
+  st = launch_status(c, qmcgb::launch_branch(ep, en, W, N, c->p.tau, e_trial, c->run.seed, gen,
+                                             cap, c->d_mult, c->d_src, c->d_bout, c->d_bsums,
+                                             c->stream));
+  if (st) return st;
+  int bo[2];
+  double sums[2];
+  CK(cudaMemcpyAsync(bo, c->d_bout, sizeof(bo), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(sums, c->d_bsums, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int n_new = bo[0];
+  if (out) {
+    out->n_before = W;
+    out->n_after = n_new;
+    out->n_wanted = bo[1];
+    out->w_sum = sums[0];
+    out->we_sum = sums[1];
+  }
+  if (n_new == 0) return QMC_ERR_STATE;  // the population died out: the crowd is unchanged
+  const int n = c->p.n;
+  qmcgb::WalkerState from{c->d_R, c->d_rows, c->d_binv, c->d_jgl, c->d_logdet, c->d_sign,
+                          c->d_jvalid, (size_t)N * 3, (size_t)es * N * 5 * c->p.n_pad,
+                          (size_t)es * 2 * n * n, (size_t)es * N * 4};
+  qmcgb::WalkerState to = from;
+  to.R = c->d_R2;
+  to.rows = c->d_rows2;
+  to.binv = c->d_binv2;
+  to.jgl = c->d_jgl2;
+  to.logdet = c->d_logdet2;
+  to.sign = c->d_sign2;
+  to.jvalid = c->d_jvalid2;
+  double* e_out = c->d_e + 2 * (size_t)cap;
+  st = launch_status(c, qmcgb::launch_gather(to, from, c->d_src, n_new, en, e_out, c->stream));
+  if (st) return st;
+  std::swap(c->d_R, c->d_R2);
+  std::swap(c->d_rows, c->d_rows2);
+  std::swap(c->d_binv, c->d_binv2);
+  std::swap(c->d_jgl, c->d_jgl2);
+  std::swap(c->d_logdet, c->d_logdet2);
+  std::swap(c->d_sign, c->d_sign2);
+  std::swap(c->d_jvalid, c->d_jvalid2);
+  CK(cudaMemsetAsync(c->d_pend, 0, sizeof(double) * cap * qmcgb::PEND_STRIDE, c->stream));
+  c->p.W = n_new;
+  sync_params(c);
+  CK(cudaMemcpyAsync(e_new, e_out, sizeof(double) * n_new,
+                     mem == QMC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return QMC_OK;
 }
 

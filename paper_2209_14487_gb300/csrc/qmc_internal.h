@@ -45,6 +45,7 @@ struct Params {
   int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
   int inc_jastrow;          // mixed Sherman-Morrison sweep: incremental Jastrow grad/lap
+  int dmc;                  // fixed node: a move that changes the determinant's sign is rejected
   int eloc_by_gen;          // E_L of generation g goes to eloc_out[(g - eloc_gen0) W + w]
   uint32_t eloc_gen0;
   int stencil_bytes;        // bytes of that copy
@@ -86,6 +87,23 @@ struct Params {
 
 size_t move_smem_bytes(const Params& p, int elem_bytes);
 int max_smem_optin();
+
+// The per-walker state a DMC branching step copies (one half of a double buffer).
+struct WalkerState {
+  double* R;
+  void* rows;
+  void* binv;
+  void* jgl;
+  double* logdet;
+  int* sign;
+  int* jvalid;
+  size_t r_elems, rows_bytes, binv_bytes, jgl_bytes;  // per walker
+};
+cudaError_t launch_branch(const double* e_prev, const double* e_new, int W, int N, double tau,
+                          double e_trial, uint64_t seed, uint32_t gen, int cap, int* mult,
+                          int* src, int* out, double* sums, cudaStream_t s);
+cudaError_t launch_gather(const WalkerState& to, const WalkerState& from, const int* src,
+                          int n_new, const double* e_new, double* e_out, cudaStream_t s);
 
 // tmap: host copy of the table's CUtensorMap (128 bytes), or null when p.use_tma == 0.
 // The move kernel is compiled once per CTA width (p.nt); these dispatch on it.

@@ -956,12 +956,14 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
 }
 
 // Metropolis(-Hastings): A = rho^2 G(r<-r')/G(r'<-r) with drift, rho^2 without;
-// accept iff u < A; rho = 0 or non-finite rejects.
+// accept iff u < A; rho = 0 or non-finite rejects, and with DMC (fixed node) so does a
+// change of the determinant's sign.
 template <typename T>
 __device__ __forceinline__ int metropolis(const Params& p, const Cst<T>& k, const Prop<T>& pr,
                                           const Res<T>& rs, T u) {
   const T rho = rs.rho;
   if (!(rho != T(0)) || !isfinite(rho)) return 0;
+  if (p.dmc && rs.rhoD < T(0)) return 0;  // fixed node: no crossing of a nodal surface
   T A;
   if (p.drift) {
     T gb = 0;

@@ -37,7 +37,7 @@ EXPORTS = [
     "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
     "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
-    "qmc_batch_get_launch_count",
+    "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count",
 ]
 
 
@@ -50,7 +50,13 @@ class qmc_run_desc(C.Structure):
     _fields_ = [("n_walkers", C.c_int), ("precision", C.c_int), ("update", C.c_int),
                 ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("drift", C.c_int),
                 ("potential", C.c_int), ("staging", C.c_int), ("tau", C.c_double),
-                ("seed", C.c_uint64), ("cta_threads", C.c_int), ("engine", C.c_int)]
+                ("seed", C.c_uint64), ("cta_threads", C.c_int), ("engine", C.c_int),
+                ("dmc", C.c_int), ("reserved", C.c_int)]
+
+
+class qmc_dmc_stats(C.Structure):
+    _fields_ = [("n_before", C.c_int), ("n_after", C.c_int), ("n_wanted", C.c_longlong),
+                ("w_sum", C.c_double), ("we_sum", C.c_double)]
 
 
 class qmc_stats(C.Structure):
@@ -97,6 +103,8 @@ def _load():
         "qmc_batch_destroy": [vp],
         "qmc_batch_sweep": [vp, i, vp, vp],
         "qmc_batch_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
+        "qmc_dmc_branch": [vp, vp, vp, i, C.c_double, C.POINTER(qmc_dmc_stats)],
+        "qmc_get_walker_count": [vp, C.POINTER(C.c_int)],
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -154,7 +162,8 @@ class Crowd:
 
     def __init__(self, n_up, n_dn, n_orb, n_ions, grid, L, n_walkers, tau, precision="fp64",
                  update="sm", delay_rank=1, n_recompute=0, drift=True, potential=True,
-                 seed=14487, stream=None, staging="auto", cta_threads=0, engine="auto"):
+                 seed=14487, stream=None, staging="auto", cta_threads=0, engine="auto",
+                 dmc=False):
         self.sys = qmc_system_desc(n_up=n_up, n_dn=n_dn, n_orb=n_orb, n_ions=n_ions, grid=grid,
                                    reserved=0, L=L)
         self.run = qmc_run_desc(
@@ -164,8 +173,10 @@ class Crowd:
             delay_rank=delay_rank, n_recompute=n_recompute, drift=int(drift),
             potential=int(potential), staging=QMC_STAGING_LDG if staging == "ldg" else QMC_STAGING_AUTO,
             tau=tau, seed=seed, cta_threads=cta_threads,
-            engine=QMC_ENGINE_SIMT if engine == "simt" else QMC_ENGINE_AUTO)
+            engine=QMC_ENGINE_SIMT if engine == "simt" else QMC_ENGINE_AUTO,
+            dmc=int(bool(dmc)), reserved=0)
         self.W, self.N, self.n = n_walkers, n_up + n_dn, n_up
+        self.capacity = n_walkers
         h = C.c_void_p()
         _check("qmc_crowd_create",
                lib.qmc_crowd_create(C.byref(self.sys), C.byref(self.run), stream, C.byref(h)))
@@ -174,13 +185,14 @@ class Crowd:
     @classmethod
     def from_workload(cls, wl, precision="fp64", update="sm", delay_rank=1, n_walkers=None,
                       stream=None, n_recompute=None, staging="auto", cta_threads=0,
-                      engine="auto"):
+                      engine="auto", dmc=False, tau=None):
         c = cls(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L,
-                wl.n_walkers if n_walkers is None else n_walkers, wl.tau, precision=precision,
+                wl.n_walkers if n_walkers is None else n_walkers,
+                wl.tau if tau is None else tau, precision=precision,
                 update=update, delay_rank=delay_rank,
                 n_recompute=wl.n_recompute if n_recompute is None else n_recompute,
                 drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream,
-                staging=staging, cta_threads=cta_threads, engine=engine)
+                staging=staging, cta_threads=cta_threads, engine=engine, dmc=dmc)
         if wl.n_ions:
             c.qmc_load_ions(np.ascontiguousarray(wl.ions, dtype=np.float64))
         if wl.j2_uu is not None:
@@ -304,6 +316,26 @@ class Crowd:
                lib.qmc_get_kernel_config(self.h, *[C.byref(x) for x in v]))
         return dict(zip(("b_in_smem", "stencil_tma", "smem_bytes", "cta_threads", "tc_flush"),
                         (x.value for x in v)))
+
+    def qmc_dmc_branch(self, e_prev, e_new, e_trial: float):
+        """DMC reweighting and branching after a generation (host arrays [W]); returns
+        (qmc_dmc_stats, E_L of the new population).  The crowd's walker count changes."""
+        ep = np.ascontiguousarray(e_prev, dtype=np.float64)
+        # the gathered E_L of the new population, up to the capacity
+        en = np.zeros(self.capacity, dtype=np.float64)
+        en[:len(e_new)] = e_new
+        st = qmc_dmc_stats()
+        _check("qmc_dmc_branch", lib.qmc_dmc_branch(self.h, ep.ctypes.data, en.ctypes.data,
+                                                    QMC_MEM_HOST, float(e_trial),
+                                                    C.byref(st)))
+        self.W = st.n_after
+        return st, en[:st.n_after].copy()
+
+    @property
+    def walker_count(self) -> int:
+        v = C.c_int()
+        _check("qmc_get_walker_count", lib.qmc_get_walker_count(self.h, C.byref(v)))
+        return v.value
 
     def qmc_crowd_save(self) -> bytes:
         sz = C.c_size_t()

@@ -473,3 +473,70 @@ def test_potential_and_jastrow_pair_structure_closed_forms(oracle_lib):
                                     j2_K=8, j2_rc=3.0, j2_uu=j2l.coefs, j2_ud=j2.coefs)
     assert abs(osys2.potential(R2) - math.exp(-0.3 ** 2)) < 1e-14  # ion beyond L/2 of both
     assert abs(osys2.jastrow_U(R2) - oracle_lib.radial(j2.coefs, 3.0, 0.3)[0]) < 1e-14
+
+
+# ---- DMC reweighting and branching (Alg. 1 lines 13-14, readings of the scope table) ----
+
+def test_dmc_branch_static_population_at_trial_energy(oracle_lib):
+    """E_prev = E_new = E_T: every weight is 1 and floor(1 + u) = 1 for u in (0, 1), so the
+    population is unchanged and in order."""
+    e = np.full(37, -3.25)
+    src, w = oracle_lib.dmc_branch(e, e, 16, 0.01, -3.25, 99, 4, 100)
+    assert np.array_equal(src, np.arange(37))
+    assert np.allclose(w, 1.0)
+
+
+def test_dmc_branch_multiplicity_is_unbiased_and_ordered(oracle_lib):
+    """floor(w + u) with u uniform has mean w: at weight 1.37 each walker leaves one or two
+    copies, two with probability 0.37; copies of a walker are adjacent, walkers in order."""
+    W, tau, et = 40000, 0.01, 0.0
+    target = 1.37
+    e = np.full(W, et - np.log(target) / tau)
+    src, w = oracle_lib.dmc_branch(e, e, 32, tau, et, 2209, 7, 10 * W)
+    assert np.allclose(w, target, rtol=1e-12)
+    counts = np.bincount(src, minlength=W)
+    assert set(np.unique(counts)) <= {1, 2}
+    assert np.all(np.diff(src) >= 0)
+    sigma = np.sqrt(0.37 * 0.63 / W)
+    assert abs(len(src) / W - target) < 4 * sigma
+
+
+def test_dmc_branch_weight_closed_form_and_cap(oracle_lib):
+    rng = np.random.default_rng(4)
+    ep, en = rng.normal(-2.0, 0.5, 10), rng.normal(-2.0, 0.5, 10)
+    tau, et = 0.05, -1.7
+    full, w = oracle_lib.dmc_branch(ep, en, 8, tau, et, 5, 2, 1000)
+    assert np.allclose(w, np.exp(-tau * ((ep + en) / 2 - et)), rtol=1e-14)
+    cut, _ = oracle_lib.dmc_branch(ep, en, 8, tau, et, 5, 2, 6)
+    assert len(cut) == min(6, len(full))
+    assert np.array_equal(cut, full[:len(cut)])
+
+
+def test_dmc_fixed_node_rejects_a_sign_change(oracle_lib):
+    """A proposal whose determinant ratio is negative with rho^2 above the move's
+    acceptance uniform u is accepted by plain Metropolis without drift (A = rho^2 > u) and
+    rejected under the fixed-node rule."""
+    wl = wl_mod.tiny(n_el=8, n_walkers=1, j1_knots=0, j2_knots=0)
+    wl.drift = False
+    R = wl.positions()
+    plain = oracle_lib.OracleCrowd(oracle_lib.OracleSystem(wl), R)
+    fixed = oracle_lib.OracleCrowd(oracle_lib.OracleSystem(wl, dmc=1), R)
+    rng = np.random.default_rng(8)
+    found = None
+    for iel in range(wl.n_el):  # the electron with the smallest acceptance uniform first
+        _, u = oracle_lib.move_draws(wl.seed, 0, plain.generation, iel)
+        for _ in range(3000):
+            rnew = rng.uniform(0.0, wl.L, size=(1, 3))
+            ratio, _, _, _ = plain.propose(iel, rnew)
+            plain.accept(iel, np.zeros(1, dtype=np.uint8))
+            if ratio[0] < 0.0 and ratio[0] ** 2 > u:
+                found = (iel, rnew)
+                break
+        if found:
+            break
+    assert found is not None
+    iel, rnew = found
+    plain.propose(iel, rnew)
+    assert plain.accept(iel)[0] == 1
+    fixed.propose(iel, rnew)
+    assert fixed.accept(iel)[0] == 0
