@@ -147,7 +147,7 @@ def spline_table(G: int, waves: list, terms: list) -> np.ndarray:
     not depend on L.  Returns float64 [G][G][G][n].
     """
     n = len(terms)
-    out = np.zeros((G, G, G, n), dtype=np.float64)
+    out = np.zeros((n, G, G, G), dtype=np.float64)  # orbital-major while accumulating
     g = np.arange(G)
     for j, tlist in enumerate(terms):
         real_acc = np.zeros((G, G, G), dtype=np.float64)
@@ -167,8 +167,8 @@ def spline_table(G: int, waves: list, terms: list) -> np.ndarray:
                 real_acc += amp * fac * ph.real
             else:
                 real_acc += amp * fac * ph.imag
-        out[..., j] = real_acc
-    return out
+        out[j] = real_acc
+    return np.ascontiguousarray(np.moveaxis(out, 0, -1))
 
 
 def jastrow_coefs(K: int, a: float, rc: float, cusp: float | None) -> Jastrow:
@@ -253,8 +253,15 @@ def mix384() -> Workload:
 
 MIXED_BATCH = (mix64, mix192, mix384)
 
+
+def dmc1536() -> Workload:
+    """1536 electrons (768/768), 768 orbitals on 96^3, 64 ions, L = 22.9, J1 (8 knots) and
+    J2 (10), 512 walkers, DMC time step 0.01, FP64 recompute every 128 generations."""
+    return make_workload("dmc1536", n_el=1536, n_orb=768, grid=96, n_walkers=512, n_gen=100,
+                         n_ions=64, tau=0.01, n_recompute=128, j1_knots=8, j2_knots=10)
+
 WORKLOADS = {"pw16": pw16, "pw128": pw128, "pw512": pw512, "mix64": mix64, "mix192": mix192,
-             "mix384": mix384}
+             "mix384": mix384, "dmc1536": dmc1536}
 
 
 def tiny(n_el: int = 8, n_orb: int | None = None, grid: int = 12, n_walkers: int = 4,
