@@ -206,6 +206,129 @@ def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0
     return {"ms": ms, "plain_ms": plain, "eloc": e, "p_acc": p_acc, "launches": launches}
 
 
+def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, feedback=0.1):
+    """Fixed-node DMC generations of the mixed path: qmc_sweep(1) with E_L read back to the
+    host, then qmc_dmc_branch (reweighting, branching and the device gather of the new
+    population) and the trial-energy feedback E_T = E_est - feedback ln(W / W_target) / tau.
+    The crowd starts full (W = capacity) and W_target = target_frac x capacity.  Each
+    generation is bracketed by CUDA events on the crowd's stream; moves = W x N of that
+    generation."""
+    import torch
+
+    from paper_2209_14487_gb300 import qmcgb
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    cap = wl.n_walkers
+    target = max(1, int(round(target_frac * cap)))
+    c = qmcgb.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
+                                  stream=stream.cuda_stream, cta_threads=nt, dmc=True)
+    c.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+    c.qmc_recompute()
+    e_prev = np.zeros(cap)
+    c.qmc_local_energy_batch(e_prev)
+    e_trial = float(e_prev.mean())
+    ev_s, ev_b, moves, sizes, e_est_hist = [], [], [], [], []
+    launches0 = None
+    for g in range(warmup + steps):
+        timed = g >= warmup
+        if timed and launches0 is None:
+            torch.cuda.synchronize()
+            launches0 = c.launch_count
+        e_new = np.zeros((1, c.W))
+        if timed:
+            flush_buf.add_(1.0)  # evicts the previous generation from L2
+            a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            moves.append(c.W * wl.n_el)
+        c.qmc_sweep(1, e_new, stats=False)
+        if timed:
+            m.record(stream)
+        st, e_prev = c.qmc_dmc_branch(e_prev, e_new[0], e_trial)
+        if timed:
+            b.record(stream)
+            ev_s.append((a, m))
+            ev_b.append((a, b))
+            sizes.append(st.n_after)
+        e_est = st.we_sum / st.w_sum
+        if timed:
+            e_est_hist.append(e_est)
+        e_trial = e_est - feedback * math.log(st.n_after / target) / wl.tau
+    torch.cuda.synchronize()
+    launches = c.launch_count - launches0
+    st2 = c.qmc_sweep(1, None, stats=True)
+    p_acc = st2.n_accept / max(1, st2.n_moves)
+    c.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    return {"ms": [a.elapsed_time(b) for a, b in ev_b],
+            "sweep_ms": [a.elapsed_time(b) for a, b in ev_s], "moves": moves,
+            "sizes": sizes, "e_est": e_est_hist, "p_acc": p_acc, "launches": launches,
+            "capacity": cap, "target": target}
+
+
+def dmc_main(args, wl, ws, rank, cfg):
+    """The --dmc line: fixed-node DMC generations (sweep + branching) of the mixed path."""
+    import torch
+    from paper_2209_14487_gb300 import qmcgb  # noqa: F401
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        uuid = None
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    update, k, nt = args.update, args.delay_rank or 8, args.cta_threads
+    tune_table = None
+    if update == "auto":
+        from paper_2209_14487_gb300 import autotune
+        update, k, tuned_nt, tune_table = autotune.tune(
+            wl, "mixed", candidates=(("sm", 1), ("delayed", 4), ("delayed", 8)), gens=2,
+            widths=(128, 256))
+        nt = nt or tuned_nt
+    elif update == "sm":
+        k = 1
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        r = dmc_path(wl, update, k, args.steps, args.warmup, flush, nt)
+    torch.cuda.synchronize()
+    barrier(ws)
+    value = aggregate_value(sum(r["moves"]), sum(r["ms"]) / 1000.0, ws)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": statistics.mean(r["ms"]),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": dict(cfg, mode="fixed-node DMC: sweep + E_L to host + reweighting, "
+                                    "branching and device gather + E_T feedback",
+                          capacity=r["capacity"], target_walkers=r["target"],
+                          precision="mixed", update=f"{update} k={k}",
+                          cta_threads=nt or "library", parallelism=f"replicas x{ws}")}
+    if tune_table is not None:
+        out["autotune"] = {"ms_per_generation": tune_table, "chosen": f"{update}:{k}:{nt}"}
+    sweep_rate = sum(r["moves"]) / (sum(r["sweep_ms"]) / 1000.0)
+    out["dmc"] = {"sweep_only_value": sweep_rate, "unit": UNIT,
+                  "branch_ms_mean": statistics.mean(b - a for a, b in
+                                                    zip(r["sweep_ms"], r["ms"])),
+                  "walkers_min": min(r["sizes"]), "walkers_max": max(r["sizes"]),
+                  "walkers_mean": statistics.mean(r["sizes"]),
+                  "e_est_mean": statistics.mean(r["e_est"]), "acceptance": r["p_acc"]}
+    hbm, src = peaks()
+    W_mean = statistics.mean(r["moves"]) / wl.n_el
+    bpm = bytes_per_move(wl.n_orb, wl.n_el, 4, r["p_acc"], update, k)
+    achieved = sweep_rate * bpm / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                       "frac": achieved / hbm, "traffic": None,
+                       "kernel": "move_kernel<float> (fused generation)",
+                       "bytes_per_move": bpm, "walkers_mean": W_mean, "peak_source": src}
+    out["gpu_launches"] = r["launches"]
+    out["clocks"] = clk.summary()
+    if rank == 0 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(wl, target_s=10.0, max_gens=1,
+                                              walkers=args.cpu_walkers)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": sample + " (VMC sweep of the oracle)",
+                               "cpu": cpu_model()}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def energy_stats(e: np.ndarray, n_blocks: int = 10):
     blk = e.mean(axis=1)
     nb = min(n_blocks, len(blk))
@@ -247,13 +370,16 @@ def e2e_run(wl, precision, update, k, steps, crowd_id, nt=0):
     return moves / (t1 - t0), h2d / steps, wl.n_walkers * 8
 
 
-def cpu_oracle_rate(wl, target_s=12.0, max_gens=None):
-    """Moves/s of the CPU oracle (as it stands) on a bounded sample of the workload."""
+def cpu_oracle_rate(wl, target_s=12.0, max_gens=None, walkers=None):
+    """Moves/s of the CPU oracle (as it stands) on a bounded sample of the workload: all
+    walkers, or the first `walkers` of them."""
     import oracle
     oracle.build()
     osys = oracle.OracleSystem(wl)
-    W = wl.n_walkers
     R = wl.positions()
+    if walkers:
+        R = np.ascontiguousarray(R[:walkers])
+    W = R.shape[0]
     crowd = oracle.OracleCrowd(osys, R)
     t0 = time.perf_counter()
     crowd.sweep(1)
@@ -296,6 +422,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dmc", action="store_true",
+                    help="fixed-node DMC generations (sweep + branching) instead of VMC")
+    ap.add_argument("--cpu-walkers", type=int, default=None,
+                    help="walkers of the CPU oracle sample (default: all)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -367,6 +497,12 @@ def main():
         uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
     except Exception:
         uuid = None
+    if args.dmc:
+        dmc_main(args, wl, ws, rank, cfg)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
 
     tune_table = None
@@ -433,7 +569,7 @@ def main():
                       "note": "create + host loads (table, ions, Jastrow, positions) + recompute "
                               "+ K sweeps returning E_L to pinned host memory, wall clock"}
     if rank == 0 and not args.no_cpu:
-        rate, cores, sample = cpu_oracle_rate(wl)
+        rate, cores, sample = cpu_oracle_rate(wl, walkers=args.cpu_walkers)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": sample, "cpu": cpu_model()}
     if rank == 0:

@@ -148,26 +148,30 @@ def spline_table(G: int, waves: list, terms: list) -> np.ndarray:
     """
     n = len(terms)
     out = np.zeros((n, G, G, G), dtype=np.float64)  # orbital-major while accumulating
-    g = np.arange(G)
+    th = 2.0 * np.pi * np.arange(G) / G
     for j, tlist in enumerate(terms):
-        real_acc = np.zeros((G, G, G), dtype=np.float64)
-        for q, amp in tlist:
+        # sum over terms of separable products: cos(x+y+z) = c_xy cos z - s_xy sin z and
+        # sin(x+y+z) = s_xy cos z + c_xy sin z, one (G^2 x 2T) (2T x G) product per orbital
+        xy = np.zeros((G, G, 2 * len(tlist)))
+        zz = np.zeros((2 * len(tlist), G))
+        for t, (q, amp) in enumerate(tlist):
             m, kind = waves[q]
+            if kind == "1":
+                xy[:, :, 2 * t] = 1.0
+                zz[2 * t] = amp
+                continue
             fac = 1.0
             for d in range(3):
                 fac *= 3.0 / (2.0 + math.cos(2.0 * math.pi * m[d] / G))
-            if kind == "1":
-                real_acc += amp
-                continue
-            ex = np.exp(2j * np.pi * m[0] * g / G)
-            ey = np.exp(2j * np.pi * m[1] * g / G)
-            ez = np.exp(2j * np.pi * m[2] * g / G)
-            ph = ex[:, None, None] * ey[None, :, None] * ez[None, None, :]
+            a = m[0] * th[:, None] + m[1] * th[None, :]
+            cxy, sxy = np.cos(a), np.sin(a)
+            cz, sz = amp * fac * np.cos(m[2] * th), amp * fac * np.sin(m[2] * th)
+            xy[:, :, 2 * t], xy[:, :, 2 * t + 1] = cxy, sxy
             if kind == "c":
-                real_acc += amp * fac * ph.real
+                zz[2 * t], zz[2 * t + 1] = cz, -sz
             else:
-                real_acc += amp * fac * ph.imag
-        out[j] = real_acc
+                zz[2 * t], zz[2 * t + 1] = sz, cz
+        out[j] = (xy.reshape(G * G, -1) @ zz).reshape(G, G, G)
     return np.ascontiguousarray(np.moveaxis(out, 0, -1))
 
 

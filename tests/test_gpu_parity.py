@@ -490,3 +490,62 @@ def test_pw512_tensor_flush_fine_grained_and_rank_64(Q, oracle_lib, k):
         ref, rsg = osys.logpsi(Rg[w])
         assert abs(la[w] - ref) < 1e-4 * max(1.0, abs(ref)), (w, la[w], ref)
         assert sg[w] == rsg
+
+
+@pytest.mark.parametrize("update,k", [("sm", 1), ("delayed", 8)])
+def test_dmc1536_mixed_sampled(Q, oracle_lib, update, k):
+    """The 1536-electron DMC workload (n = 768 per spin, 96^3 grid, 64 ions) at two
+    walkers: the inverse lives in global memory, each thread has stencil items beyond its
+    four and Jastrow partners beyond its cached slots.  Proposals meet the mixed-path bound
+    against the oracle; after a fixed-node generation log|Psi| and E_L agree with the
+    oracle's FP64 recompute at the GPU's positions and no walker changed its sign."""
+    wl = _dmc1536()
+    W = 2
+    R = np.ascontiguousarray(wl.positions(n_walkers=W))
+    gpu = Q.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
+                                n_walkers=W, dmc=True)
+    gpu.qmc_load_positions(R)
+    gpu.qmc_recompute()
+    _, sign0 = gpu.qmc_get_logpsi()
+    osys = oracle_lib.OracleSystem(wl)
+    osys_abs = oracle_lib.OracleSystem(wl, table=np.abs(wl.table()))
+    orc = oracle_lib.OracleCrowd(osys, R)
+    rng = np.random.default_rng(15)
+    eps32 = 2.0 ** -24
+    n = wl.n_up
+    for iel in [0, n - 1, n, wl.n_el - 1, 400]:
+        rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.1, size=(W, 3)), wl.L)
+        lr, grad = np.zeros(W), np.zeros((W, 3))
+        gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, grad, lr)
+        _, _, o_lr, _ = orc.propose(iel, rnew)
+        s = 0 if iel < n else 1
+        for w in range(W):
+            err = abs(lr[w] - o_lr[w])
+            kap = _ratio_sensitivity(osys_abs, R[w], s * n, orc, w, s, iel - s * n, rnew[w], n)
+            assert err <= max(1e-5 * max(1.0, abs(o_lr[w])), 8 * eps32 * kap), (iel, w, err, kap)
+        acc = np.array([1, 0], dtype=np.uint8)
+        gpu.qmc_accept_reject_batch(iel, acc)
+        orc.accept(iel, acc)
+        R = orc.positions()
+    e = np.zeros((1, W))
+    st = gpu.qmc_sweep(1, e)
+    assert 0.5 < st.n_accept / st.n_moves <= 1.0  # tau = 0.01: almost every move accepted
+    Rg = gpu.qmc_get_positions()
+    la, sg = gpu.qmc_get_logpsi()
+    assert np.array_equal(sg, sign0)  # fixed node
+    for w in range(W):
+        ref, rs = osys.logpsi(Rg[w])
+        assert abs(la[w] - ref) < 1e-4 * max(1, abs(ref)), (w, la[w], ref)
+        assert sg[w] == rs
+        e_ref = osys.local_energy(Rg[w])[0]
+        assert abs(e[0, w] - e_ref) < 1e-3 * max(1, abs(e_ref)), (w, e[0, w], e_ref)
+
+
+_C5 = {}
+
+
+def _dmc1536():
+    # built once per module: the 96^3 x 768 table takes seconds to generate
+    if "wl" not in _C5:
+        _C5["wl"] = wl_mod.dmc1536()
+    return _C5["wl"]
