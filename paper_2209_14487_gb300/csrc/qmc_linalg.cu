@@ -244,7 +244,7 @@ __global__ void wrap_kernel(double* R, size_t n3, double L) {
 template <typename T>
 cudaError_t launch_eval_rows(const Params& p, cudaStream_t s) {
   const size_t bytes = (size_t)16 * p.n_pad * sizeof(T);
-  if (bytes > 48 * 1024) {
+  if (bytes + 1024 > 48 * 1024) {  // the dynamic part plus the kernel's static shared memory
     cudaError_t e = cudaFuncSetAttribute(eval_rows_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

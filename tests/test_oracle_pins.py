@@ -512,6 +512,32 @@ def test_dmc_branch_weight_closed_form_and_cap(oracle_lib):
     assert np.array_equal(cut, full[:len(cut)])
 
 
+def test_dmc_zero_variance_population_is_static(oracle_lib):
+    """Free electrons with analytic plane waves (no Jastrow, no potential): E_L is the
+    constant sum |k|^2 / 2 at every fixed-node DMC step, so with E_T fed back from the
+    weighted estimate every weight is 1 and the population stays the same walkers."""
+    wl, _, exact = _free_electron(oracle_lib, n=7, L=4.3, W=12)
+    waves = wl_mod.real_plane_waves(7)
+    m = np.array([w[0] for w in waves], dtype=np.int32)
+    kind = np.array([{"1": 0, "c": 1, "s": 2}[w[1]] for w in waves], dtype=np.int32)
+    tau, W = 0.01, 12
+    osys = oracle_lib.OracleSystem(wl, analytic_waves=(m, kind), dmc=1, tau=tau)
+    crowd = oracle_lib.OracleCrowd(osys, wl.positions())
+    e_prev = np.array(crowd.local_energy())
+    e_trial = float(e_prev.mean())
+    for g in range(6):
+        e_new, na = crowd.sweep(1)
+        assert na.sum() > 0
+        assert np.allclose(e_new[0], exact, rtol=1e-10)
+        src, w = oracle_lib.dmc_branch(e_prev, e_new[0], wl.n_el, tau, e_trial, wl.seed,
+                                       crowd.generation - 1, 2 * W)
+        assert np.array_equal(src, np.arange(W)), g
+        assert np.allclose(w, 1.0, rtol=0, atol=1e-12)
+        e_est = float((w * e_new[0]).sum() / w.sum())
+        e_trial = e_est - 0.1 * np.log(len(src) / W) / tau
+        e_prev = e_new[0][src]
+
+
 def test_dmc_fixed_node_rejects_a_sign_change(oracle_lib):
     """A proposal whose determinant ratio is negative with rho^2 above the move's
     acceptance uniform u is accepted by plain Metropolis without drift (A = rho^2 > u) and
