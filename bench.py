@@ -279,8 +279,8 @@ def dmc_main(args, wl, ws, rank, cfg):
     if update == "auto":
         from paper_2209_14487_gb300 import autotune
         update, k, tuned_nt, tune_table = autotune.tune(
-            wl, "mixed", candidates=(("sm", 1), ("delayed", 4), ("delayed", 8)), gens=2,
-            widths=(128, 256))
+            wl, "mixed", candidates=(("sm", 1), ("delayed", 8), ("delayed", 16), ("delayed", 32)),
+            gens=2, widths=(128, 256))
         nt = nt or tuned_nt
     elif update == "sm":
         k = 1

@@ -526,12 +526,12 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     float* alo = st + TC_TILE * TC_KC;
     float* bhi = st + 2 * TC_TILE * TC_KC;
     float* blo = st + 3 * TC_TILE * TC_KC;
-    // ---- X = B^T Phi^T - P (per 128-row tile, K = n in chunks of 32)
+    // ---- X = B^T Phi^T - P (per 128-row tile, K = n in chunks of 32; the B^T chunks are
+    // loaded two ahead, so two of them are in flight while a chunk's MMAs run)
     const uint32_t id1 = tc_idesc_tf32((uint32_t)mp);
     for (int r0 = 0; r0 < n; r0 += TC_TILE) {
-      float4 v[TC_PER_T];
-      tc_load_bt(c, r0, 0, v);
-      for (int k0 = 0; k0 < n; k0 += TC_KC) {
+      // stages chunk k0 from v, issues its MMAs, reloads v with chunk k0 + 2 TC_KC, waits
+      auto x_chunk = [&](int k0, float4 (&v)[TC_PER_T]) -> bool {
 #pragma unroll
         for (int q = 0; q < TC_PER_T; ++q) tc_store_split(ahi, alo, c.tid + q * NT, v[q]);
         for (int e = c.tid; e < mp * 8; e += NT) {  // Phi rows l < m, zero rows up to mp
@@ -551,11 +551,20 @@ __device__ void flush_window_tc(Ctx<T>& c) {
         fence_proxy_async_smem();
         __syncthreads();
         if (c.tid == 0) tc_issue_chunk(st, tm, id1, TC_KC / 8, k0 == 0, c.bar + 1);
-        if (k0 + TC_KC < n) tc_load_bt(c, r0, k0 + TC_KC, v);  // in flight during the MMAs
-        if (!tc_wait(c)) {
-          tc_release(c);
-          return;
-        }
+        if (k0 + 2 * TC_KC < n) tc_load_bt(c, r0, k0 + 2 * TC_KC, v);
+        return tc_wait(c);
+      };
+      float4 va[TC_PER_T], vb[TC_PER_T];
+      tc_load_bt(c, r0, 0, va);
+      tc_load_bt(c, r0, TC_KC, vb);  // zeros (no loads) past n
+      bool ok = true;
+      for (int k0 = 0; k0 < n && ok; k0 += 2 * TC_KC) {
+        ok = x_chunk(k0, va);
+        if (ok && k0 + TC_KC < n) ok = x_chunk(k0 + TC_KC, vb);
+      }
+      if (!ok) {
+        tc_release(c);
+        return;
       }
       tc_fence_after_sync();
       // epilogue: row r of the tile is TMEM lane r; warps of one lane quadrant split columns
@@ -585,8 +594,28 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     __syncthreads();
     // ---- B^T -= Y snap (per 128 x 128 output tile, K = mp in chunks of 32)
     const uint32_t id2 = tc_idesc_tf32((uint32_t)TC_TILE);
+    // epilogue geometry: row r of the tile is TMEM lane r; the warps of one lane quadrant
+    // split the columns into EP_IT groups of 16 per thread
+    constexpr int EP_STEP = (NWARP / 4) * 16;
+    constexpr int EP_IT = TC_TILE / EP_STEP;
+    // groups loaded ahead of the MMAs (at 256 threads, whose register cap is 128, half)
+    constexpr int EP_PF = NT >= 256 ? EP_IT / 2 : EP_IT;
     for (int r0 = 0; r0 < n; r0 += TC_TILE) {
       for (int j0 = 0; j0 < n; j0 += TC_TILE) {
+        // this thread's part of the B^T tile, loaded while the operands are staged and the
+        // MMAs run (only the epilogue below writes the tile)
+        const int r = r0 + (c.warp & 3) * 32 + c.lane;
+        const int jb = j0 + (c.warp >> 2) * 16;
+        float4 bt[EP_PF][4];
+#pragma unroll
+        for (int it = 0; it < EP_PF; ++it) {
+          const int j = jb + it * EP_STEP;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)  // n % 4 == 0: whole float4 groups in or out
+            bt[it][q] = (r < n && j + 4 * q < n)
+                            ? __ldcg(reinterpret_cast<const float4*>(c.B + (size_t)r * bs + j) + q)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (int b0 = 0; b0 < mp; b0 += TC_KC) {
           for (int e = c.tid; e < TC_SLOTS; e += NT) {
             int rr, kk;
@@ -619,23 +648,22 @@ __device__ void flush_window_tc(Ctx<T>& c) {
           }
         }
         tc_fence_after_sync();
-        const int r = r0 + (c.warp & 3) * 32 + c.lane;
-        for (int c0 = (c.warp >> 2) * 16; c0 < TC_TILE; c0 += (NWARP / 4) * 16) {
+#pragma unroll
+        for (int it = 0; it < EP_IT; ++it) {
+          const int c0 = (c.warp >> 2) * 16 + it * EP_STEP;
           float d[16];
           tmem_ld16(tm + lane_base + (uint32_t)c0, d);
           const int j = j0 + c0;
-          if (r < n && j < n) {  // n % 4 == 0: whole float4 groups in or out
-            float4* brow = reinterpret_cast<float4*>(c.B + (size_t)r * bs + j);
+          float4* brow = reinterpret_cast<float4*>(c.B + (size_t)r * bs + j);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (j + 4 * q < n) {
-                float4 bv = brow[q];
-                bv.x -= d[4 * q];
-                bv.y -= d[4 * q + 1];
-                bv.z -= d[4 * q + 2];
-                bv.w -= d[4 * q + 3];
-                brow[q] = bv;
-              }
+          for (int q = 0; q < 4; ++q) {
+            if (r < n && j + 4 * q < n) {
+              float4 bv = it < EP_PF ? bt[it < EP_PF ? it : 0][q] : __ldcg(brow + q);
+              bv.x -= d[4 * q];
+              bv.y -= d[4 * q + 1];
+              bv.z -= d[4 * q + 2];
+              bv.w -= d[4 * q + 3];
+              brow[q] = bv;
             }
           }
         }
