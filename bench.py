@@ -370,11 +370,21 @@ def e2e_run(wl, precision, update, k, steps, crowd_id, nt=0):
     return moves / (t1 - t0), h2d / steps, wl.n_walkers * 8
 
 
-def cpu_oracle_rate(wl, target_s=12.0, max_gens=None, walkers=None):
+def cpu_oracle_rate(wl, target_s=12.0, max_gens=None, walkers=None, threads=None):
     """Moves/s of the CPU oracle (as it stands) on a bounded sample of the workload: all
-    walkers, or the first `walkers` of them."""
+    walkers, or the first `walkers` of them; all host threads, or `threads` of them."""
     import oracle
     oracle.build()
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(threads)
+    try:
+        return _cpu_oracle_rate(oracle, wl, target_s, max_gens, walkers)
+    finally:
+        oracle.set_num_threads(all_threads)
+
+
+def _cpu_oracle_rate(oracle, wl, target_s, max_gens, walkers):
     osys = oracle.OracleSystem(wl)
     R = wl.positions()
     if walkers:
@@ -570,8 +580,10 @@ def main():
                               "+ K sweeps returning E_L to pinned host memory, wall clock"}
     if rank == 0 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl, walkers=args.cpu_walkers)
+        r1, _, s1 = cpu_oracle_rate(wl, target_s=5.0, walkers=args.cpu_walkers, threads=1)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": sample, "cpu": cpu_model()}
+                               "sample": sample, "cpu": cpu_model(),
+                               "one_core": {"value": r1, "sample": s1}}
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

@@ -83,6 +83,7 @@ def lib():
         L.or_crowd_get_generation.restype = C.c_uint32
         L.or_crowd_set_generation.argtypes = [C.c_void_p, C.c_uint32]
         L.or_num_threads.restype = C.c_int
+        L.or_set_num_threads.argtypes = [C.c_int]
         L.or_dmc_branch.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                     C.c_double, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p,
                                     C.c_void_p]
@@ -330,3 +331,8 @@ def dmc_branch(e_prev, e_new, n_el: int, tau: float, e_trial: float, seed: int, 
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops over walkers from now on."""
+    lib().or_set_num_threads(int(n))

@@ -956,6 +956,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel regions (n >= 1); no effect without OpenMP. */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 
 /* ------------------------------------------------------------------------------------ */
 /* DMC reweighting and branching (Alg. 1 lines 13-14; the paper gives no formulas, the     */
