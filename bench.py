@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -86,7 +87,9 @@ class ClockSampler:
     def __init__(self, uuid: str | None):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to $QMCGB_CLOCKS_DIR (default: the temporary directory)
+        d = os.environ.get("QMCGB_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -204,6 +207,92 @@ def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0
     c.close()
     torch.cuda.set_stream(torch.cuda.default_stream())
     return {"ms": ms, "plain_ms": plain, "eloc": e, "p_acc": p_acc, "launches": launches}
+
+
+def crowds_path(wl, n_crowds, update, k, steps, warmup, flush_buf, nt=0):
+    """The workload's walkers split over `n_crowds` crowds, each on its own CUDA stream
+    (the batched driver's crowds, Alg. 4): every step enqueues one qmc_sweep(1) per crowd
+    (asynchronous: E_L stays on the device) between a start event the crowds' streams wait
+    on and an end event that waits on all of them."""
+    import dataclasses
+
+    import torch
+    main = torch.cuda.Stream()
+    torch.cuda.set_stream(main)
+    Wc = wl.n_walkers // n_crowds
+    wlc = dataclasses.replace(wl, n_walkers=Wc)
+    streams = [torch.cuda.Stream() for _ in range(n_crowds)]
+    crowds = [make_crowd(wlc, "mixed", update, k, s.cuda_stream, i, nt)
+              for i, s in enumerate(streams)]
+    eloc = [torch.zeros(Wc, dtype=torch.float64, device="cuda") for _ in range(n_crowds)]
+    torch.cuda.synchronize()
+    ms = []
+    for g in range(warmup + steps):
+        flush_buf.add_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        for s in streams:
+            s.wait_event(a)
+        for c, e in zip(crowds, eloc):
+            c.qmc_sweep(1, e, stats=False)
+        for s in streams:
+            d = torch.cuda.Event()
+            d.record(s)
+            main.wait_event(d)
+        b.record(main)
+        if g >= warmup:
+            ms.append((a, b))
+    torch.cuda.synchronize()
+    out = [x.elapsed_time(y) for x, y in ms]
+    for c in crowds:
+        c.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    return out, Wc * n_crowds
+
+
+def scan_main(args, wl, ws, rank, cfg):
+    """Throughput against walkers per GPU (the shape of the paper's Fig. 5 scan) and against
+    the number of crowds the walkers are split into, mixed path."""
+    import dataclasses
+
+    import torch
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        uuid = None
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    update = "sm" if args.update == "auto" else args.update
+    k = 1 if update == "sm" else (args.delay_rank or 8)
+    nt = args.cta_threads
+    walkers = [int(x) for x in args.walker_scan.split(",")] if args.walker_scan else []
+    crowds = [int(x) for x in args.crowds.split(",")] if args.crowds else []
+    scan, cscan = [], []
+    barrier(ws)
+    with ClockSampler(uuid) as clk:
+        for W in walkers:
+            r = time_path(dataclasses.replace(wl, n_walkers=W), "mixed", update, k, args.steps,
+                          args.warmup, rank, flush, nt)
+            plain = r["plain_ms"] or r["ms"]
+            scan.append({"walkers": W, "value": W * wl.n_el / (statistics.mean(r["ms"]) / 1e3),
+                         "ms_per_step": statistics.mean(r["ms"]),
+                         "ms_per_plain_step": statistics.mean(plain)})
+        for C in crowds:
+            ms, Wt = crowds_path(wl, C, update, k, args.steps, args.warmup, flush, nt)
+            cscan.append({"crowds": C, "walkers": Wt,
+                          "value": Wt * wl.n_el / (statistics.mean(ms) / 1e3),
+                          "ms_per_step": statistics.mean(ms)})
+    torch.cuda.synchronize()
+    barrier(ws)
+    head = (scan or cscan)[-1]
+    out = {"metric": METRIC, "value": head["value"] * ws, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": dict(cfg, mode="scan", precision="mixed", update=f"{update} k={k}",
+                          cta_threads=nt or "library", parallelism=f"replicas x{ws}"),
+           "walker_scan": scan, "crowd_scan": cscan, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(out))
 
 
 def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, feedback=0.1):
@@ -436,6 +525,11 @@ def main():
                     help="fixed-node DMC generations (sweep + branching) instead of VMC")
     ap.add_argument("--cpu-walkers", type=int, default=None,
                     help="walkers of the CPU oracle sample (default: all)")
+    ap.add_argument("--walker-scan", default=None,
+                    help="comma-separated walkers per GPU: throughput against crowd size")
+    ap.add_argument("--crowds", default=None,
+                    help="comma-separated crowd counts: the walkers split over crowds on "
+                         "their own streams")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -507,6 +601,12 @@ def main():
         uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
     except Exception:
         uuid = None
+    if args.walker_scan or args.crowds:
+        scan_main(args, wl, ws, rank, cfg)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     if args.dmc:
         dmc_main(args, wl, ws, rank, cfg)
         if ws > 1:
