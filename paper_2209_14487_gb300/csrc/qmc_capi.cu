@@ -209,19 +209,19 @@ bool encode_table_map(qmc_crowd* c) {
   cuuint32_t estr[4] = {1, 1, 1, 1};
   std::memset(&c->tmap, 0, sizeof(c->tmap));
   // the driver's encoder, looked up at run time so the library needs no driver at link
-  // or load time (hosts without a GPU still load it)
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // or load time (hosts without a GPU still load it); looked up once, thread-safely
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                          &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
+        q != cudaDriverEntryPointSuccess) {
       cudaGetLastError();
-      return false;
+      fn = nullptr;
     }
-    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
+    return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }();
+  if (!encode) return false;
   CUresult r = encode(
       &c->tmap, is_mixed(c) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
       c->d_table, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -23,6 +23,7 @@
 #endif
 #include <cuda.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -2103,11 +2104,12 @@ __global__ void __launch_bounds__(NT, 2) move_kernel_batch(const Params* __restr
 // once per process and device; crowds of any size then launch it without resetting it).
 template <typename T, int MODE, int UPD, int BSM>
 static cudaError_t allow_max_smem() {
-  static int done_for = -1;  // one per kernel instantiation
+  static std::atomic<int> done_for{-1};  // one per kernel instantiation (crowds may be
+                                          // driven from several host threads)
   auto kern = move_kernel<T, MODE, UPD, BSM>;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || done_for == dev) return e;
+  if (e != cudaSuccess || done_for.load() == dev) return e;
   int optin = 0;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e == cudaSuccess)
@@ -2169,11 +2171,11 @@ cudaError_t launch_move(const Params& p_in, int mode, const void* tmap, cudaStre
 template <typename T, int UPD>
 static cudaError_t launch_batch_upd(const Params* d_plist, const BatchArgs& a, size_t bytes,
                                     cudaStream_t s) {
-  static int done_for = -1;
+  static std::atomic<int> done_for{-1};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (done_for != dev) {
+  if (done_for.load() != dev) {
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int avail = optin - (int)sizeof(Params) - 16;  // the static Params copy
