@@ -153,6 +153,17 @@ def reduce_max(x: float, ws: int) -> float:
     return float(t.item())
 
 
+def reduce_sum(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def aggregate_value(units_per_rank: float, seconds_local: float, ws: int) -> float:
     """Whole-job throughput: every rank processes `units_per_rank`; the job takes as long
     as the slowest rank."""
@@ -295,27 +306,31 @@ def scan_main(args, wl, ws, rank, cfg):
         print(json.dumps(out))
 
 
-def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, feedback=0.1):
+def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, feedback=0.1,
+             ws=1, crowd_id=0):
     """Fixed-node DMC generations of the mixed path: qmc_sweep(1) with E_L read back to the
     host, then qmc_dmc_branch (reweighting, branching and the device gather of the new
     population) and the trial-energy feedback E_T = E_est - feedback ln(W / W_target) / tau.
-    The crowd starts full (W = capacity) and W_target = target_frac x capacity.  Each
-    generation is bracketed by CUDA events on the crowd's stream; moves = W x N of that
-    generation."""
+    The crowd starts full (W = capacity) and W_target = target_frac x capacity.  With
+    several ranks E_est and W are the whole population's and the ranks even out their
+    walkers after each branching (population.exchange).  Each generation is bracketed by
+    CUDA events on the crowd's stream; moves = W x N of that generation."""
     import torch
 
-    from paper_2209_14487_gb300 import qmcgb
+    from paper_2209_14487_gb300 import population, qmcgb
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     cap = wl.n_walkers
     target = max(1, int(round(target_frac * cap)))
     c = qmcgb.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
                                   stream=stream.cuda_stream, cta_threads=nt, dmc=True)
-    c.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+    c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=crowd_id)))
     c.qmc_recompute()
     e_prev = np.zeros(cap)
     c.qmc_local_energy_batch(e_prev)
     e_trial = float(e_prev.mean())
+    if ws > 1:
+        e_trial, _ = population.global_estimate(float(cap), float(e_prev.sum()), cap)
     ev_s, ev_b, moves, sizes, e_est_hist = [], [], [], [], []
     launches0 = None
     for g in range(warmup + steps):
@@ -333,15 +348,19 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
         if timed:
             m.record(stream)
         st, e_prev = c.qmc_dmc_branch(e_prev, e_new[0], e_trial)
+        if ws > 1:
+            e_est, n_all = population.global_estimate(st.w_sum, st.we_sum, st.n_after)
+            e_trial = population.trial_energy(e_est, n_all, ws * target, wl.tau, feedback)
+            e_prev = population.exchange(c, e_prev)
+        else:
+            e_est = st.we_sum / st.w_sum
+            e_trial = population.trial_energy(e_est, st.n_after, target, wl.tau, feedback)
         if timed:
             b.record(stream)
             ev_s.append((a, m))
             ev_b.append((a, b))
             sizes.append(st.n_after)
-        e_est = st.we_sum / st.w_sum
-        if timed:
             e_est_hist.append(e_est)
-        e_trial = e_est - feedback * math.log(st.n_after / target) / wl.tau
     torch.cuda.synchronize()
     launches = c.launch_count - launches0
     st2 = c.qmc_sweep(1, None, stats=True)
@@ -376,10 +395,11 @@ def dmc_main(args, wl, ws, rank, cfg):
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(uuid) as clk:
-        r = dmc_path(wl, update, k, args.steps, args.warmup, flush, nt)
+        r = dmc_path(wl, update, k, args.steps, args.warmup, flush, nt, ws=ws, crowd_id=rank)
     torch.cuda.synchronize()
     barrier(ws)
-    value = aggregate_value(sum(r["moves"]), sum(r["ms"]) / 1000.0, ws)
+    # DMC populations differ between ranks: all ranks' moves over the slowest rank's time
+    value = reduce_sum(float(sum(r["moves"])), ws) / reduce_max(sum(r["ms"]) / 1000.0, ws)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": statistics.mean(r["ms"]),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -245,6 +245,24 @@ int qmc_dmc_branch(qmc_crowd* crowd, const double* e_prev, double* e_new, int me
 /* Active walkers of the crowd (n_walkers unless DMC branching changed it). */
 int qmc_get_walker_count(const qmc_crowd* crowd, int* count);
 
+/* ---------------------------------------------------------------------------------------
+ * Population edits for walker exchange between crowds (one crowd per GPU; Sec. III's
+ * walkers are independent, so any walker may move to any crowd of the same system).
+ *
+ * qmc_dmc_select: the new population is walkers src[0..n_new) of the current one, in
+ * that order, repeats allowed (each copy carries the walker's full state, as in
+ * qmc_dmc_branch); pending delayed windows are applied first.  src: int [n_new] (mem),
+ * every entry in [0, W); 1 <= n_new <= capacity.  Needs run.dmc.  Synchronous.
+ * Errors: INVALID_ARG (a bad index or size: nothing changes), STATE (no DMC crowd).
+ *
+ * qmc_dmc_append: m walkers join at slots W..W+m-1 with positions R: double [m][N][3]
+ * (mem), wrapped into the cell; their orbital rows and inverses are built (FP64
+ * recompute) and nothing of the other walkers changes.  W + m <= capacity.  Synchronous.
+ * Errors: INVALID_ARG; SINGULAR (a joining walker's Slater matrix is singular).
+ * --------------------------------------------------------------------------------------- */
+int qmc_dmc_select(qmc_crowd* crowd, const int* src, int n_new, int mem);
+int qmc_dmc_append(qmc_crowd* crowd, const double* R, int m, int mem);
+
 /* Text of the CUDA error behind the calling thread's last QMC_ERR_CUDA ("no error" if none). */
 const char* qmc_last_cuda_error(void);
 

@@ -191,6 +191,8 @@ int launch_status(qmc_crowd* c, cudaError_t e) {
   return e == cudaSuccess ? QMC_OK : cuda_fail(e);
 }
 
+int gather_population(qmc_crowd* c, int n_new, const double* e_in, double* e_out);
+
 int move(qmc_crowd* c, int mode) {
   const void* tm = c->p.use_tma ? (const void*)&c->tmap : nullptr;
   if (is_mixed(c)) return launch_status(c, qmcgb::launch_move<float>(c->p, mode, tm, c->stream));
@@ -877,13 +879,111 @@ int qmc_get_walker_count(const qmc_crowd* c, int* count) {
   return QMC_OK;
 }
 
+int qmc_dmc_select(qmc_crowd* c, const int* src, int n_new, int mem) {
+  if (!c || !src || n_new < 1 || n_new > c->run.n_walkers) return QMC_ERR_INVALID_ARG;
+  if (mem != QMC_MEM_HOST && mem != QMC_MEM_DEVICE) return QMC_ERR_INVALID_ARG;
+  if (!c->run.dmc) return QMC_ERR_STATE;
+  int st = ensure_ready(c);
+  if (st) return st;
+  // every index is checked on the host before the gather reads with it
+  std::vector<int> h(n_new);
+  if (mem == QMC_MEM_DEVICE) {
+    CK(cudaMemcpyAsync(h.data(), src, sizeof(int) * n_new, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(h.data(), src, sizeof(int) * n_new);
+  }
+  for (int v : h)
+    if (v < 0 || v >= c->p.W) return QMC_ERR_INVALID_ARG;
+  if (c->run.update == QMC_UPDATE_DELAYED) {  // apply pending windows before copying walkers
+    st = move(c, qmcgb::MODE_FLUSH);
+    if (st) return st;
+  }
+  CK(cudaMemcpyAsync(c->d_src, h.data(), sizeof(int) * n_new, cudaMemcpyHostToDevice,
+                     c->stream));
+  st = gather_population(c, n_new, nullptr, nullptr);
+  if (st) return st;
+  return read_status(c);
+}
+
+int qmc_dmc_append(qmc_crowd* c, const double* R, int m, int mem) {
+  if (!c || !R || m < 1) return QMC_ERR_INVALID_ARG;
+  if (mem != QMC_MEM_HOST && mem != QMC_MEM_DEVICE) return QMC_ERR_INVALID_ARG;
+  const int W = c->p.W, N = c->p.N;
+  if (W + m > c->run.n_walkers) return QMC_ERR_INVALID_ARG;
+  int st = ensure_ready(c);
+  if (st) return st;
+  const size_t off = (size_t)W * N * 3, n3 = (size_t)m * N * 3;
+  CK(cudaMemcpyAsync(c->d_R + off, R, n3 * sizeof(double),
+                     mem == QMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R + off, n3, c->p.L, c->stream));
+  if (st) return st;
+  // the new walkers' orbital rows and FP64 inverses, nobody else's
+  if (is_mixed(c)) st = launch_status(c, qmcgb::launch_eval_rows<float>(c->p, c->stream, W, m));
+  else st = launch_status(c, qmcgb::launch_eval_rows<double>(c->p, c->stream, W, m));
+  if (st) return st;
+  if (is_mixed(c))
+    st = launch_status(c, qmcgb::launch_recompute<float>(c->p, c->d_ws, c->stream, W, m));
+  else
+    st = launch_status(c, qmcgb::launch_recompute<double>(c->p, c->d_ws, c->stream, W, m));
+  if (st) return st;
+  CK(cudaMemsetAsync(c->d_pend + (size_t)W * qmcgb::PEND_STRIDE, 0,
+                     sizeof(double) * m * qmcgb::PEND_STRIDE, c->stream));
+  CK(cudaMemsetAsync(c->d_jvalid + W, 0, sizeof(int) * m, c->stream));
+  c->p.W = W + m;
+  sync_params(c);
+  return read_status(c);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The new population is walkers d_src[0..n_new) of the current one: their whole state is
+// gathered into the idle half of the double buffer, the halves swap, and the pending
+// proposals are dropped.  e_in/e_out: optional device E_L carried along.
+int gather_population(qmc_crowd* c, int n_new, const double* e_in, double* e_out) {
+  const int N = c->p.N, n = c->p.n, es = c->es;
+  qmcgb::WalkerState from{c->d_R, c->d_rows, c->d_binv, c->d_jgl, c->d_logdet, c->d_sign,
+                          c->d_jvalid, (size_t)N * 3, (size_t)es * N * 5 * c->p.n_pad,
+                          (size_t)es * 2 * n * n, (size_t)es * N * 4};
+  qmcgb::WalkerState to = from;
+  to.R = c->d_R2;
+  to.rows = c->d_rows2;
+  to.binv = c->d_binv2;
+  to.jgl = c->d_jgl2;
+  to.logdet = c->d_logdet2;
+  to.sign = c->d_sign2;
+  to.jvalid = c->d_jvalid2;
+  int st = launch_status(c, qmcgb::launch_gather(to, from, c->d_src, n_new, e_in, e_out,
+                                                 c->stream));
+  if (st) return st;
+  std::swap(c->d_R, c->d_R2);
+  std::swap(c->d_rows, c->d_rows2);
+  std::swap(c->d_binv, c->d_binv2);
+  std::swap(c->d_jgl, c->d_jgl2);
+  std::swap(c->d_logdet, c->d_logdet2);
+  std::swap(c->d_sign, c->d_sign2);
+  std::swap(c->d_jvalid, c->d_jvalid2);
+  CK(cudaMemsetAsync(c->d_pend, 0, sizeof(double) * c->run.n_walkers * qmcgb::PEND_STRIDE,
+                     c->stream));
+  c->p.W = n_new;
+  sync_params(c);
+  return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int qmc_dmc_branch(qmc_crowd* c, const double* e_prev, double* e_new, int mem, double e_trial,
                    qmc_dmc_stats* out) {
   if (!c || !e_prev || !e_new) return QMC_ERR_INVALID_ARG;
   if (!c->run.dmc) return QMC_ERR_STATE;
   int st = ensure_ready(c);
   if (st) return st;
-  const int W = c->p.W, N = c->p.N, cap = c->run.n_walkers, es = c->es;
+  const int W = c->p.W, N = c->p.N, cap = c->run.n_walkers;
   if (c->run.update == QMC_UPDATE_DELAYED) {  // apply pending windows before copying walkers
     st = move(c, qmcgb::MODE_FLUSH);
     if (st) return st;
@@ -916,31 +1016,9 @@ int qmc_dmc_branch(qmc_crowd* c, const double* e_prev, double* e_new, int mem, d
     out->we_sum = sums[1];
   }
   if (n_new == 0) return QMC_ERR_STATE;  // the population died out: the crowd is unchanged
-  const int n = c->p.n;
-  qmcgb::WalkerState from{c->d_R, c->d_rows, c->d_binv, c->d_jgl, c->d_logdet, c->d_sign,
-                          c->d_jvalid, (size_t)N * 3, (size_t)es * N * 5 * c->p.n_pad,
-                          (size_t)es * 2 * n * n, (size_t)es * N * 4};
-  qmcgb::WalkerState to = from;
-  to.R = c->d_R2;
-  to.rows = c->d_rows2;
-  to.binv = c->d_binv2;
-  to.jgl = c->d_jgl2;
-  to.logdet = c->d_logdet2;
-  to.sign = c->d_sign2;
-  to.jvalid = c->d_jvalid2;
   double* e_out = c->d_e + 2 * (size_t)cap;
-  st = launch_status(c, qmcgb::launch_gather(to, from, c->d_src, n_new, en, e_out, c->stream));
+  st = gather_population(c, n_new, en, e_out);
   if (st) return st;
-  std::swap(c->d_R, c->d_R2);
-  std::swap(c->d_rows, c->d_rows2);
-  std::swap(c->d_binv, c->d_binv2);
-  std::swap(c->d_jgl, c->d_jgl2);
-  std::swap(c->d_logdet, c->d_logdet2);
-  std::swap(c->d_sign, c->d_sign2);
-  std::swap(c->d_jvalid, c->d_jvalid2);
-  CK(cudaMemsetAsync(c->d_pend, 0, sizeof(double) * cap * qmcgb::PEND_STRIDE, c->stream));
-  c->p.W = n_new;
-  sync_params(c);
   CK(cudaMemcpyAsync(e_new, e_out, sizeof(double) * n_new,
                      mem == QMC_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                      c->stream));

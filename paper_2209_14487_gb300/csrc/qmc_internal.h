@@ -131,10 +131,12 @@ QMCGB_DECLARE_MOVE_WIDTH(nt128)
 QMCGB_DECLARE_MOVE_WIDTH(nt160)
 QMCGB_DECLARE_MOVE_WIDTH(nt256)
 #undef QMCGB_DECLARE_MOVE_WIDTH
+// walkers [w0, w0 + count) (count < 0: through p.W)
 template <typename T>
-cudaError_t launch_eval_rows(const Params& p, cudaStream_t s);
+cudaError_t launch_eval_rows(const Params& p, cudaStream_t s, int w0 = 0, int count = -1);
 template <typename T>
-cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s);
+cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s, int w0 = 0,
+                             int count = -1);
 template <typename T>
 cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int n_orb,
                              cudaStream_t s);

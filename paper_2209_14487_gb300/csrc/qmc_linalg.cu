@@ -8,15 +8,16 @@
 
 namespace qmcgb {
 
-// One CTA per (walker, electron): phi, grad phi, lap phi of the occupied orbitals at r_i.
+// One CTA per (walker, electron) of walkers w0, w0 + 1, ...: phi, grad phi, lap phi of the
+// occupied orbitals at r_i.
 template <typename T>
-__global__ void __launch_bounds__(LA_NT) eval_rows_kernel(const Params p) {
+__global__ void __launch_bounds__(LA_NT) eval_rows_kernel(const Params p, int w0) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* part = (T*)smem;  // [16][n_pad]
   __shared__ T wts[48];
   __shared__ int cell[3];
   __shared__ T tt[3];
-  const int w = blockIdx.x / p.N, i = blockIdx.x - w * p.N;
+  const int wl = blockIdx.x / p.N, i = blockIdx.x - wl * p.N, w = w0 + wl;
   const int n = p.n, n_pad = p.n_pad;
   if (threadIdx.x < 3) {
     const int d = threadIdx.x;
@@ -54,19 +55,19 @@ __global__ void __launch_bounds__(LA_NT) eval_rows_kernel(const Params p) {
   }
 }
 
-// One CTA per (walker, spin): FP64 LU with partial pivoting (row exchanges) of A_s, then
-// the columns of A_s^-1 by forward/back substitution; writes B^T = (A^-1)^T in the
-// crowd's precision, log|det A_s| and its sign, and empties the delayed window.
-// `ws` is scratch: 2 n^2 doubles per (walker, spin).
+// One CTA per (walker, spin) of walkers w0, w0 + 1, ...: FP64 LU with partial pivoting
+// (row exchanges) of A_s, then the columns of A_s^-1 by forward/back substitution; writes
+// B^T = (A^-1)^T in the crowd's precision, log|det A_s| and its sign, and empties the
+// delayed window.  `ws` is scratch: 2 n^2 doubles per CTA.
 template <typename T>
-__global__ void __launch_bounds__(LA_NT) recompute_kernel(const Params p, double* ws) {
+__global__ void __launch_bounds__(LA_NT) recompute_kernel(const Params p, double* ws, int w0) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* piv = (int*)smem;  // [n]
   __shared__ double red_v[LA_NWARP];
   __shared__ int red_i[LA_NWARP];
   __shared__ int s_piv, s_sing, s_sign;
   __shared__ double s_logabs;
-  const int ws_id = blockIdx.x, w = ws_id / 2, s = ws_id - 2 * w;
+  const int ws_id = blockIdx.x, s = ws_id & 1, w = w0 + (ws_id >> 1);
   const int n = p.n, n_pad = p.n_pad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* LU = ws + (size_t)ws_id * 2 * n * n;
@@ -242,20 +243,24 @@ __global__ void wrap_kernel(double* R, size_t n3, double L) {
 }
 
 template <typename T>
-cudaError_t launch_eval_rows(const Params& p, cudaStream_t s) {
+cudaError_t launch_eval_rows(const Params& p, cudaStream_t s, int w0, int count) {
+  if (count < 0) count = p.W - w0;
+  if (count <= 0) return cudaSuccess;
   const size_t bytes = (size_t)16 * p.n_pad * sizeof(T);
   if (bytes + 1024 > 48 * 1024) {  // the dynamic part plus the kernel's static shared memory
     cudaError_t e = cudaFuncSetAttribute(eval_rows_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
-  eval_rows_kernel<T><<<p.W * p.N, LA_NT, bytes, s>>>(p);
+  eval_rows_kernel<T><<<count * p.N, LA_NT, bytes, s>>>(p, w0);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s) {
-  recompute_kernel<T><<<p.W * 2, LA_NT, (size_t)p.n * sizeof(int), s>>>(p, ws);
+cudaError_t launch_recompute(const Params& p, double* ws, cudaStream_t s, int w0, int count) {
+  if (count < 0) count = p.W - w0;
+  if (count <= 0) return cudaSuccess;
+  recompute_kernel<T><<<count * 2, LA_NT, (size_t)p.n * sizeof(int), s>>>(p, ws, w0);
   return cudaGetLastError();
 }
 
@@ -277,10 +282,10 @@ cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s
   return cudaGetLastError();
 }
 
-template cudaError_t launch_eval_rows<double>(const Params&, cudaStream_t);
-template cudaError_t launch_eval_rows<float>(const Params&, cudaStream_t);
-template cudaError_t launch_recompute<double>(const Params&, double*, cudaStream_t);
-template cudaError_t launch_recompute<float>(const Params&, double*, cudaStream_t);
+template cudaError_t launch_eval_rows<double>(const Params&, cudaStream_t, int, int);
+template cudaError_t launch_eval_rows<float>(const Params&, cudaStream_t, int, int);
+template cudaError_t launch_recompute<double>(const Params&, double*, cudaStream_t, int, int);
+template cudaError_t launch_recompute<float>(const Params&, double*, cudaStream_t, int, int);
 template cudaError_t launch_pad_table<double>(const Params&, const void*, int, int, cudaStream_t);
 template cudaError_t launch_pad_table<float>(const Params&, const void*, int, int, cudaStream_t);
 template cudaError_t launch_jastrow_U<double>(const Params&, double*, cudaStream_t);

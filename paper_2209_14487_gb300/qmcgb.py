@@ -37,7 +37,8 @@ EXPORTS = [
     "qmc_get_generation", "qmc_set_generation", "qmc_get_launch_count", "qmc_crowd_save",
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
     "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
-    "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count",
+    "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count", "qmc_dmc_select",
+    "qmc_dmc_append",
 ]
 
 
@@ -105,6 +106,8 @@ def _load():
         "qmc_batch_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
         "qmc_dmc_branch": [vp, vp, vp, i, C.c_double, C.POINTER(qmc_dmc_stats)],
         "qmc_get_walker_count": [vp, C.POINTER(C.c_int)],
+        "qmc_dmc_select": [vp, vp, i, i],
+        "qmc_dmc_append": [vp, vp, i, i],
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -143,7 +146,8 @@ def _buf(x, dtype=np.float64):
     except ImportError as e:  # pragma: no cover
         raise TypeError("expected a numpy array or a torch tensor") from e
     if isinstance(x, torch.Tensor):
-        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.uint8: torch.uint8,
+               np.int32: torch.int32}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             raise TypeError(f"expected a contiguous {tdt} tensor")
         return x.data_ptr(), (QMC_MEM_DEVICE if x.is_cuda else QMC_MEM_HOST), x
@@ -330,6 +334,22 @@ class Crowd:
                                                     C.byref(st)))
         self.W = st.n_after
         return st, en[:st.n_after].copy()
+
+    def qmc_dmc_select(self, src):
+        """The new population is walkers src (indices into the current one, in order)."""
+        if not hasattr(src, "data_ptr"):  # anything but a torch tensor: a host int32 copy
+            src = np.ascontiguousarray(src, dtype=np.int32)
+        p, m, keep = _buf(src, np.int32)
+        n_new = int(keep.shape[0])
+        _check("qmc_dmc_select", lib.qmc_dmc_select(self.h, p, n_new, m))
+        self.W = n_new
+
+    def qmc_dmc_append(self, R):
+        """Walkers with positions R [m][N][3] join the crowd (their inverses are built)."""
+        p, m, keep = _buf(R)
+        n_add = int(keep.shape[0])
+        _check("qmc_dmc_append", lib.qmc_dmc_append(self.h, p, n_add, m))
+        self.W += n_add
 
     @property
     def walker_count(self) -> int:

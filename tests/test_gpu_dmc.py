@@ -121,3 +121,54 @@ def test_dmc_mixed_population_control(Q):
         e_trial = e_est - np.log(st.n_after / target) / TAU * 0.1
     assert c.walker_count == sizes[-1] == c.W
     assert 0.5 * target <= np.mean(sizes[-10:]) <= cap, sizes
+
+
+@pytest.mark.parametrize("precision,update,k", [("fp64", "sm", 1), ("mixed", "delayed", 8)])
+def test_select_and_append_walkers(Q, oracle_lib, precision, update, k):
+    """qmc_dmc_select keeps walkers src in order with their whole state; qmc_dmc_append adds
+    walkers whose rows and inverses are built on arrival, leaving the others untouched.
+    The FP64 crowd then sweeps exactly as an oracle crowd started from its positions."""
+    wl = _system()
+    gpu = Q.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
+                                dmc=True)
+    gpu.qmc_load_positions(np.ascontiguousarray(wl.positions()))
+    gpu.qmc_recompute()
+    gpu.qmc_sweep(1, np.zeros((1, gpu.W)))
+    R1 = gpu.qmc_get_positions()
+    la1, sg1 = gpu.qmc_get_logpsi()
+    src = [5, 5, 0, 17, 3, 22, 9]
+    gpu.qmc_dmc_select(src)
+    assert gpu.W == gpu.walker_count == len(src)
+    R2 = gpu.qmc_get_positions()
+    la2, sg2 = gpu.qmc_get_logpsi()
+    assert np.array_equal(R2, R1[src])
+    assert np.array_equal(la2, la1[src]) and np.array_equal(sg2, sg1[src])
+    # bad requests change nothing
+    for bad in ([0, 7], [-1]):
+        with pytest.raises(Q.QmcError):
+            gpu.qmc_dmc_select(bad)
+    with pytest.raises(Q.QmcError):
+        gpu.qmc_dmc_append(np.zeros((wl.n_walkers, wl.n_el, 3)))
+    assert gpu.walker_count == len(src)
+    Rn = np.ascontiguousarray(wl.positions(crowd_id=3, n_walkers=5))
+    gpu.qmc_dmc_append(Rn)
+    assert gpu.W == gpu.walker_count == 12
+    R3 = gpu.qmc_get_positions()
+    la3, sg3 = gpu.qmc_get_logpsi()
+    assert np.array_equal(R3[:7], R2) and np.array_equal(la3[:7], la2)
+    assert np.allclose(R3[7:], np.mod(Rn, wl.L), rtol=0, atol=1e-12)
+    osys = oracle_lib.OracleSystem(wl, dmc=1, update=1 if update == "delayed" else 0,
+                                   delay_rank=k)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for w in range(7, 12):
+        ref, rs = osys.logpsi(R3[w])
+        assert abs(la3[w] - ref) <= tol * max(1.0, abs(ref)) and sg3[w] == rs
+    if precision == "fp64":
+        gen = gpu.generation
+        e = np.zeros((1, 12))
+        gpu.qmc_sweep(1, e)
+        orc = oracle_lib.OracleCrowd(osys, np.ascontiguousarray(R3))
+        orc.generation = gen
+        e_or, _ = orc.sweep(1)
+        assert np.allclose(e, e_or, rtol=1e-9)
+        assert np.allclose(gpu.qmc_get_positions(), orc.positions(), rtol=0, atol=1e-12)

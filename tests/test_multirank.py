@@ -46,3 +46,27 @@ def test_two_rank_aggregation_gloo():
         assert v == pytest.approx(2 * 1000.0 / 3.0)   # slowest rank sets the time
         assert m == 11.0
         assert env == (2, rank, rank)
+
+
+def _sum_worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    q.put((rank, bench.reduce_sum([3.0, 4.5][rank], ws)))
+    dist.destroy_process_group()
+
+
+def test_two_rank_sum_gloo():
+    """DMC populations differ between ranks: the job's moves are the sum over ranks."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_sum_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [v for _, v in out] == [7.5, 7.5]
