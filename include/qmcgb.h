@@ -246,6 +246,21 @@ int qmc_dmc_branch(qmc_crowd* crowd, const double* e_prev, double* e_new, int me
 int qmc_get_walker_count(const qmc_crowd* crowd, int* count);
 
 /* ---------------------------------------------------------------------------------------
+ * Nonlocal pseudopotential in E_L (the locality approximation; the paper's NiO runs use
+ * pseudopotentials, its text gives no form, so the channels are synthetic Gaussians):
+ * every ion carries channels l = 0..n_l-1 with v_l(r) = amp[l] exp(-(r / width[l])^2) for
+ * r < rc.  Each electron i within rc of ion I (d = r_i - R_I, minimum image, r = |d|) adds
+ *   sum_l v_l(r) (2l+1) (1/12) sum_q P_l(d.u_q / r) Psi(r_i -> R_I + r u_q) / Psi(R)
+ * over the 12 vertices u_q of an icosahedron in a fixed orientation ((0, +-1, +-phi)
+ * normalised and its cyclic shifts), P_0 = 1, P_1 = x, P_2 = (3x^2 - 1) / 2.  Every E_L the
+ * crowd computes from then on includes it (one extra launch per E_L); batches of crowds
+ * (qmc_batch_*) do not serve it and return UNSUPPORTED.  n_l = 0 removes it.
+ * amp, width: double [n_l] (host); 0 <= n_l <= 3; width > 0; 0 < rc <= L/2.
+ * Errors: INVALID_ARG (nothing changes).
+ * --------------------------------------------------------------------------------------- */
+int qmc_load_nlpp(qmc_crowd* crowd, int n_l, const double* amp, const double* width, double rc);
+
+/* ---------------------------------------------------------------------------------------
  * Population edits for walker exchange between crowds (one crowd per GPU; Sec. III's
  * walkers are independent, so any walker may move to any crowd of the same system).
  *

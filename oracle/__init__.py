@@ -39,6 +39,8 @@ class System(C.Structure):
         ("table", C.c_void_p), ("ions", C.c_void_p), ("j2_uu", C.c_void_p),
         ("j2_ud", C.c_void_p), ("j1", C.c_void_p), ("pw_m", C.c_void_p),
         ("pw_kind", C.c_void_p),
+        ("nl_n", C.c_int), ("nl_pad", C.c_int), ("nl_rc", C.c_double),
+        ("nl_a", C.c_double * 3), ("nl_s", C.c_double * 3),
     ]
 
 
@@ -83,6 +85,8 @@ def lib():
         L.or_crowd_get_generation.restype = C.c_uint32
         L.or_crowd_set_generation.argtypes = [C.c_void_p, C.c_uint32]
         L.or_num_threads.restype = C.c_int
+        L.or_nlpp.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+        L.or_nlpp.restype = C.c_double
         L.or_set_num_threads.argtypes = [C.c_int]
         L.or_dmc_branch.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double,
                                     C.c_double, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p,
@@ -132,6 +136,12 @@ class OracleSystem:
             self.pw_kind = np.ascontiguousarray(kind, dtype=np.int32)
             s.analytic = 1
             s.pw_m, s.pw_kind = _p(self.pw_m), _p(self.pw_kind)
+        nlpp = override.pop("nlpp", None)
+        if nlpp is not None:  # (amplitudes a_l, widths s_l, cutoff): channels l = 0..
+            amps, widths, rc = nlpp
+            s.nl_n, s.nl_rc = len(amps), float(rc)
+            s.nl_a = (C.c_double * 3)(*amps)
+            s.nl_s = (C.c_double * 3)(*widths)
         for k, v in override.items():
             if isinstance(v, np.ndarray):
                 self._keep.append(v)
@@ -170,6 +180,12 @@ class OracleSystem:
     def potential(self, R):
         R = np.ascontiguousarray(R, dtype=np.float64)
         return lib().or_potential(self.ref, _p(R))
+
+    def nlpp(self, R, direct: bool = False) -> float:
+        """The nonlocal term of E_L at R: ratios from full recomputes of log|Psi|
+        (direct) or from the inverse's columns."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        return lib().or_nlpp(self.ref, _p(R), int(direct))
 
     def local_energy(self, R):
         """(E_L, grad log Psi [N][3], lap log Psi [N]) by full recompute."""

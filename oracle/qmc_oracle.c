@@ -52,6 +52,10 @@ typedef struct or_system {
   const double* j1;     /* [j1_K] electron-ion functor                           */
   const int* pw_m;      /* [n_orb][3] integer wave vectors (analytic mode)       */
   const int* pw_kind;   /* [n_orb]: 0 constant, 1 cos, 2 sin (analytic mode)     */
+  int nl_n, nl_pad;     /* nonlocal channels l = 0..nl_n-1 (0: none), at most 3    */
+  double nl_rc;         /* their cutoff radius                                    */
+  double nl_a[3];       /* v_l(r) = nl_a[l] exp(-(r / nl_s[l])^2), r < nl_rc       */
+  double nl_s[3];
 } or_system;
 
 static const double OR_TWO_PI = 6.283185307179586476925286766559;
@@ -433,6 +437,91 @@ int or_logpsi(const or_system* s, const double* R, double* logabs, int* sign) {
   return 0;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Nonlocal pseudopotential, reading (the paper's NiO runs use pseudopotentials; its text */
+/* gives no form): every ion carries channels l = 0..nl_n-1, v_l(r) = a_l exp(-(r/s_l)^2) */
+/* for r < nl_rc, zero beyond (minimum image).  For electron i at d = r_i - R_I, r = |d|: */
+/*   V_iI = sum_l v_l(r) (2l+1) (1/12) sum_q P_l(d.u_q / r) Psi(r_i -> R_I + r u_q)/Psi(R) */
+/* with u_q the 12 vertices of an icosahedron in a fixed orientation (a spherical design  */
+/* that integrates polynomials of degree <= 5 exactly), P_0 = 1, P_1 = x,                 */
+/* P_2 = (3x^2 - 1)/2.  E_L gains sum_{i,I} V_iI (the locality approximation).            */
+/* ------------------------------------------------------------------------------------ */
+static void icosahedron(double u[12][3]) {
+  const double ph = 0.5 * (1.0 + sqrt(5.0)), nrm = 1.0 / sqrt(1.0 + ph * ph);
+  const double sg[4][2] = {{1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
+  for (int k = 0; k < 4; ++k) {  /* (0, +-1, +-phi) and its two cyclic shifts */
+    double a = sg[k][0] * nrm, b = sg[k][1] * ph * nrm;
+    u[k][0] = 0.0;    u[k][1] = a;        u[k][2] = b;
+    u[4 + k][0] = a;  u[4 + k][1] = b;    u[4 + k][2] = 0.0;
+    u[8 + k][0] = b;  u[8 + k][1] = 0.0;  u[8 + k][2] = a;
+  }
+}
+
+static double legendre(int l, double x) {
+  return l == 0 ? 1.0 : (l == 1 ? x : 1.5 * x * x - 0.5);
+}
+
+/* Psi(R with r_i -> rp) / Psi(R) from two full recomputes. */
+static double ratio_direct(const or_system* s, const double* R, int i, const double* rp) {
+  int N = n_el(s);
+  double* R2 = (double*)malloc(sizeof(double) * 3 * N);
+  memcpy(R2, R, sizeof(double) * 3 * N);
+  for (int k = 0; k < 3; ++k) R2[3 * i + k] = rp[k];
+  double la0, la1;
+  int s0, s1;
+  int bad = or_logpsi(s, R, &la0, &s0) || or_logpsi(s, R2, &la1, &s1);
+  free(R2);
+  return bad ? NAN : (double)(s0 * s1) * exp(la1 - la0);
+}
+
+/* The same ratio from electron i's column of A^-1 (one row of A replaced):
+ * phi(rp) . Ainv[:, l] times exp(-(U_i(rp) - U_i(r_i))). */
+static double ratio_column(const or_system* s, const double* R, int i, const double* rp,
+                           const double* Binv) {
+  int sp = spin_of(s, i), ns = spin_size(s, sp), l = i - spin_off(s, sp);
+  double* v = (double*)malloc(sizeof(double) * ns * 5);
+  or_spo_vgl(s, rp, ns, v, v + ns, v + 4 * ns);
+  double det = 0.0;
+  for (int j = 0; j < ns; ++j) det += v[j] * Binv[(size_t)j * ns + l];
+  free(v);
+  double U0, U1, gU[3], lU;
+  jastrow_one(s, R, i, R + 3 * i, &U0, gU, &lU);
+  jastrow_one(s, R, i, rp, &U1, gU, &lU);
+  return det * exp(-(U1 - U0));
+}
+
+/* sum_{i,I} V_iI; Binv[sp] = A_sp^-1 (row-major), or NULL for the direct ratios. */
+static double nlpp_energy(const or_system* s, const double* R, const double* const* Binv) {
+  if (s->nl_n <= 0 || s->n_ions == 0) return 0.0;
+  double u[12][3];
+  icosahedron(u);
+  int N = n_el(s);
+  double V = 0.0;
+  for (int i = 0; i < N; ++i)
+    for (int I = 0; I < s->n_ions; ++I) {
+      double d[3];
+      double r = min_image(R + 3 * i, s->ions + 3 * I, s->L, d);
+      if (!(r < s->nl_rc) || r == 0.0) continue;
+      double acc[3] = {0.0, 0.0, 0.0};
+      for (int q = 0; q < 12; ++q) {
+        double rp[3], c = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          rp[k] = R[3 * i + k] - d[k] + r * u[q][k];  /* the ion's image + r u_q */
+          c += d[k] * u[q][k];
+        }
+        c /= r;
+        double rho = Binv ? ratio_column(s, R, i, rp, Binv[spin_of(s, i)])
+                          : ratio_direct(s, R, i, rp);
+        for (int l = 0; l < s->nl_n; ++l) acc[l] += legendre(l, c) * rho;
+      }
+      for (int l = 0; l < s->nl_n; ++l) {
+        double x = r / s->nl_s[l];
+        V += s->nl_a[l] * exp(-x * x) * (double)(2 * l + 1) * acc[l] / 12.0;
+      }
+    }
+  return V;
+}
+
 /* grad_i log Psi and lap_i log Psi for every electron, and the local energy
  * E_L = -1/2 sum_i [lap_i log Psi + |grad_i log Psi|^2] + V  (Alg. 1 line 11), with
  * grad_i log D = sum_j dA[l][j] Ainv[j][l],  lap_i D / D = sum_j d2A[l][j] Ainv[j][l]. */
@@ -440,6 +529,7 @@ int or_local_energy(const or_system* s, const double* R, double* grad, double* l
                     double* eloc) {
   int N = n_el(s);
   double kin = 0.0;
+  double* Bk[2] = {NULL, NULL};
   for (int sp = 0; sp < 2; ++sp) {
     int ns = spin_size(s, sp), off = spin_off(s, sp);
     if (ns == 0) continue;
@@ -447,10 +537,11 @@ int or_local_energy(const or_system* s, const double* R, double* grad, double* l
     double* dA = (double*)malloc(sizeof(double) * ns * ns * 3);
     double* d2A = (double*)malloc(sizeof(double) * ns * ns);
     double* B = (double*)malloc(sizeof(double) * ns * ns);
+    Bk[sp] = B;
     build_rows(s, R, sp, A, dA, d2A);
     double la; int sg;
     if (or_inverse(A, ns, B, &la, &sg)) {
-      free(A); free(dA); free(d2A); free(B);
+      free(A); free(dA); free(d2A); free(Bk[0]); free(Bk[1]);
       return 1;
     }
     for (int l = 0; l < ns; ++l) {
@@ -474,11 +565,36 @@ int or_local_energy(const or_system* s, const double* R, double* grad, double* l
       if (lap) lap[i] = lp;
       kin += -0.5 * (lp + g2);
     }
-    free(A); free(dA); free(d2A); free(B);
+    free(A); free(dA); free(d2A);
   }
   (void)N;
-  if (eloc) *eloc = kin + or_potential(s, R);
+  if (eloc) *eloc = kin + or_potential(s, R) + nlpp_energy(s, R, (const double* const*)Bk);
+  free(Bk[0]); free(Bk[1]);
   return 0;
+}
+
+/* The nonlocal term by its plain definition: every ratio from two full recomputes of
+ * log|Psi| (direct = 1), or from the inverses of a full recompute (direct = 0).  NaN if
+ * a Slater matrix is singular. */
+double or_nlpp(const or_system* s, const double* R, int direct) {
+  if (direct) return nlpp_energy(s, R, NULL);
+  double* Bk[2] = {NULL, NULL};
+  double out = 0.0;
+  for (int sp = 0; sp < 2 && !isnan(out); ++sp) {
+    int ns = spin_size(s, sp);
+    if (ns == 0) continue;
+    double* A = (double*)malloc(sizeof(double) * ns * ns);
+    double* dA = (double*)malloc(sizeof(double) * ns * ns * 3);
+    double* d2A = (double*)malloc(sizeof(double) * ns * ns);
+    Bk[sp] = (double*)malloc(sizeof(double) * ns * ns);
+    build_rows(s, R, sp, A, dA, d2A);
+    double la; int sg;
+    if (or_inverse(A, ns, Bk[sp], &la, &sg)) out = NAN;
+    free(A); free(dA); free(d2A);
+  }
+  if (!isnan(out)) out = nlpp_energy(s, R, (const double* const*)Bk);
+  free(Bk[0]); free(Bk[1]);
+  return out;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -821,7 +937,7 @@ static double walker_local_energy(or_crowd* c, int w) {
       kin += -0.5 * ((lD - gD2) - lU + g2);
     }
   }
-  return kin + or_potential(s, R);
+  return kin + or_potential(s, R) + nlpp_energy(s, R, (const double* const*)wk->B);
 }
 
 /* ---- exported fine-grained calls ---------------------------------------------------- */

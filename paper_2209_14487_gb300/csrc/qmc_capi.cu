@@ -199,6 +199,13 @@ int move(qmc_crowd* c, int mode) {
   return launch_status(c, qmcgb::launch_move<double>(c->p, mode, tm, c->stream));
 }
 
+// Adds the nonlocal pseudopotential term to the E_L the last launch wrote to p.eloc_out.
+int add_nlpp(qmc_crowd* c) {
+  if (c->p.nl_n <= 0 || c->p.n_ions == 0 || !c->p.eloc_out) return QMC_OK;
+  if (is_mixed(c)) return launch_status(c, qmcgb::launch_nlpp<float>(c->p, c->p.eloc_out, c->stream));
+  return launch_status(c, qmcgb::launch_nlpp<double>(c->p, c->p.eloc_out, c->stream));
+}
+
 // The padded table [GP][GP][GP][n_pad] (x slowest) as a 4-D tensor, innermost first, with
 // a box of one full 4x4x4 stencil: one copy per move lands it in shared memory.
 bool encode_table_map(qmc_crowd* c) {
@@ -707,6 +714,8 @@ int qmc_local_energy_batch(qmc_crowd* c, double* eloc, int mem) {
   c->p.eloc_out = mem == QMC_MEM_DEVICE ? eloc : c->d_io;
   st = move(c, qmcgb::MODE_ELOC);
   if (st) return st;
+  st = add_nlpp(c);
+  if (st) return st;
   if (mem == QMC_MEM_HOST) {
     CK(cudaMemcpyAsync(eloc, c->d_io, sizeof(double) * c->p.W, cudaMemcpyDeviceToHost, c->stream));
     return read_status(c);
@@ -750,6 +759,8 @@ int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) 
         if (st) return st;
       }
     }
+    st = add_nlpp(c);
+    if (st) return st;
     c->gen += 1;
   }
   if (eloc && mem == QMC_MEM_HOST)
@@ -876,6 +887,23 @@ int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, 
 int qmc_get_walker_count(const qmc_crowd* c, int* count) {
   if (!c || !count) return QMC_ERR_INVALID_ARG;
   *count = c->p.W;
+  return QMC_OK;
+}
+
+int qmc_load_nlpp(qmc_crowd* c, int n_l, const double* amp, const double* width, double rc) {
+  if (!c || n_l < 0 || n_l > 3) return QMC_ERR_INVALID_ARG;
+  if (n_l > 0) {
+    if (!amp || !width || !(rc > 0.0) || rc > 0.5 * c->p.L) return QMC_ERR_INVALID_ARG;
+    for (int l = 0; l < n_l; ++l)
+      if (!(width[l] > 0.0) || !std::isfinite(amp[l])) return QMC_ERR_INVALID_ARG;
+  }
+  c->p.nl_n = n_l;
+  c->p.nl_rc = n_l > 0 ? rc : 0.0;
+  for (int l = 0; l < 3; ++l) {
+    c->p.nl_a[l] = l < n_l ? amp[l] : 0.0;
+    c->p.nl_sinv2[l] = l < n_l ? 1.0 / (width[l] * width[l]) : 0.0;
+  }
+  sync_params(c);
   return QMC_OK;
 }
 
@@ -1125,7 +1153,7 @@ int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out) {
     const qmc_crowd* c = crowds[i];
     const qmc_crowd* c0 = crowds[0];
     if (c->run.precision != c0->run.precision || c->run.update != c0->run.update ||
-        c->p.nt != c0->p.nt)
+        c->p.nt != c0->p.nt || c->p.nl_n > 0)
       return QMC_ERR_UNSUPPORTED;
   }
   qmc_batch* b = new qmc_batch();
@@ -1173,6 +1201,7 @@ int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* sta
   if (!b || n_gen < 0) return QMC_ERR_INVALID_ARG;
   const int nc = (int)b->crowds.size();
   for (qmc_crowd* c : b->crowds) {
+    if (c->p.nl_n > 0) return QMC_ERR_UNSUPPORTED;  // batches run without the nonlocal term
     const int st = ensure_ready(c);
     if (st) return st;
   }

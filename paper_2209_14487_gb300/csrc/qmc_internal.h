@@ -46,6 +46,9 @@ struct Params {
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
   int inc_jastrow;          // mixed Sherman-Morrison sweep: incremental Jastrow grad/lap
   int dmc;                  // fixed node: a move that changes the determinant's sign is rejected
+  int nl_n;                 // nonlocal pseudopotential channels l < nl_n in E_L (0: none)
+  double nl_rc;             // their cutoff; v_l(r) = nl_a[l] exp(-r^2 nl_sinv2[l])
+  double nl_a[3], nl_sinv2[3];
   int eloc_by_gen;          // E_L of generation g goes to eloc_out[(g - eloc_gen0) W + w]
   uint32_t eloc_gen0;
   int stencil_bytes;        // bytes of that copy
@@ -143,5 +146,8 @@ cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int 
 template <typename T>
 cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s);
 cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s);
+// adds the nonlocal pseudopotential term to eloc[0..W) (nothing when p.nl_n == 0)
+template <typename T>
+cudaError_t launch_nlpp(const Params& p, double* eloc, cudaStream_t s);
 
 }  // namespace qmcgb

@@ -1,0 +1,251 @@
+// Nonlocal pseudopotential term of the local energy (Alg. 1 line 11) in the locality
+// approximation, as a kernel of its own that adds to the E_L a sweep has written (the
+// move kernel's registers stay those of the move).
+//
+// Every ion carries channels l < p.nl_n with v_l(r) = a_l exp(-r^2 / s_l^2) for r < nl_rc.
+// Electron i at d = r_i - R_I (minimum image), r = |d| < nl_rc, adds
+//   sum_l v_l(r) (2l+1) (1/12) sum_q P_l(d.u_q / r) Psi(r_i -> R_I + r u_q) / Psi(R)
+// over the 12 vertices u_q of an icosahedron (a spherical design exact to degree 5),
+// P_0 = 1, P_1 = x, P_2 = (3x^2 - 1)/2.  Each ratio is a virtual move of electron i: the
+// orbitals' values at the point dotted with electron i's column of A^-1, times
+// exp(-(U_i(point) - U_i(r_i))).
+//
+// One CTA per walker; one warp per electron (electrons warp, warp + 8, ...), lanes over
+// orbitals for the determinant and over partners for the Jastrow sums; the warps' FP64
+// sums are combined in a fixed order, so E_L stays deterministic.  The mixed path works
+// in FP32 on 32-bit fixed-point positions like the move kernel; the FP64 path in double.
+#include <cmath>
+
+#include "qmc_device.cuh"
+#include "qmc_internal.h"
+
+namespace qmcgb {
+namespace {
+
+constexpr int NL_NT = 256;
+constexpr int NL_NW = NL_NT / 32;
+
+// Vertex q of the icosahedron: (0, +-1, +-phi) / sqrt(1 + phi^2) for q < 4 and its cyclic
+// shifts (+-1, +-phi, 0), (+-phi, 0, +-1) for q / 4 = 1, 2; bits 0 and 1 of q are the signs.
+template <typename T>
+__device__ __forceinline__ void ico_vertex(int q, T* u) {
+  const T nrm = T(0.52573111211913360603);  // 1 / sqrt(1 + phi^2)
+  const T phn = T(0.85065080835203993218);  // phi / sqrt(1 + phi^2)
+  const T v[3] = {T(0), (q & 1) ? -nrm : nrm, (q & 2) ? -phn : phn};
+  const int sft = q >> 2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) u[k] = v[(k + sft) % 3];
+}
+
+// A point: FP64 coordinates, or fixed point in the mixed path.
+template <typename T> struct Pt { double x[3]; };
+template <> struct Pt<float> { uint32_t q[3]; };
+
+template <typename T>
+struct NlCtx {
+  const Params& p;
+  const Pt<T>* R;    // electrons (shared memory)
+  const Pt<T>* ion;  // ions (shared memory)
+  const T* jc;       // radial coefficients (shared memory)
+  T unit, scale, L, invL, h2inv, h1inv, rc2, rc1;
+  int lane;
+};
+
+template <typename T>
+__device__ __forceinline__ void disp(const NlCtx<T>& c, const Pt<T>& a, const Pt<T>& b, T* d,
+                                     T& r) {
+  if constexpr (IsMixed<T>::value) {
+    disp_fx(a.q, b.q, c.unit, d);
+  } else {
+    disp_f64(a.x, b.x, c.p.L, c.p.invL, d);
+  }
+  r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+// sum over partners t != i (electrons, then ions) of u(|x - r_t|): the warp total.
+template <typename T>
+__device__ T jastrow_sum(const NlCtx<T>& c, int i, const Pt<T>& x) {
+  const Params& p = c.p;
+  const int N = p.N;
+  const int t0 = p.K2 > 0 ? 0 : N, t1 = p.K1 > 0 ? N + p.n_ions : N;
+  T acc = 0;
+  for (int t = t0 + c.lane; t < t1; t += 32) {
+    if (t == i) continue;
+    T d[3], r;
+    const T* coef;
+    int K;
+    T hinv, rc;
+    if (t < N) {
+      disp(c, x, c.R[t], d, r);
+      coef = c.jc + (((i < p.n_up) == (t < p.n_up)) ? 0 : p.K2 + 3);
+      K = p.K2;
+      hinv = c.h2inv;
+      rc = c.rc2;
+    } else {
+      disp(c, x, c.ion[t - N], d, r);
+      coef = c.jc + 2 * (p.K2 + 3);
+      K = p.K1;
+      hinv = c.h1inv;
+      rc = c.rc1;
+    }
+    T u, du, d2u;
+    radial(coef, K, hinv, rc, r, u, du, d2u);
+    acc += u;
+  }
+  return warp_sum(acc);
+}
+
+// Shared-memory layout (byte offsets, each 16-byte aligned): electrons, ions, radial
+// coefficients, the warps' FP64 partial sums.
+struct NlLay {
+  size_t R, ion, jc, red, total;
+};
+
+__host__ __device__ inline size_t nl_al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename T>
+__host__ __device__ inline NlLay nl_lay(const Params& p) {
+  NlLay L;
+  const size_t njc = 2 * (size_t)(p.K2 + 3) + p.K1 + 3;
+  L.R = 0;
+  L.ion = nl_al16(L.R + (size_t)p.N * sizeof(Pt<T>));
+  L.jc = nl_al16(L.ion + (size_t)p.n_ions * sizeof(Pt<T>));
+  L.red = nl_al16(L.jc + njc * sizeof(T));
+  L.total = L.red + NL_NW * sizeof(double);
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NL_NT) nlpp_kernel(const Params p, double* eloc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int w = blockIdx.x, N = p.N, NI = p.n_ions, n = p.n, n_pad = p.n_pad, GP = p.GP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const NlLay lay = nl_lay<T>(p);
+  Pt<T>* R = reinterpret_cast<Pt<T>*>(smem + lay.R);
+  Pt<T>* ion = reinterpret_cast<Pt<T>*>(smem + lay.ion);
+  T* jc = reinterpret_cast<T*>(smem + lay.jc);
+  double* red = reinterpret_cast<double*>(smem + lay.red);
+  const int njc = 2 * (p.K2 + 3) + p.K1 + 3;
+  const double* Rg = p.R + (size_t)w * N * 3;
+  for (int e = threadIdx.x; e < (N + NI) * 3; e += NL_NT) {
+    const double x = e < N * 3 ? Rg[e] : p.ions[e - N * 3];
+    Pt<T>* dst = e < N * 3 ? R : ion;
+    const int k = e < N * 3 ? e : e - N * 3;
+    if constexpr (IsMixed<T>::value) dst[k / 3].q[k % 3] = to_fixed(x, p.fx_scale);
+    else dst[k / 3].x[k % 3] = x;
+  }
+  for (int e = threadIdx.x; e < njc; e += NL_NT) jc[e] = ((const T*)p.jc)[e];
+  __syncthreads();
+  NlCtx<T> c{p, R, ion, jc, (T)p.fx_unit, (T)p.fx_scale, (T)p.L, (T)p.invL,
+             (T)p.h2inv, (T)p.h1inv, (T)p.rc2, (T)p.rc1, lane};
+  const T* table = (const T*)p.table;
+  const T* Bw = (const T*)p.binv + (size_t)w * 2 * n * n;
+  double vsum = 0.0;  // lane 0 of each warp
+  for (int i = warp; i < N; i += NL_NW) {
+    const int s = i < p.n_up ? 0 : 1;
+    const T* bcol = Bw + ((size_t)s * n + (i - s * p.n_up)) * n;  // column of A^-1
+    bool have_u0 = false;
+    T u0 = 0;
+    for (int I = 0; I < NI; ++I) {
+      T d[3], r;
+      disp(c, R[i], ion[I], d, r);  // r_i - R_I
+      if (!(r < (T)p.nl_rc) || !(r > T(0))) continue;  // the same on every lane
+      if (!have_u0) {
+        u0 = jastrow_sum(c, i, R[i]);
+        have_u0 = true;
+      }
+      const T rinv = T(1) / r;
+      T acc0 = 0, acc1 = 0, acc2 = 0;
+      for (int q = 0; q < 12; ++q) {
+        T u[3];
+        ico_vertex(q, u);
+        Pt<T> xq;
+        int cell[3];
+        T wt[3][4];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          T t;
+          if constexpr (IsMixed<T>::value) {  // R_I + r u_q in fixed point (wraps by itself)
+            xq.q[k] = ion[I].q[k] + (uint32_t)__float2int_rn(r * u[k] * c.scale);
+            const unsigned long long prod =
+                (unsigned long long)xq.q[k] * (unsigned long long)p.G;
+            cell[k] = (int)(prod >> 32);
+            t = (float)(uint32_t)prod * 0x1p-32f;
+          } else {
+            double x = ion[I].x[k] + r * u[k];
+            x -= p.L * floor(x * p.invL);
+            xq.x[k] = x;
+            const double sg = x * p.dgrid;
+            int g = (int)floor(sg);
+            g = g > p.G - 1 ? p.G - 1 : (g < 0 ? 0 : g);
+            cell[k] = g;
+            t = sg - (double)g;
+          }
+          const T t2 = t * t, t3 = t2 * t, sm = T(1) - t, sixth = T(1) / T(6);
+          wt[k][0] = sm * sm * sm * sixth;
+          wt[k][1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+          wt[k][2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
+          wt[k][3] = t3 * sixth;
+        }
+        // the orbitals' values at the point, dotted with the inverse's column
+        T det = 0;
+        for (int j = lane; j < n; j += 32) {
+          T v = 0;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const T* row = table + (((size_t)(cell[0] + a) * GP + cell[1] + b) * GP +
+                                      cell[2]) * (size_t)n_pad + j;
+              const T wab = wt[0][a] * wt[1][b];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) v += wab * wt[2][e] * __ldg(row + (size_t)e * n_pad);
+            }
+          det += v * bcol[j];
+        }
+        det = warp_sum(det);
+        const T u1 = jastrow_sum(c, i, xq);
+        T rho;
+        if constexpr (IsMixed<T>::value) rho = det * __expf(u0 - u1);
+        else rho = det * exp(u0 - u1);
+        const T cth = (d[0] * u[0] + d[1] * u[1] + d[2] * u[2]) * rinv;
+        acc0 += rho;
+        acc1 += cth * rho;
+        acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
+      }
+      if (lane == 0) {
+        const double acc[3] = {(double)acc0, (double)acc1, (double)acc2};
+        const double r2 = (double)r * (double)r;
+        for (int l = 0; l < p.nl_n; ++l)
+          vsum += p.nl_a[l] * exp(-r2 * p.nl_sinv2[l]) * (double)(2 * l + 1) * acc[l] / 12.0;
+      }
+    }
+  }
+  double v1[1] = {vsum};
+  block_sum_to0<NL_NW, 1>(v1, red);
+  if (threadIdx.x == 0) {
+    const double e = eloc[w] + v1[0];
+    eloc[w] = e;
+    if (!isfinite(e)) atomicOr(p.status, ST_NAN);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_nlpp(const Params& p, double* eloc, cudaStream_t s) {
+  if (p.nl_n <= 0 || p.n_ions == 0 || p.W == 0) return cudaSuccess;
+  const size_t bytes = nl_lay<T>(p).total;
+  if (bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        nlpp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  nlpp_kernel<T><<<p.W, NL_NT, bytes, s>>>(p, eloc);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_nlpp<float>(const Params&, double*, cudaStream_t);
+template cudaError_t launch_nlpp<double>(const Params&, double*, cudaStream_t);
+
+}  // namespace qmcgb

@@ -38,7 +38,7 @@ EXPORTS = [
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
     "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
     "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count", "qmc_dmc_select",
-    "qmc_dmc_append",
+    "qmc_dmc_append", "qmc_load_nlpp",
 ]
 
 
@@ -108,6 +108,7 @@ def _load():
         "qmc_get_walker_count": [vp, C.POINTER(C.c_int)],
         "qmc_dmc_select": [vp, vp, i, i],
         "qmc_dmc_append": [vp, vp, i, i],
+        "qmc_load_nlpp": [vp, i, vp, vp, C.c_double],
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -334,6 +335,15 @@ class Crowd:
                                                     C.byref(st)))
         self.W = st.n_after
         return st, en[:st.n_after].copy()
+
+    def qmc_load_nlpp(self, amps, widths, rc):
+        """Nonlocal channels l = 0..len(amps)-1 in every E_L from now on (empty: none)."""
+        a = np.ascontiguousarray(amps, dtype=np.float64)
+        w = np.ascontiguousarray(widths, dtype=np.float64)
+        if a.shape != w.shape:
+            raise ValueError("one width per amplitude")
+        _check("qmc_load_nlpp", lib.qmc_load_nlpp(self.h, int(a.size), a.ctypes.data,
+                                                  w.ctypes.data, float(rc)))
 
     def qmc_dmc_select(self, src):
         """The new population is walkers src (indices into the current one, in order)."""

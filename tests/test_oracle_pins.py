@@ -566,3 +566,68 @@ def test_dmc_fixed_node_rejects_a_sign_change(oracle_lib):
     assert plain.accept(iel)[0] == 1
     fixed.propose(iel, rnew)
     assert fixed.accept(iel)[0] == 0
+
+
+# ------------------------------------------------------------------ nonlocal pseudopotential
+def test_nlpp_column_ratios_equal_full_recomputes(oracle_lib):
+    """The nonlocal term from the inverse's columns (the fast form both the crowd and the
+    CUDA path use) equals the one whose every ratio comes from two full recomputes of
+    log|Psi| (Jastrow J1 + J2, both spins, three channels)."""
+    wl = wl_mod.tiny(n_el=8, n_walkers=2, n_ions=3, L=4.0)
+    osys = oracle_lib.OracleSystem(wl, nlpp=((0.8, -0.5, 0.3), (0.9, 1.1, 0.7), 1.6))
+    R = wl.positions()
+    n_pairs = 0
+    for w in range(R.shape[0]):
+        fast, slow = osys.nlpp(R[w]), osys.nlpp(R[w], direct=True)
+        assert fast != 0.0
+        assert abs(fast - slow) < 1e-10 * max(1.0, abs(slow))
+        for i in range(wl.n_el):
+            d = R[w, i] - wl.ions
+            d -= wl.L * np.round(d / wl.L)
+            n_pairs += int((np.linalg.norm(d, axis=1) < 1.6).sum())
+    assert n_pairs >= 4
+    # and the local energy carries it
+    e_with = osys.local_energy(R[0])[0]
+    e_without = oracle_lib.OracleSystem(wl).local_energy(R[0])[0]
+    assert abs((e_with - e_without) - osys.nlpp(R[0])) < 1e-10 * max(1.0, abs(e_with))
+
+
+def _one_wave_nlpp(oracle_lib, l, r):
+    """One electron in a single real plane wave cos(k.x), one ion at distance r: the
+    channel-l term against the exact sphere average (2l+1) Re(i^l e^{ik.c}) j_l(kr)
+    P_l(d.k / (r k)) / cos(k.r_e), c the ion."""
+    from scipy.special import eval_legendre, spherical_jn
+    L = 6.0
+    m = np.array([[1, 1, 0]], dtype=np.int32)
+    kind = np.array([1], dtype=np.int32)
+    k = 2 * np.pi / L * m[0].astype(float)
+    wl = wl_mod.make_workload("one", n_el=2, n_orb=1, grid=8, n_walkers=1, n_gen=1, L=L,
+                              j2_knots=0, admix=0.0, potential=False)
+    ion = np.array([[2.1, 2.7, 3.0]])
+    wl.ions = ion
+    dirn = np.array([0.48, -0.6, 0.64])
+    dirn /= np.linalg.norm(dirn)
+    amps = [0.0, 0.0, 0.0]
+    amps[l] = 1.0
+    osys = oracle_lib.OracleSystem(wl, analytic_waves=(m, kind), n_up=1, n_dn=0, n_orb=1,
+                                   nlpp=(amps[:l + 1], (1e6,) * (l + 1), 2.0))
+    re = ion[0] + r * dirn
+    got = osys.nlpp(re[None, :])
+    kr = np.linalg.norm(k) * r
+    phase = np.exp(1j * (k @ ion[0])) * (1j ** l)
+    exact = ((2 * l + 1) * phase.real * spherical_jn(l, kr)
+             * eval_legendre(l, dirn @ k / np.linalg.norm(k)) / np.cos(k @ re))
+    return got, exact
+
+
+@pytest.mark.parametrize("l,order", [(0, 6), (1, 5), (2, 4)])
+def test_nlpp_channels_against_the_sphere_average(oracle_lib, l, order):
+    """The 12-point rule is exact to degree 5: channel l misses the exact average by
+    O((kr)^(6-l)), so halving r shrinks the error by about 2^(6-l); a wrong point set,
+    weight, (2l+1), Legendre polynomial or sign of d would leave an O(1) error."""
+    g1, x1 = _one_wave_nlpp(oracle_lib, l, 0.6)
+    g2, x2 = _one_wave_nlpp(oracle_lib, l, 0.3)
+    e1, e2 = abs(g1 - x1), abs(g2 - x2)
+    assert abs(x1) > 1e-2 and abs(x2) > 1e-3
+    assert e1 < 1e-2 * abs(x1)
+    assert 0.5 * 2 ** order < e1 / e2 < 2.0 * 2 ** order, (e1, e2)
