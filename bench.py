@@ -178,25 +178,33 @@ def barrier(ws: int):
 
 # synthetic nonlocal channels for --nlpp: amplitudes, widths (l = 0, 1, 2) and the cutoff
 NLPP = ((1.2, -0.8, 0.5), (0.7, 0.9, 0.8), 1.5)
+# Ewald Coulomb for --coulomb: alpha L and mmax; the ion charge makes the cell neutral
 
 
-def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0, nlpp=None):
+def coulomb_args(wl):
+    return (wl.n_el / max(1, wl.n_ions), 8.0 / wl.L, 10)
+
+
+def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0, nlpp=None, coulomb=None):
     from paper_2209_14487_gb300 import qmcgb
     c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
                                   stream=stream, cta_threads=nt)
     if nlpp is not None:
         c.qmc_load_nlpp(*nlpp)
+    if coulomb is not None:
+        c.qmc_load_coulomb(*coulomb)
     c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=crowd_id)))
     c.qmc_recompute()
     return c
 
 
-def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0, nlpp=None):
+def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0, nlpp=None,
+              coulomb=None):
     """Per-step CUDA-event timing of qmc_sweep(1) on torch's current stream."""
     import torch
     stream = torch.cuda.Stream()  # a real stream: torch's default is the legacy NULL stream
     torch.cuda.set_stream(stream)
-    c = make_crowd(wl, precision, update, k, stream.cuda_stream, crowd_id, nt, nlpp)
+    c = make_crowd(wl, precision, update, k, stream.cuda_stream, crowd_id, nt, nlpp, coulomb)
     eloc = torch.zeros((warmup + steps, wl.n_walkers), dtype=torch.float64, device="cuda")
     for g in range(warmup):
         c.qmc_sweep(1, eloc[g], stats=False)
@@ -553,6 +561,8 @@ def main():
                     help="walkers of the CPU oracle sample (default: all)")
     ap.add_argument("--nlpp", action="store_true",
                     help="also time the mixed path with the synthetic nonlocal term in E_L")
+    ap.add_argument("--coulomb", action="store_true",
+                    help="also time the mixed path with the Ewald Coulomb energy in E_L")
     ap.add_argument("--walker-scan", default=None,
                     help="comma-separated walkers per GPU: throughput against crowd size")
     ap.add_argument("--crowds", default=None,
@@ -698,18 +708,23 @@ def main():
                        "bytes_per_move": bpm, "acceptance": mixed["p_acc"],
                        "peak_source": src}
     out["gpu_launches"] = mixed["launches"]
+    extras = []
     if args.nlpp:
-        with ClockSampler(uuid) as clk_nl:
-            nl = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush,
-                           args.cta_threads, nlpp=NLPP)
-        v_nl = aggregate_value(moves_step * args.steps, sum(nl["ms"]) / 1000.0, ws)
-        e_nl, s_nl = energy_stats(nl["eloc"])
-        out["nlpp"] = {"value": v_nl, "unit": UNIT,
-                       "ms_per_step": 1000.0 * ws * moves_step / v_nl,
-                       "channels": {"amplitudes": NLPP[0], "widths": NLPP[1], "rc": NLPP[2]},
-                       "energy": {"mean": e_nl, "sigma": s_nl},
-                       "launches_per_step": nl["launches"] / args.steps,
-                       "clocks": clk_nl.summary()}
+        extras.append(("nlpp", dict(nlpp=NLPP),
+                       {"amplitudes": NLPP[0], "widths": NLPP[1], "rc": NLPP[2]}))
+    if args.coulomb:
+        ca = coulomb_args(wl)
+        extras.append(("coulomb", dict(coulomb=ca), {"Z": ca[0], "alpha": ca[1], "mmax": ca[2]}))
+    for name, kw, desc in extras:
+        with ClockSampler(uuid) as clk_x:
+            xr = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush,
+                           args.cta_threads, **kw)
+        v_x = aggregate_value(moves_step * args.steps, sum(xr["ms"]) / 1000.0, ws)
+        e_x, s_x = energy_stats(xr["eloc"])
+        out[name] = {"value": v_x, "unit": UNIT, "ms_per_step": 1000.0 * ws * moves_step / v_x,
+                     "parameters": desc, "energy": {"mean": e_x, "sigma": s_x},
+                     "launches_per_step": xr["launches"] / args.steps,
+                     "clocks": clk_x.summary()}
     out["clocks"] = clk.summary()
     if not args.no_e2e:
         rate, h2d, d2h = e2e_run(wl, "mixed", update, k, args.steps, rank, args.cta_threads)

@@ -261,6 +261,22 @@ int qmc_get_walker_count(const qmc_crowd* crowd, int* count);
 int qmc_load_nlpp(qmc_crowd* crowd, int n_l, const double* amp, const double* width, double rc);
 
 /* ---------------------------------------------------------------------------------------
+ * Coulomb energy in E_L by Ewald summation (the paper's runs use it; its text gives no
+ * form): charges -1 (electrons) and +Z (every ion) in the periodic cube, V = L^3,
+ *   E = sum_{a<b} q_a q_b erfc(alpha r_ab) / r_ab   (minimum image of each pair)
+ *     + (2 pi / V) sum_{k != 0} exp(-k^2 / (4 alpha^2)) / k^2 |S(k)|^2
+ *     - (alpha / sqrt(pi)) sum_a q_a^2 - pi Q^2 / (2 V alpha^2),
+ * S(k) = sum_a q_a exp(i k.r_a), k = 2 pi m / L over integer m, 0 < |m|^2 <= mmax^2,
+ * Q = sum_a q_a (the last term is the neutralising background's).  The ion-ion part is
+ * included.  It adds to the model potential of run.potential.  The minimum-image
+ * real-space sum is exact when erfc(alpha L / 2) is negligible (alpha L >~ 10).
+ * on: 1 to add the term (Z >= 0, alpha > 0, mmax >= 1), 0 to remove it.  Batches of crowds
+ * do not serve it.  Errors: INVALID_ARG; UNSUPPORTED (more than 4096 half-space vectors:
+ * mmax above about 12); OOM.
+ * --------------------------------------------------------------------------------------- */
+int qmc_load_coulomb(qmc_crowd* crowd, int on, double Z, double alpha, int mmax);
+
+/* ---------------------------------------------------------------------------------------
  * Population edits for walker exchange between crowds (one crowd per GPU; Sec. III's
  * walkers are independent, so any walker may move to any crowd of the same system).
  *

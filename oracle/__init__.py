@@ -41,6 +41,8 @@ class System(C.Structure):
         ("pw_kind", C.c_void_p),
         ("nl_n", C.c_int), ("nl_pad", C.c_int), ("nl_rc", C.c_double),
         ("nl_a", C.c_double * 3), ("nl_s", C.c_double * 3),
+        ("coul", C.c_int), ("coul_mmax", C.c_int), ("coul_alpha", C.c_double),
+        ("coul_Z", C.c_double),
     ]
 
 
@@ -85,6 +87,8 @@ def lib():
         L.or_crowd_get_generation.restype = C.c_uint32
         L.or_crowd_set_generation.argtypes = [C.c_void_p, C.c_uint32]
         L.or_num_threads.restype = C.c_int
+        L.or_coulomb.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+        L.or_coulomb.restype = C.c_double
         L.or_nlpp.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
         L.or_nlpp.restype = C.c_double
         L.or_set_num_threads.argtypes = [C.c_int]
@@ -180,6 +184,11 @@ class OracleSystem:
     def potential(self, R):
         R = np.ascontiguousarray(R, dtype=np.float64)
         return lib().or_potential(self.ref, _p(R))
+
+    def coulomb(self, R, images: bool = False) -> float:
+        """The Ewald Coulomb energy at R (minimum-image or 27-cell real-space sum)."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        return lib().or_coulomb(self.ref, _p(R), int(images))
 
     def nlpp(self, R, direct: bool = False) -> float:
         """The nonlocal term of E_L at R: ratios from full recomputes of log|Psi|

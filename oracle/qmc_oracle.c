@@ -56,6 +56,10 @@ typedef struct or_system {
   double nl_rc;         /* their cutoff radius                                    */
   double nl_a[3];       /* v_l(r) = nl_a[l] exp(-(r / nl_s[l])^2), r < nl_rc       */
   double nl_s[3];
+  int coul;             /* 1: add the Ewald Coulomb energy (electrons -1, ions +Z) */
+  int coul_mmax;        /* reciprocal vectors k = 2 pi m / L with |m|^2 <= mmax^2  */
+  double coul_alpha;    /* Ewald splitting parameter                              */
+  double coul_Z;        /* ion charge                                             */
 } or_system;
 
 static const double OR_TWO_PI = 6.283185307179586476925286766559;
@@ -309,8 +313,11 @@ double or_jastrow_U(const or_system* s, const double* R) {
 
 /* Model potential, reading (the paper gives no Hamiltonian): smooth Gaussians,
  * v_ee = exp(-r^2), v_eI = -2 exp(-r^2/2), minimum image, zero for r >= L/2. */
+double or_coulomb(const or_system* s, const double* R, int images);
+
 double or_potential(const or_system* s, const double* R) {
-  if (!s->potential) return 0.0;
+  double Vc = s->coul ? or_coulomb(s, R, 0) : 0.0;
+  if (!s->potential) return Vc;
   int N = n_el(s);
   double V = 0.0, d[3], half = 0.5 * s->L;
   for (int i = 0; i < N; ++i)
@@ -323,7 +330,78 @@ double or_potential(const or_system* s, const double* R) {
       double rr = min_image(R + 3 * i, s->ions + 3 * I, s->L, d);
       if (rr < half) V += -2.0 * exp(-0.5 * rr * rr);
     }
-  return V;
+  return V + Vc;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Coulomb energy by Ewald summation, reading (the paper's runs use it; its text gives no */
+/* form): charges -1 (electrons) and +Z (ions) in the periodic cube, V = L^3,             */
+/*   E = sum_{a<b} q_a q_b erfc(alpha r_ab) / r_ab                      (real space)      */
+/*     + (2 pi / V) sum_{k != 0} exp(-k^2 / (4 alpha^2)) / k^2 |S(k)|^2 (reciprocal)      */
+/*     - (alpha / sqrt(pi)) sum_a q_a^2 - pi Q^2 / (2 V alpha^2)        (self, background)*/
+/* S(k) = sum_a q_a exp(i k.r_a), k = 2 pi m / L over integer m with 0 < |m|^2 <= mmax^2,  */
+/* Q = sum_a q_a.  The real-space sum takes the minimum image of each pair (images = 0)   */
+/* or every pair and self-image within the 27 nearest cells (images = 1).                */
+/* ------------------------------------------------------------------------------------ */
+double or_coulomb(const or_system* s, const double* R, int images) {
+  const int N = n_el(s), NI = s->n_ions, M = N + NI;
+  const double L = s->L, V = L * L * L, a = s->coul_alpha, Z = s->coul_Z;
+  double* x = (double*)malloc(sizeof(double) * 3 * (M > 0 ? M : 1));
+  double* q = (double*)malloc(sizeof(double) * (M > 0 ? M : 1));
+  for (int i = 0; i < N; ++i) {
+    for (int k = 0; k < 3; ++k) x[3 * i + k] = R[3 * i + k];
+    q[i] = -1.0;
+  }
+  for (int I = 0; I < NI; ++I) {
+    for (int k = 0; k < 3; ++k) x[3 * (N + I) + k] = s->ions[3 * I + k];
+    q[N + I] = Z;
+  }
+  double Ereal = 0.0, Erec = 0.0, Q = 0.0, Q2 = 0.0;
+  for (int i = 0; i < M; ++i) {
+    Q += q[i];
+    Q2 += q[i] * q[i];
+  }
+  for (int i = 0; i < M; ++i)
+    for (int j = i; j < M; ++j) {
+      double d[3];
+      if (!images) {
+        if (j == i) continue;
+        double r = min_image(x + 3 * i, x + 3 * j, L, d);
+        Ereal += q[i] * q[j] * erfc(a * r) / r;
+        continue;
+      }
+      for (int k = 0; k < 3; ++k) d[k] = x[3 * i + k] - x[3 * j + k];
+      for (int n0 = -1; n0 <= 1; ++n0)
+        for (int n1 = -1; n1 <= 1; ++n1)
+          for (int n2 = -1; n2 <= 1; ++n2) {
+            if (i == j && n0 == 0 && n1 == 0 && n2 == 0) continue;
+            double e0 = d[0] + n0 * L, e1 = d[1] + n1 * L, e2 = d[2] + n2 * L;
+            double r = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+            /* a pair's images once each; a self-image pair (n, -n) twice, so halve it */
+            Ereal += (i == j ? 0.5 : 1.0) * q[i] * q[j] * erfc(a * r) / r;
+          }
+    }
+  const int mm = s->coul_mmax;
+  for (int m0 = -mm; m0 <= mm; ++m0)
+    for (int m1 = -mm; m1 <= mm; ++m1)
+      for (int m2 = -mm; m2 <= mm; ++m2) {
+        int m2s = m0 * m0 + m1 * m1 + m2 * m2;
+        if (m2s == 0 || m2s > mm * mm) continue;
+        double k[3] = {OR_TWO_PI * m0 / L, OR_TWO_PI * m1 / L, OR_TWO_PI * m2 / L};
+        double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        double re = 0.0, im = 0.0;
+        for (int i = 0; i < M; ++i) {
+          double ph = k[0] * x[3 * i] + k[1] * x[3 * i + 1] + k[2] * x[3 * i + 2];
+          re += q[i] * cos(ph);
+          im += q[i] * sin(ph);
+        }
+        Erec += exp(-k2 / (4.0 * a * a)) / k2 * (re * re + im * im);
+      }
+  Erec *= OR_TWO_PI / V;
+  free(x);
+  free(q);
+  const double sqrt_pi = 1.7724538509055160273;
+  return Ereal + Erec - a / sqrt_pi * Q2 - 0.5 * OR_TWO_PI * Q * Q / (2.0 * V * a * a);
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -83,6 +83,9 @@ struct qmc_crowd {
   void* d_rows2 = nullptr;
   void* d_binv2 = nullptr;
   void* d_jgl2 = nullptr;
+  double* d_nlpart = nullptr;   // [capacity][splits] partial sums of the nonlocal term
+  int* d_coul_m = nullptr;      // Ewald reciprocal vectors and their coefficients
+  double* d_coul_c = nullptr;
   double* d_logdet2 = nullptr;
   int* d_sign2 = nullptr;
   int* d_jvalid2 = nullptr;
@@ -145,7 +148,8 @@ void free_all(qmc_crowd* c) {
                   c->d_pend_phi, c->d_pend, c->d_ws, c->d_eloc, c->d_nacc, c->d_status,
                   c->d_io, c->d_io8, c->d_jgl, c->d_jvalid, c->d_flush, c->d_R2,
                   c->d_rows2, c->d_binv2, c->d_jgl2, c->d_logdet2, c->d_sign2, c->d_jvalid2,
-                  c->d_mult, c->d_src, c->d_bout, c->d_bsums, c->d_e};
+                  c->d_mult, c->d_src, c->d_bout, c->d_bsums, c->d_e, c->d_coul_m,
+                  c->d_coul_c, c->d_nlpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -199,11 +203,23 @@ int move(qmc_crowd* c, int mode) {
   return launch_status(c, qmcgb::launch_move<double>(c->p, mode, tm, c->stream));
 }
 
-// Adds the nonlocal pseudopotential term to the E_L the last launch wrote to p.eloc_out.
+// Adds the nonlocal pseudopotential and Ewald Coulomb terms to the E_L the last launch
+// wrote to p.eloc_out.
 int add_nlpp(qmc_crowd* c) {
-  if (c->p.nl_n <= 0 || c->p.n_ions == 0 || !c->p.eloc_out) return QMC_OK;
-  if (is_mixed(c)) return launch_status(c, qmcgb::launch_nlpp<float>(c->p, c->p.eloc_out, c->stream));
-  return launch_status(c, qmcgb::launch_nlpp<double>(c->p, c->p.eloc_out, c->stream));
+  if (!c->p.eloc_out) return QMC_OK;
+  int st = QMC_OK;
+  if (c->p.nl_n > 0 && c->p.n_ions > 0) {
+    if (is_mixed(c))
+      st = launch_status(c, qmcgb::launch_nlpp<float>(c->p, c->p.eloc_out, c->d_nlpart, c->stream));
+    else
+      st = launch_status(c, qmcgb::launch_nlpp<double>(c->p, c->p.eloc_out, c->d_nlpart, c->stream));
+    if (st) return st;
+  }
+  if (c->p.coul) {
+    if (is_mixed(c)) st = launch_status(c, qmcgb::launch_ewald<float>(c->p, c->p.eloc_out, c->stream));
+    else st = launch_status(c, qmcgb::launch_ewald<double>(c->p, c->p.eloc_out, c->stream));
+  }
+  return st;
 }
 
 // The padded table [GP][GP][GP][n_pad] (x slowest) as a 4-D tensor, innermost first, with
@@ -897,12 +913,75 @@ int qmc_load_nlpp(qmc_crowd* c, int n_l, const double* amp, const double* width,
     for (int l = 0; l < n_l; ++l)
       if (!(width[l] > 0.0) || !std::isfinite(amp[l])) return QMC_ERR_INVALID_ARG;
   }
+  if (n_l > 0 && !c->d_nlpart &&
+      dmalloc((void**)&c->d_nlpart, sizeof(double) * (size_t)c->run.n_walkers *
+                                        qmcgb::nlpp_partials_per_walker()))
+    return QMC_ERR_OOM;
   c->p.nl_n = n_l;
   c->p.nl_rc = n_l > 0 ? rc : 0.0;
   for (int l = 0; l < 3; ++l) {
     c->p.nl_a[l] = l < n_l ? amp[l] : 0.0;
     c->p.nl_sinv2[l] = l < n_l ? 1.0 / (width[l] * width[l]) : 0.0;
   }
+  sync_params(c);
+  return QMC_OK;
+}
+
+int qmc_load_coulomb(qmc_crowd* c, int on, double Z, double alpha, int mmax) {
+  if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
+  if (on == 0) {
+    c->p.coul = 0;
+    sync_params(c);
+    return QMC_OK;
+  }
+  if (!(Z >= 0.0) || !std::isfinite(Z) || !(alpha > 0.0) || !std::isfinite(alpha) || mmax < 1)
+    return QMC_ERR_INVALID_ARG;
+  // the half space of 0 < |m|^2 <= mmax^2: m0 > 0, or m0 = 0 < m1, or m0 = m1 = 0 < m2
+  const double L = c->p.L, V = L * L * L, two_pi = 6.283185307179586476925286766559;
+  std::vector<int> m;
+  std::vector<double> cf;
+  for (int m0 = 0; m0 <= mmax; ++m0)
+    for (int m1 = -mmax; m1 <= mmax; ++m1)
+      for (int m2 = -mmax; m2 <= mmax; ++m2) {
+        const int n2 = m0 * m0 + m1 * m1 + m2 * m2;
+        if (n2 == 0 || n2 > mmax * mmax) continue;
+        if (m0 == 0 && (m1 < 0 || (m1 == 0 && m2 < 0))) continue;
+        const double k2 = (two_pi / L) * (two_pi / L) * n2;
+        m.push_back(m0);
+        m.push_back(m1);
+        m.push_back(m2);
+        cf.push_back(2.0 * two_pi / V * std::exp(-k2 / (4.0 * alpha * alpha)) / k2);
+      }
+  const int nk = (int)cf.size();
+  if (nk > qmcgb::ewald_max_vectors()) return QMC_ERR_UNSUPPORTED;
+  int* dm = nullptr;
+  double* dc = nullptr;
+  if (dmalloc((void**)&dm, sizeof(int) * m.size()) || dmalloc((void**)&dc, sizeof(double) * nk)) {
+    if (dm) cudaFree(dm);
+    return QMC_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpy(dm, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dc, cf.data(), sizeof(double) * nk, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dm);
+    cudaFree(dc);
+    return cuda_fail(e);
+  }
+  CK(cudaStreamSynchronize(c->stream));  // no launch still reads the previous lists
+  if (c->d_coul_m) cudaFree(c->d_coul_m);
+  if (c->d_coul_c) cudaFree(c->d_coul_c);
+  c->d_coul_m = dm;
+  c->d_coul_c = dc;
+  const int N = c->p.N, NI = c->p.n_ions;
+  const double Q = NI * Z - N, Q2 = N + NI * Z * Z, sqrt_pi = 1.7724538509055160273;
+  c->p.coul = 1;
+  c->p.coul_mmax = mmax;
+  c->p.coul_nk = nk;
+  c->p.coul_alpha = alpha;
+  c->p.coul_Z = Z;
+  c->p.coul_const = -alpha / sqrt_pi * Q2 - 0.5 * two_pi * Q * Q / (2.0 * V * alpha * alpha);
+  c->p.coul_m = dm;
+  c->p.coul_c = dc;
   sync_params(c);
   return QMC_OK;
 }
@@ -1153,7 +1232,7 @@ int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out) {
     const qmc_crowd* c = crowds[i];
     const qmc_crowd* c0 = crowds[0];
     if (c->run.precision != c0->run.precision || c->run.update != c0->run.update ||
-        c->p.nt != c0->p.nt || c->p.nl_n > 0)
+        c->p.nt != c0->p.nt || c->p.nl_n > 0 || c->p.coul)
       return QMC_ERR_UNSUPPORTED;
   }
   qmc_batch* b = new qmc_batch();
@@ -1201,7 +1280,8 @@ int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* sta
   if (!b || n_gen < 0) return QMC_ERR_INVALID_ARG;
   const int nc = (int)b->crowds.size();
   for (qmc_crowd* c : b->crowds) {
-    if (c->p.nl_n > 0) return QMC_ERR_UNSUPPORTED;  // batches run without the nonlocal term
+    // batches run without the nonlocal and Coulomb terms
+    if (c->p.nl_n > 0 || c->p.coul) return QMC_ERR_UNSUPPORTED;
     const int st = ensure_ready(c);
     if (st) return st;
   }

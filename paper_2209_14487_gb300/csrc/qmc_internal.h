@@ -49,6 +49,11 @@ struct Params {
   int nl_n;                 // nonlocal pseudopotential channels l < nl_n in E_L (0: none)
   double nl_rc;             // their cutoff; v_l(r) = nl_a[l] exp(-r^2 nl_sinv2[l])
   double nl_a[3], nl_sinv2[3];
+  int coul;                 // Ewald Coulomb energy in E_L (electrons -1, ions +coul_Z)
+  int coul_mmax, coul_nk;   // |m| <= mmax; coul_nk half-space vectors in coul_m / coul_c
+  double coul_alpha, coul_Z, coul_const;  // splitting, ion charge, self + background terms
+  const int* coul_m;        // [coul_nk][3] integer vectors m (k = 2 pi m / L)
+  const double* coul_c;     // [coul_nk] (4 pi / V) exp(-k^2 / (4 alpha^2)) / k^2
   int eloc_by_gen;          // E_L of generation g goes to eloc_out[(g - eloc_gen0) W + w]
   uint32_t eloc_gen0;
   int stencil_bytes;        // bytes of that copy
@@ -146,8 +151,14 @@ cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int 
 template <typename T>
 cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s);
 cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s);
-// adds the nonlocal pseudopotential term to eloc[0..W) (nothing when p.nl_n == 0)
+// adds the nonlocal pseudopotential term to eloc[0..W) (nothing when p.nl_n == 0);
+// partial: scratch of W * nlpp_partials_per_walker() doubles
 template <typename T>
-cudaError_t launch_nlpp(const Params& p, double* eloc, cudaStream_t s);
+cudaError_t launch_nlpp(const Params& p, double* eloc, double* partial, cudaStream_t s);
+int nlpp_partials_per_walker();
+// adds the Ewald Coulomb energy to eloc[0..W) (nothing when p.coul == 0)
+template <typename T>
+cudaError_t launch_ewald(const Params& p, double* eloc, cudaStream_t s);
+int ewald_max_vectors();
 
 }  // namespace qmcgb

@@ -10,9 +10,11 @@
 // orbitals' values at the point dotted with electron i's column of A^-1, times
 // exp(-(U_i(point) - U_i(r_i))).
 //
-// One CTA per walker; one warp per electron (electrons warp, warp + 8, ...), lanes over
-// orbitals for the determinant and over partners for the Jastrow sums; the warps' FP64
-// sums are combined in a fixed order, so E_L stays deterministic.  The mixed path works
+// NL_SPLIT CTAs per walker (more CTAs than SMs, two resident per SM); one warp per
+// electron (the walker's 32 warps take electrons gw, gw + 32, ...), lanes over orbitals for
+// the determinant and over partners for the Jastrow sums.  Each CTA writes its FP64 sum
+// to a partial slot; a second kernel adds a walker's partials to E_L in a fixed order, so
+// E_L stays deterministic.  The mixed path works
 // in FP32 on 32-bit fixed-point positions like the move kernel; the FP64 path in double.
 #include <cmath>
 
@@ -24,6 +26,7 @@ namespace {
 
 constexpr int NL_NT = 256;
 constexpr int NL_NW = NL_NT / 32;
+constexpr int NL_SPLIT = 4;  // CTAs per walker
 
 // Vertex q of the icosahedron: (0, +-1, +-phi) / sqrt(1 + phi^2) for q < 4 and its cyclic
 // shifts (+-1, +-phi, 0), (+-phi, 0, +-1) for q / 4 = 1, 2; bits 0 and 1 of q are the signs.
@@ -116,10 +119,11 @@ __host__ __device__ inline NlLay nl_lay(const Params& p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NL_NT) nlpp_kernel(const Params p, double* eloc) {
+__global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* partial) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = blockIdx.x, N = p.N, NI = p.n_ions, n = p.n, n_pad = p.n_pad, GP = p.GP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.y * NL_NW + warp;  // this warp among the walker's
   const NlLay lay = nl_lay<T>(p);
   Pt<T>* R = reinterpret_cast<Pt<T>*>(smem + lay.R);
   Pt<T>* ion = reinterpret_cast<Pt<T>*>(smem + lay.ion);
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(NL_NT) nlpp_kernel(const Params p, double* elo
   const T* table = (const T*)p.table;
   const T* Bw = (const T*)p.binv + (size_t)w * 2 * n * n;
   double vsum = 0.0;  // lane 0 of each warp
-  for (int i = warp; i < N; i += NL_NW) {
+  for (int i = gw; i < N; i += NL_NW * NL_SPLIT) {
     const int s = i < p.n_up ? 0 : 1;
     const T* bcol = Bw + ((size_t)s * n + (i - s * p.n_up)) * n;  // column of A^-1
     bool have_u0 = false;
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(NL_NT) nlpp_kernel(const Params p, double* elo
         T det = 0;
         for (int j = lane; j < n; j += 32) {
           T v = 0;
-#pragma unroll
+#pragma unroll 1
           for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
@@ -223,17 +227,26 @@ __global__ void __launch_bounds__(NL_NT) nlpp_kernel(const Params p, double* elo
   }
   double v1[1] = {vsum};
   block_sum_to0<NL_NW, 1>(v1, red);
-  if (threadIdx.x == 0) {
-    const double e = eloc[w] + v1[0];
-    eloc[w] = e;
-    if (!isfinite(e)) atomicOr(p.status, ST_NAN);
-  }
+  if (threadIdx.x == 0) partial[(size_t)w * NL_SPLIT + blockIdx.y] = v1[0];
+}
+
+// eloc[w] += the walker's partial sums, in order.
+__global__ void nlpp_add_kernel(const double* __restrict__ partial, double* eloc, int W,
+                                int* status) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  double e = eloc[w];
+  for (int q = 0; q < NL_SPLIT; ++q) e += partial[(size_t)w * NL_SPLIT + q];
+  eloc[w] = e;
+  if (!isfinite(e)) atomicOr(status, ST_NAN);
 }
 
 }  // namespace
 
+int nlpp_partials_per_walker() { return NL_SPLIT; }
+
 template <typename T>
-cudaError_t launch_nlpp(const Params& p, double* eloc, cudaStream_t s) {
+cudaError_t launch_nlpp(const Params& p, double* eloc, double* partial, cudaStream_t s) {
   if (p.nl_n <= 0 || p.n_ions == 0 || p.W == 0) return cudaSuccess;
   const size_t bytes = nl_lay<T>(p).total;
   if (bytes > 48 * 1024) {
@@ -241,11 +254,12 @@ cudaError_t launch_nlpp(const Params& p, double* eloc, cudaStream_t s) {
         nlpp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
-  nlpp_kernel<T><<<p.W, NL_NT, bytes, s>>>(p, eloc);
+  nlpp_kernel<T><<<dim3(p.W, NL_SPLIT), NL_NT, bytes, s>>>(p, partial);
+  nlpp_add_kernel<<<(p.W + 255) / 256, 256, 0, s>>>(partial, eloc, p.W, p.status);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_nlpp<float>(const Params&, double*, cudaStream_t);
-template cudaError_t launch_nlpp<double>(const Params&, double*, cudaStream_t);
+template cudaError_t launch_nlpp<float>(const Params&, double*, double*, cudaStream_t);
+template cudaError_t launch_nlpp<double>(const Params&, double*, double*, cudaStream_t);
 
 }  // namespace qmcgb

@@ -38,7 +38,7 @@ EXPORTS = [
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
     "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
     "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count", "qmc_dmc_select",
-    "qmc_dmc_append", "qmc_load_nlpp",
+    "qmc_dmc_append", "qmc_load_nlpp", "qmc_load_coulomb",
 ]
 
 
@@ -109,6 +109,7 @@ def _load():
         "qmc_dmc_select": [vp, vp, i, i],
         "qmc_dmc_append": [vp, vp, i, i],
         "qmc_load_nlpp": [vp, i, vp, vp, C.c_double],
+        "qmc_load_coulomb": [vp, i, C.c_double, C.c_double, i],
         "qmc_crowd_save": [vp, vp, C.POINTER(C.c_size_t)],
         "qmc_crowd_restore": [vp, vp, C.c_size_t],
     }
@@ -344,6 +345,11 @@ class Crowd:
             raise ValueError("one width per amplitude")
         _check("qmc_load_nlpp", lib.qmc_load_nlpp(self.h, int(a.size), a.ctypes.data,
                                                   w.ctypes.data, float(rc)))
+
+    def qmc_load_coulomb(self, Z, alpha, mmax, on=True):
+        """Ewald Coulomb energy (electrons -1, ions +Z) in every E_L from now on."""
+        _check("qmc_load_coulomb", lib.qmc_load_coulomb(self.h, int(bool(on)), float(Z),
+                                                        float(alpha), int(mmax)))
 
     def qmc_dmc_select(self, src):
         """The new population is walkers src (indices into the current one, in order)."""

@@ -631,3 +631,55 @@ def test_nlpp_channels_against_the_sphere_average(oracle_lib, l, order):
     assert abs(x1) > 1e-2 and abs(x2) > 1e-3
     assert e1 < 1e-2 * abs(x1)
     assert 0.5 * 2 ** order < e1 / e2 < 2.0 * 2 ** order, (e1, e2)
+
+
+# ------------------------------------------------------------------ Ewald Coulomb energy
+MADELUNG_NACL = 1.747564594633182  # rock salt, per ion pair in units of 1/d (d: nearest)
+
+
+def _rock_salt(oracle_lib, L, alpha, mmax, shift=(0.0, 0.0, 0.0)):
+    """The conventional rock-salt cell: 4 cations (+1, as ions) and 4 anions (-1, as
+    electrons) at nearest-neighbour distance L/2."""
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    cat = np.mod((fcc + np.array(shift)) * L, L)
+    an = np.mod((fcc + 0.5 + np.array(shift)) * L, L)
+    osys = oracle_lib.OracleSystem(None, n_up=2, n_dn=2, n_orb=2, n_ions=4, L=L,
+                                   ions=np.ascontiguousarray(cat), coul=1, coul_Z=1.0,
+                                   coul_alpha=alpha, coul_mmax=mmax)
+    return osys, np.ascontiguousarray(an)
+
+
+def test_ewald_reproduces_the_rock_salt_madelung_constant(oracle_lib):
+    L = 5.2
+    for alpha, mmax in ((5.0 / L, 12), (7.0 / L, 16)):
+        osys, R = _rock_salt(oracle_lib, L, alpha, mmax, shift=(0.13, 0.02, 0.31))
+        E = osys.coulomb(R, images=True)
+        assert abs(E - (-8.0 * MADELUNG_NACL / L)) < 1e-9, (alpha, E)
+
+
+def test_ewald_is_independent_of_alpha_and_min_image_converges(oracle_lib):
+    """The total does not depend on the splitting; with a large alpha the minimum-image
+    real-space sum equals the 27-cell one."""
+    rng = np.random.default_rng(3)
+    L = 4.7
+    osys, _ = _rock_salt(oracle_lib, L, 5.0 / L, 12)
+    R = np.ascontiguousarray(rng.uniform(0, L, size=(4, 3)))
+    ions = np.ascontiguousarray(rng.uniform(0, L, size=(4, 3)))
+    ref = None
+    for alpha, mmax in ((5.0 / L, 12), (6.5 / L, 15), (9.0 / L, 22)):
+        o = oracle_lib.OracleSystem(None, n_up=2, n_dn=2, n_orb=2, n_ions=4, L=L, ions=ions,
+                                    coul=1, coul_Z=1.0, coul_alpha=alpha, coul_mmax=mmax)
+        e = o.coulomb(R, images=True)
+        ref = e if ref is None else ref
+        assert abs(e - ref) < 1e-9
+    o = oracle_lib.OracleSystem(None, n_up=2, n_dn=2, n_orb=2, n_ions=4, L=L, ions=ions,
+                                coul=1, coul_Z=1.0, coul_alpha=10.0 / L, coul_mmax=24)
+    assert abs(o.coulomb(R, images=False) - ref) < 1e-8
+    # a charged system: the background term keeps the total independent of alpha too
+    e1 = oracle_lib.OracleSystem(None, n_up=2, n_dn=2, n_orb=2, n_ions=4, L=L, ions=ions,
+                                 coul=1, coul_Z=2.0, coul_alpha=5.0 / L,
+                                 coul_mmax=12).coulomb(R, images=True)
+    e2 = oracle_lib.OracleSystem(None, n_up=2, n_dn=2, n_orb=2, n_ions=4, L=L, ions=ions,
+                                 coul=1, coul_Z=2.0, coul_alpha=8.0 / L,
+                                 coul_mmax=20).coulomb(R, images=True)
+    assert abs(e1 - e2) < 1e-9
