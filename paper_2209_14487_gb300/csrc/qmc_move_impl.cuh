@@ -119,9 +119,14 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.bar = o; o += 16;
   L.stc = o; o += p.use_tma ? al16((size_t)p.stencil_bytes + 128) : 0;  // +128: alignment slack
   // tensor-core flush staging: shares the stencil buffer (unused during a flush) when that
-  // is large enough
+  // is large enough, else the move's phi', partial sums and column (dead during a flush,
+  // see accept_update) when those are, else a buffer of its own
   L.tcs = L.stc;
-  if (p.tc_flush && !(p.use_tma && p.stencil_bytes >= TC_STAGE_BYTES)) {
+  const size_t move_bufs =
+      al16((size_t)5 * p.n_pad * es) + al16((size_t)16 * p.n_pad * es) + al16((size_t)p.n_pad * es);
+  const bool need_stage = p.tc_flush && !(p.use_tma && p.stencil_bytes >= TC_STAGE_BYTES);
+  const bool over_move = need_stage && es == 4 && move_bufs >= (size_t)TC_STAGE_BYTES + 128;
+  if (need_stage && !over_move) {
     L.tcs = o;
     o += al16((size_t)TC_STAGE_BYTES + 128);
   }
@@ -135,6 +140,7 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.phi = o; o += al16((size_t)5 * p.n_pad * es);
   L.part = o; o += al16((size_t)16 * p.n_pad * es);
   L.col = o; o += al16((size_t)p.n_pad * es);
+  if (over_move) L.tcs = L.phi;
   L.dchi = o; o += al16((size_t)p.N * 3 * es);
   L.du = o; o += al16((size_t)p.N * es);
   L.red0 = o; o += al16((size_t)NWARP * 8 * 8);  // eight values per warp, FP64 at most
@@ -207,6 +213,7 @@ struct Ctx {
   uint32_t mma_phase;
   float* tcs;         // tensor-core staging: A hi, A lo, B hi, B lo (128 x 32 each)
   bool tc;            // windows flushed on the tensor cores (TMEM held by this CTA)
+  bool tc_over_move;  // their operand stage overlays phi', part and col
   bool failed;        // a bounded wait ran out (status set); the sweep stops
   // stencil items of this thread (orbital j, x offset a), at most 4
   int nit;
@@ -1117,12 +1124,29 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
     int m = c.sc->m;
     bool dup = false;
     for (int l = 0; l < m; ++l) dup |= (c.wP[l] == pp);
+    // with the flush's operand stage over phi', the five new rows go out and phi' itself
+    // moves into the window's free slot m before any flush can overwrite it
+    const bool over = c.tc_over_move;
+    if (over) {
+      for (int j = c.tid; j < n; j += NT) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = c.phi[q * n_pad + j];
+      }
+      T* vs = c.wV + (size_t)m * p.vs;
+      for (int j = c.tid; j < n; j += NT) vs[j] = c.phi[j];
+      __syncthreads();
+    }
     if (dup) {
-      flush_window(c);
+      flush_window(c);  // applies slots l < m; slot m is not read
+      if (over) {  // the saved row to slot 0
+        const T* vs = c.wV + (size_t)m * p.vs;
+        for (int j = c.tid; j < n; j += NT) c.wV[j] = vs[j];
+      }
       m = 0;
     }
     T* vm = c.wV + (size_t)m * p.vs;
-    for (int j = c.tid; j < n; j += NT) vm[j] = c.phi[j];
+    if (!over)
+      for (int j = c.tid; j < n; j += NT) vm[j] = c.phi[j];
     if (c.tid == 0) c.wP[m] = pp;
     __syncthreads();
     for (int l = c.warp; l <= m; l += NWARP) {
@@ -1163,9 +1187,11 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
     __syncthreads();
     if (m + 1 >= p.k) flush_window(c);
   }
-  for (int j = c.tid; j < n; j += NT) {
+  if (!(c.upd == 1 && c.tc_over_move)) {
+    for (int j = c.tid; j < n; j += NT) {
 #pragma unroll
-    for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = c.phi[q * n_pad + j];
+      for (int q = 0; q < 5; ++q) rw[q * n_pad + j] = c.phi[q * n_pad + j];
+    }
   }
   if (c.tid == 0) {
     for (int k = 0; k < 3; ++k) {
@@ -1748,6 +1774,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
   c.mma_phase = 0;
   c.tcs = (float*)((reinterpret_cast<uintptr_t>(smem + lay.tcs) + 127) & ~(uintptr_t)127);
   c.tc = false;
+  c.tc_over_move = lay.tcs == lay.phi;
   c.failed = false;
   c.nit = 0;
 #pragma unroll
@@ -2068,9 +2095,11 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
   }
 }
 
+// Two CTAs per SM; with the inverse in global memory at 256 threads the shared memory
+// already holds one CTA per SM, so the register cap is lifted to that of one CTA.
 template <typename T, int MODE, int UPD, int BSM>
-__global__ void __launch_bounds__(NT, 2) move_kernel(const Params p,
-                                                     const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(NT, (BSM == 2 && NT >= 256) ? 1 : 2)
+    move_kernel(const Params p, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(16) unsigned char smem[];
   move_body<T, MODE, UPD, BSM>(p, blockIdx.x, &tmap, smem);
 }

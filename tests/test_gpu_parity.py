@@ -498,10 +498,10 @@ def test_dmc1536_mixed_sampled(Q, oracle_lib, update, k):
     walkers: the inverse lives in global memory, each thread has stencil items beyond its
     four and Jastrow partners beyond its cached slots.  Proposals meet the mixed-path bound
     against the oracle; after a fixed-node generation log|Psi| agrees with the oracle's FP64
-    recompute at the GPU's positions, no walker changed its sign, E_L agrees to 1e-3 for
-    every walker whose FP32 inverse is accurate to 1e-3 (max|A^-1 A - I|; an ill-conditioned
-    walker's FP32 inverse is not, see the readings), and after the GPU's own FP64 recompute
-    every walker's E_L agrees to 1e-5."""
+    recompute at the GPU's positions (a repeated accept included), no walker changed its
+    sign, E_L agrees to 1e-3 for every walker whose FP32 inverse is accurate to 1e-3
+    (max|A^-1 A - I|; an ill-conditioned walker's FP32 inverse is not), and after the GPU's
+    own FP64 recompute every walker's E_L agrees to 1e-5."""
     wl = _dmc1536()
     W = 2
     R = np.ascontiguousarray(wl.positions(n_walkers=W))
@@ -516,7 +516,9 @@ def test_dmc1536_mixed_sampled(Q, oracle_lib, update, k):
     rng = np.random.default_rng(15)
     eps32 = 2.0 ** -24
     n = wl.n_up
-    for iel in [0, n - 1, n, wl.n_el - 1, 400]:
+    # electron 400 twice: its second accept finds its row already in walker 0's window
+    # (the flush of a repeated row), then electron 3 reads the inverse after that flush
+    for iel in [0, n - 1, n, wl.n_el - 1, 400, 400, 3]:
         rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.1, size=(W, 3)), wl.L)
         lr, grad = np.zeros(W), np.zeros((W, 3))
         gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, grad, lr)
