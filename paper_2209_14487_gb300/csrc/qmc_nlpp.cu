@@ -27,6 +27,7 @@ namespace {
 constexpr int NL_NT = 256;
 constexpr int NL_NW = NL_NT / 32;
 constexpr int NL_SPLIT = 4;  // CTAs per walker
+constexpr int NL_QB = 2;     // quadrature points evaluated together
 
 // Vertex q of the icosahedron: (0, +-1, +-phi) / sqrt(1 + phi^2) for q < 4 and its cyclic
 // shifts (+-1, +-phi, 0), (+-phi, 0, +-1) for q / 4 = 1, 2; bits 0 and 1 of q are the signs.
@@ -65,37 +66,76 @@ __device__ __forceinline__ void disp(const NlCtx<T>& c, const Pt<T>& a, const Pt
   r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
 }
 
-// sum over partners t != i (electrons, then ions) of u(|x - r_t|): the warp total.
-template <typename T>
-__device__ T jastrow_sum(const NlCtx<T>& c, int i, const Pt<T>& x) {
+// out[b] = sum over partners t != i (electrons, then ions) of u(|x[b] - r_t|) for B points
+// at once (independent chains): the warp totals.
+template <typename T, int B>
+__device__ void jastrow_sums(const NlCtx<T>& c, int i, const Pt<T>* x, T* out) {
   const Params& p = c.p;
   const int N = p.N;
   const int t0 = p.K2 > 0 ? 0 : N, t1 = p.K1 > 0 ? N + p.n_ions : N;
-  T acc = 0;
+  T acc[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) acc[b] = 0;
   for (int t = t0 + c.lane; t < t1; t += 32) {
     if (t == i) continue;
-    T d[3], r;
+    const Pt<T>& pt = t < N ? c.R[t] : c.ion[t - N];
     const T* coef;
     int K;
     T hinv, rc;
     if (t < N) {
-      disp(c, x, c.R[t], d, r);
       coef = c.jc + (((i < p.n_up) == (t < p.n_up)) ? 0 : p.K2 + 3);
       K = p.K2;
       hinv = c.h2inv;
       rc = c.rc2;
     } else {
-      disp(c, x, c.ion[t - N], d, r);
       coef = c.jc + 2 * (p.K2 + 3);
       K = p.K1;
       hinv = c.h1inv;
       rc = c.rc1;
     }
-    T u, du, d2u;
-    radial(coef, K, hinv, rc, r, u, du, d2u);
-    acc += u;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      T d[3], r, u, du, d2u;
+      disp(c, x[b], pt, d, r);
+      radial(coef, K, hinv, rc, r, u, du, d2u);
+      acc[b] += u;
+    }
   }
-  return warp_sum(acc);
+#pragma unroll
+  for (int b = 0; b < B; ++b) out[b] = warp_sum(acc[b]);
+}
+
+// Quadrature point q of the pair (electron, ion I at distance r): R_I + r u_q, its spline
+// cell and value weights.
+template <typename T>
+__device__ __forceinline__ void quad_point(const NlCtx<T>& c, const Pt<T>& ion, T r, int q,
+                                           T* u, Pt<T>& xq, int* cell, T (*wt)[4]) {
+  const Params& p = c.p;
+  ico_vertex(q, u);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T t;
+    if constexpr (IsMixed<T>::value) {  // fixed point wraps by itself
+      xq.q[k] = ion.q[k] + (uint32_t)__float2int_rn(r * u[k] * c.scale);
+      const unsigned long long prod = (unsigned long long)xq.q[k] * (unsigned long long)p.G;
+      cell[k] = (int)(prod >> 32);
+      t = (float)(uint32_t)prod * 0x1p-32f;
+    } else {
+      double x = ion.x[k] + r * u[k];
+      x -= p.L * floor(x * p.invL);
+      xq.x[k] = x;
+      const double sg = x * p.dgrid;
+      int g = (int)floor(sg);
+      g = g > p.G - 1 ? p.G - 1 : (g < 0 ? 0 : g);
+      cell[k] = g;
+      t = sg - (double)g;
+    }
+    const T t2 = t * t, t3 = t2 * t, sm = T(1) - t, sixth = T(1) / T(6);
+    wt[k][0] = sm * sm * sm * sixth;
+    wt[k][1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
+    wt[k][2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
+    wt[k][3] = t3 * sixth;
+  }
 }
 
 // Shared-memory layout (byte offsets, each 16-byte aligned): electrons, ions, radial
@@ -155,67 +195,54 @@ __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* 
       disp(c, R[i], ion[I], d, r);  // r_i - R_I
       if (!(r < (T)p.nl_rc) || !(r > T(0))) continue;  // the same on every lane
       if (!have_u0) {
-        u0 = jastrow_sum(c, i, R[i]);
+        jastrow_sums<T, 1>(c, i, &R[i], &u0);
         have_u0 = true;
       }
       const T rinv = T(1) / r;
       T acc0 = 0, acc1 = 0, acc2 = 0;
-      for (int q = 0; q < 12; ++q) {
-        T u[3];
-        ico_vertex(q, u);
-        Pt<T> xq;
-        int cell[3];
-        T wt[3][4];
+      for (int q0 = 0; q0 < 12; q0 += NL_QB) {  // NL_QB points at once: independent chains
+        T u[NL_QB][3];
+        Pt<T> xq[NL_QB];
+        int cell[NL_QB][3];
+        T wt[NL_QB][3][4];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          T t;
-          if constexpr (IsMixed<T>::value) {  // R_I + r u_q in fixed point (wraps by itself)
-            xq.q[k] = ion[I].q[k] + (uint32_t)__float2int_rn(r * u[k] * c.scale);
-            const unsigned long long prod =
-                (unsigned long long)xq.q[k] * (unsigned long long)p.G;
-            cell[k] = (int)(prod >> 32);
-            t = (float)(uint32_t)prod * 0x1p-32f;
-          } else {
-            double x = ion[I].x[k] + r * u[k];
-            x -= p.L * floor(x * p.invL);
-            xq.x[k] = x;
-            const double sg = x * p.dgrid;
-            int g = (int)floor(sg);
-            g = g > p.G - 1 ? p.G - 1 : (g < 0 ? 0 : g);
-            cell[k] = g;
-            t = sg - (double)g;
-          }
-          const T t2 = t * t, t3 = t2 * t, sm = T(1) - t, sixth = T(1) / T(6);
-          wt[k][0] = sm * sm * sm * sixth;
-          wt[k][1] = (T(3) * t3 - T(6) * t2 + T(4)) * sixth;
-          wt[k][2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * sixth;
-          wt[k][3] = t3 * sixth;
-        }
-        // the orbitals' values at the point, dotted with the inverse's column
-        T det = 0;
+        for (int b = 0; b < NL_QB; ++b) quad_point(c, ion[I], r, q0 + b, u[b], xq[b], cell[b], wt[b]);
+        // the orbitals' values at the points, dotted with the inverse's column
+        T det[NL_QB];
+#pragma unroll
+        for (int b = 0; b < NL_QB; ++b) det[b] = 0;
         for (int j = lane; j < n; j += 32) {
-          T v = 0;
+          const T bj = bcol[j];
+#pragma unroll
+          for (int b = 0; b < NL_QB; ++b) {
+            T v = 0;
 #pragma unroll 1
-          for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const T* row = table + (((size_t)(cell[0] + a) * GP + cell[1] + b) * GP +
-                                      cell[2]) * (size_t)n_pad + j;
-              const T wab = wt[0][a] * wt[1][b];
+              for (int bb = 0; bb < 4; ++bb) {
+                const T* row = table + (((size_t)(cell[b][0] + a) * GP + cell[b][1] + bb) * GP +
+                                        cell[b][2]) * (size_t)n_pad + j;
+                const T wab = wt[b][0][a] * wt[b][1][bb];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) v += wab * wt[2][e] * __ldg(row + (size_t)e * n_pad);
-            }
-          det += v * bcol[j];
+                for (int e = 0; e < 4; ++e)
+                  v += wab * wt[b][2][e] * __ldg(row + (size_t)e * n_pad);
+              }
+            det[b] += v * bj;
+          }
         }
-        det = warp_sum(det);
-        const T u1 = jastrow_sum(c, i, xq);
-        T rho;
-        if constexpr (IsMixed<T>::value) rho = det * __expf(u0 - u1);
-        else rho = det * exp(u0 - u1);
-        const T cth = (d[0] * u[0] + d[1] * u[1] + d[2] * u[2]) * rinv;
-        acc0 += rho;
-        acc1 += cth * rho;
-        acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
+        T u1[NL_QB];
+        jastrow_sums<T, NL_QB>(c, i, xq, u1);
+#pragma unroll
+        for (int b = 0; b < NL_QB; ++b) {
+          const T dt = warp_sum(det[b]);
+          T rho;
+          if constexpr (IsMixed<T>::value) rho = dt * __expf(u0 - u1[b]);
+          else rho = dt * exp(u0 - u1[b]);
+          const T cth = (d[0] * u[b][0] + d[1] * u[b][1] + d[2] * u[b][2]) * rinv;
+          acc0 += rho;
+          acc1 += cth * rho;
+          acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
+        }
       }
       if (lane == 0) {
         const double acc[3] = {(double)acc0, (double)acc1, (double)acc2};
