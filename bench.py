@@ -557,6 +557,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dmc", action="store_true",
                     help="fixed-node DMC generations (sweep + branching) instead of VMC")
+    ap.add_argument("--tau", type=float, default=None,
+                    help="time step (default: the workload's; DMC wants about 0.01)")
     ap.add_argument("--cpu-walkers", type=int, default=None,
                     help="walkers of the CPU oracle sample (default: all)")
     ap.add_argument("--nlpp", action="store_true",
@@ -575,6 +577,8 @@ def main():
     wl = workloads.WORKLOADS[args.workload]()
     if args.walkers:
         wl.n_walkers = args.walkers
+    if args.tau:
+        wl.tau = args.tau
     ws, rank, local = dist_env()
     update = args.update
     k = args.delay_rank or (1 if update == "sm" else 8)
