@@ -320,6 +320,82 @@ def scan_main(args, wl, ws, rank, cfg):
         print(json.dumps(out))
 
 
+def batch_main(args, ws, rank, cfg):
+    """The mixed-size batch (64/192/384 electrons with 512/256/128 walkers): one launch per
+    generation for every walker of the three crowds (qmc_batch_sweep, CUDA graph replay),
+    against the same crowds swept one after the other."""
+    import torch
+
+    from paper_2209_14487_gb300 import qmcgb, workloads
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        uuid = None
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    nt = args.cta_threads or 128  # one width for the whole batch
+    wls = [make() for make in workloads.MIXED_BATCH]
+    crowds = []
+    for wl in wls:
+        c = qmcgb.Crowd.from_workload(wl, precision="mixed", stream=stream.cuda_stream,
+                                      cta_threads=nt)
+        c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=rank)))
+        c.qmc_recompute()
+        crowds.append(c)
+    b = qmcgb.Batch(crowds)
+    moves = sum(wl.n_walkers * wl.n_el for wl in wls)
+
+    def timed(step):
+        ms = []
+        for g in range(args.warmup + args.steps):
+            flush.add_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            if g >= args.warmup:
+                ms.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(z) for a, z in ms]
+
+    barrier(ws)
+    with ClockSampler(uuid) as clk:
+        l0 = b.launch_count
+        ms_b = timed(lambda: b.qmc_batch_sweep(1, eloc=False, stats=False))
+        launches = b.launch_count - l0
+        ms_s = timed(lambda: [c.qmc_sweep(1, stats=False) for c in crowds])
+    _, st = b.qmc_batch_sweep(1, eloc=False, stats=True)
+    barrier(ws)
+    value = aggregate_value(moves * args.steps, sum(ms_b) / 1000.0, ws)
+    t_b = statistics.mean(ms_b) / 1000.0
+    bpg = sum(wl.n_walkers * wl.n_el *
+              bytes_per_move(wl.n_orb, wl.n_el, 4, s_.n_accept / max(1, s_.n_moves), "sm", 1)
+              for wl, s_ in zip(wls, st))
+    hbm, src = peaks()
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": statistics.mean(ms_b), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "mixed-size batch: " + " + ".join(
+               f"{wl.name} ({wl.n_el} e, {wl.n_walkers} walkers)" for wl in wls),
+               "step": "one generation of every walker of the three crowds",
+               "l2": cfg["l2"], "precision": "mixed", "update": "sm", "cta_threads": nt,
+               "parallelism": f"replicas x{ws}"},
+           "sequential": {"value": aggregate_value(moves * args.steps, sum(ms_s) / 1000.0, ws),
+                          "ms_per_step": statistics.mean(ms_s), "unit": UNIT},
+           "roofline": {"bound": "hbm", "achieved": bpg / t_b / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": bpg / t_b / 1e9 / hbm, "traffic": None,
+                        "kernel": "move_kernel_batch<float> (fused generation, three crowds)",
+                        "bytes_per_generation": bpg, "peak_source": src},
+           "gpu_launches": launches, "clocks": clk.summary()}
+    b.close()
+    for c in crowds:
+        c.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, feedback=0.1,
              ws=1, crowd_id=0):
     """Fixed-node DMC generations of the mixed path: qmc_sweep(1) with E_L read back to the
@@ -565,6 +641,8 @@ def main():
                     help="also time the mixed path with the synthetic nonlocal term in E_L")
     ap.add_argument("--coulomb", action="store_true",
                     help="also time the mixed path with the Ewald Coulomb energy in E_L")
+    ap.add_argument("--batch", action="store_true",
+                    help="the mixed-size batch (64/192/384 electrons) in one launch per generation")
     ap.add_argument("--walker-scan", default=None,
                     help="comma-separated walkers per GPU: throughput against crowd size")
     ap.add_argument("--crowds", default=None,
@@ -643,6 +721,12 @@ def main():
         uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
     except Exception:
         uuid = None
+    if args.batch:
+        batch_main(args, ws, rank, cfg)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     if args.walker_scan or args.crowds:
         scan_main(args, wl, ws, rank, cfg)
         if ws > 1:
