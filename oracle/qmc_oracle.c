@@ -19,7 +19,11 @@
  * Pins (tests/): cubic-polynomial reproduction and plane-wave node values of the spline,
  * central differences of value/gradient/Laplacian, Leibniz determinants, A^-1 A = I,
  * ratios against full recomputes of log|Psi|, delayed == Sherman-Morrison, the
- * free-electron zero-variance local energy, Philox known answers, Metropolis histogram.
+ * free-electron zero-variance local energy, Philox known answers, Metropolis histogram;
+ * DMC weights in closed form, unbiased multiplicities, the fixed-node rejection and the
+ * zero-variance static population; the nonlocal term against full recomputes and the
+ * exact sphere average of a plane wave (l = 0, 1, 2); the Ewald sum against the rock-salt
+ * Madelung constant and its independence of the splitting.
  */
 #include <math.h>
 #include <stdint.h>
