@@ -10,12 +10,11 @@
 // orbitals' values at the point dotted with electron i's column of A^-1, times
 // exp(-(U_i(point) - U_i(r_i))).
 //
-// NL_SPLIT CTAs per walker (more CTAs than SMs, two resident per SM), CTA y taking the
-// electrons y, y + NL_SPLIT, ...; its warps take the work items (electron, ion, batch of
-// quadrature points) in turn, so the pairs within the cutoff spread evenly over them; lanes
-// run over orbitals for the determinant and over partners for the Jastrow sums.  Each CTA
-// writes its FP64 sum to a partial slot; a second kernel adds a walker's partials to E_L in
-// a fixed order, so E_L stays deterministic.  The mixed path works
+// NL_SPLIT CTAs per walker (more CTAs than SMs, two resident per SM); one warp per
+// electron (the walker's 32 warps take electrons gw, gw + 32, ...), lanes over orbitals for
+// the determinant and over partners for the Jastrow sums.  Each CTA writes its FP64 sum
+// to a partial slot; a second kernel adds a walker's partials to E_L in a fixed order, so
+// E_L stays deterministic.  The mixed path works
 // in FP32 on 32-bit fixed-point positions like the move kernel; the FP64 path in double.
 #include <cmath>
 
@@ -142,7 +141,7 @@ __device__ __forceinline__ void quad_point(const NlCtx<T>& c, const Pt<T>& ion, 
 // Shared-memory layout (byte offsets, each 16-byte aligned): electrons, ions, radial
 // coefficients, the warps' FP64 partial sums.
 struct NlLay {
-  size_t R, ion, jc, U, red, total;
+  size_t R, ion, jc, red, total;
 };
 
 __host__ __device__ inline size_t nl_al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -154,8 +153,7 @@ __host__ __device__ inline NlLay nl_lay(const Params& p) {
   L.R = 0;
   L.ion = nl_al16(L.R + (size_t)p.N * sizeof(Pt<T>));
   L.jc = nl_al16(L.ion + (size_t)p.n_ions * sizeof(Pt<T>));
-  L.U = nl_al16(L.jc + njc * sizeof(T));  // U_i of this CTA's electrons
-  L.red = nl_al16(L.U + ((size_t)p.N / NL_SPLIT + 1) * sizeof(T));
+  L.red = nl_al16(L.jc + njc * sizeof(T));
   L.total = L.red + NL_NW * sizeof(double);
   return L;
 }
@@ -165,11 +163,11 @@ __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* 
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = blockIdx.x, N = p.N, NI = p.n_ions, n = p.n, n_pad = p.n_pad, GP = p.GP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.y * NL_NW + warp;  // this warp among the walker's
   const NlLay lay = nl_lay<T>(p);
   Pt<T>* R = reinterpret_cast<Pt<T>*>(smem + lay.R);
   Pt<T>* ion = reinterpret_cast<Pt<T>*>(smem + lay.ion);
   T* jc = reinterpret_cast<T*>(smem + lay.jc);
-  T* Ue = reinterpret_cast<T*>(smem + lay.U);
   double* red = reinterpret_cast<double*>(smem + lay.red);
   const int njc = 2 * (p.K2 + 3) + p.K1 + 3;
   const double* Rg = p.R + (size_t)w * N * 3;
@@ -187,80 +185,71 @@ __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* 
   const T* table = (const T*)p.table;
   const T* Bw = (const T*)p.binv + (size_t)w * 2 * n * n;
   double vsum = 0.0;  // lane 0 of each warp
-  // this CTA's electrons: i = blockIdx.y + NL_SPLIT e; their U_i first, once each
-  const int nE = (N - (int)blockIdx.y + NL_SPLIT - 1) / NL_SPLIT;
-  for (int e = warp; e < nE; e += NL_NW) {
-    const int i = blockIdx.y + NL_SPLIT * e;
-    T u0;
-    jastrow_sums<T, 1>(c, i, &R[i], &u0);
-    if (lane == 0) Ue[e] = u0;
-  }
-  __syncthreads();
-  // work items (electron, ion, batch of NL_QB quadrature points), dealt to the warps in
-  // turn so that the pairs within nl_rc spread evenly; out-of-range items cost a distance
-  constexpr int NQB = 12 / NL_QB;
-  const int n_items = nE * NI * NQB;
-  for (int item = warp; item < n_items; item += NL_NW) {
-    const int e = item / (NI * NQB), rem = item - e * (NI * NQB);
-    const int I = rem / NQB, q0 = (rem - I * NQB) * NL_QB;
-    const int i = blockIdx.y + NL_SPLIT * e;
-    T d[3], r;
-    disp(c, R[i], ion[I], d, r);  // r_i - R_I
-    if (!(r < (T)p.nl_rc) || !(r > T(0))) continue;  // the same on every lane
+  for (int i = gw; i < N; i += NL_NW * NL_SPLIT) {
     const int s = i < p.n_up ? 0 : 1;
     const T* bcol = Bw + ((size_t)s * n + (i - s * p.n_up)) * n;  // column of A^-1
-    const T u0 = Ue[e];
-    const T rinv = T(1) / r;
-    T acc0 = 0, acc1 = 0, acc2 = 0;
-    {
-      T u[NL_QB][3];
-      Pt<T> xq[NL_QB];
-      int cell[NL_QB][3];
-      T wt[NL_QB][3][4];
+    bool have_u0 = false;
+    T u0 = 0;
+    for (int I = 0; I < NI; ++I) {
+      T d[3], r;
+      disp(c, R[i], ion[I], d, r);  // r_i - R_I
+      if (!(r < (T)p.nl_rc) || !(r > T(0))) continue;  // the same on every lane
+      if (!have_u0) {
+        jastrow_sums<T, 1>(c, i, &R[i], &u0);
+        have_u0 = true;
+      }
+      const T rinv = T(1) / r;
+      T acc0 = 0, acc1 = 0, acc2 = 0;
+      for (int q0 = 0; q0 < 12; q0 += NL_QB) {  // NL_QB points at once: independent chains
+        T u[NL_QB][3];
+        Pt<T> xq[NL_QB];
+        int cell[NL_QB][3];
+        T wt[NL_QB][3][4];
 #pragma unroll
-      for (int b = 0; b < NL_QB; ++b) quad_point(c, ion[I], r, q0 + b, u[b], xq[b], cell[b], wt[b]);
-      // the orbitals' values at the points, dotted with the inverse's column
-      T det[NL_QB];
+        for (int b = 0; b < NL_QB; ++b) quad_point(c, ion[I], r, q0 + b, u[b], xq[b], cell[b], wt[b]);
+        // the orbitals' values at the points, dotted with the inverse's column
+        T det[NL_QB];
 #pragma unroll
-      for (int b = 0; b < NL_QB; ++b) det[b] = 0;
-      for (int j = lane; j < n; j += 32) {
-        const T bj = bcol[j];
+        for (int b = 0; b < NL_QB; ++b) det[b] = 0;
+        for (int j = lane; j < n; j += 32) {
+          const T bj = bcol[j];
+#pragma unroll
+          for (int b = 0; b < NL_QB; ++b) {
+            T v = 0;
+#pragma unroll 1
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int bb = 0; bb < 4; ++bb) {
+                const T* row = table + (((size_t)(cell[b][0] + a) * GP + cell[b][1] + bb) * GP +
+                                        cell[b][2]) * (size_t)n_pad + j;
+                const T wab = wt[b][0][a] * wt[b][1][bb];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  v += wab * wt[b][2][e] * __ldg(row + (size_t)e * n_pad);
+              }
+            det[b] += v * bj;
+          }
+        }
+        T u1[NL_QB];
+        jastrow_sums<T, NL_QB>(c, i, xq, u1);
 #pragma unroll
         for (int b = 0; b < NL_QB; ++b) {
-          T v = 0;
-#pragma unroll 1
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-              const T* row = table + (((size_t)(cell[b][0] + a) * GP + cell[b][1] + bb) * GP +
-                                      cell[b][2]) * (size_t)n_pad + j;
-              const T wab = wt[b][0][a] * wt[b][1][bb];
-#pragma unroll
-              for (int e2 = 0; e2 < 4; ++e2)
-                v += wab * wt[b][2][e2] * __ldg(row + (size_t)e2 * n_pad);
-            }
-          det[b] += v * bj;
+          const T dt = warp_sum(det[b]);
+          T rho;
+          if constexpr (IsMixed<T>::value) rho = dt * __expf(u0 - u1[b]);
+          else rho = dt * exp(u0 - u1[b]);
+          const T cth = (d[0] * u[b][0] + d[1] * u[b][1] + d[2] * u[b][2]) * rinv;
+          acc0 += rho;
+          acc1 += cth * rho;
+          acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
         }
       }
-      T u1[NL_QB];
-      jastrow_sums<T, NL_QB>(c, i, xq, u1);
-#pragma unroll
-      for (int b = 0; b < NL_QB; ++b) {
-        const T dt = warp_sum(det[b]);
-        T rho;
-        if constexpr (IsMixed<T>::value) rho = dt * __expf(u0 - u1[b]);
-        else rho = dt * exp(u0 - u1[b]);
-        const T cth = (d[0] * u[b][0] + d[1] * u[b][1] + d[2] * u[b][2]) * rinv;
-        acc0 += rho;
-        acc1 += cth * rho;
-        acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
+      if (lane == 0) {
+        const double acc[3] = {(double)acc0, (double)acc1, (double)acc2};
+        const double r2 = (double)r * (double)r;
+        for (int l = 0; l < p.nl_n; ++l)
+          vsum += p.nl_a[l] * exp(-r2 * p.nl_sinv2[l]) * (double)(2 * l + 1) * acc[l] / 12.0;
       }
-    }
-    if (lane == 0) {
-      const double acc[3] = {(double)acc0, (double)acc1, (double)acc2};
-      const double r2 = (double)r * (double)r;
-      for (int l = 0; l < p.nl_n; ++l)
-        vsum += p.nl_a[l] * exp(-r2 * p.nl_sinv2[l]) * (double)(2 * l + 1) * acc[l] / 12.0;
     }
   }
   double v1[1] = {vsum};
