@@ -77,7 +77,10 @@ typedef struct qmc_run_desc {
   int precision;    /* QMC_PREC_FP64: FP64 everywhere; QMC_PREC_MIXED: FP32 orbitals,  *
                      * Jastrow, ratios and inverse, FP64 recompute and energy sums     */
   int update;       /* QMC_UPDATE_SM (rank-1 per accept) or QMC_UPDATE_DELAYED         */
-  int delay_rank;   /* k for QMC_UPDATE_DELAYED, 1..64                                 */
+  int delay_rank;   /* k for QMC_UPDATE_DELAYED, 1..64; 0: the library picks k (the   *
+                     * largest rank up to 32 its shared-memory plan holds with the       *
+                     * inverse in global memory, 8 when the inverse fits in shared       *
+                     * memory: the measured optima on GB300); qmc_get_update reports it  */
   int n_recompute;  /* generations between FP64 recomputes of A^-1; 0 = never        */
   int drift;        /* 1: drift-diffusion proposal with Metropolis-Hastings            */
   int potential;    /* 1: add the model potential to E_L                              */
@@ -244,6 +247,9 @@ int qmc_dmc_branch(qmc_crowd* crowd, const double* e_prev, double* e_new, int me
                    double e_trial, qmc_dmc_stats* out);
 /* Active walkers of the crowd (n_walkers unless DMC branching changed it). */
 int qmc_get_walker_count(const qmc_crowd* crowd, int* count);
+/* The crowd's update scheme and delay rank (the library's pick when run.delay_rank was 0;
+ * 1 for Sherman-Morrison). */
+int qmc_get_update(const qmc_crowd* crowd, int* update, int* delay_rank);
 
 /* ---------------------------------------------------------------------------------------
  * Nonlocal pseudopotential in E_L (the locality approximation; the paper's NiO runs use

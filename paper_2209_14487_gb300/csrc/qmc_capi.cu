@@ -352,7 +352,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   if (run->update != QMC_UPDATE_SM && run->update != QMC_UPDATE_DELAYED)
     return QMC_ERR_INVALID_ARG;
   if (run->update == QMC_UPDATE_DELAYED &&
-      (run->delay_rank < 1 || run->delay_rank > qmcgb::MAX_K))
+      (run->delay_rank < 0 || run->delay_rank > qmcgb::MAX_K))  // 0: the library picks k
     return QMC_ERR_INVALID_ARG;
   if (run->n_recompute < 0) return QMC_ERR_INVALID_ARG;
   if (run->staging != QMC_STAGING_AUTO && run->staging != QMC_STAGING_LDG)
@@ -422,32 +422,46 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
                      (p.nt == 128 || p.nt == 256);
   const int plans[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   size_t smem = 0;
-  bool placed = false;
-  for (const auto& pl : plans) {
-    if (pl[1] && !tma_ok) continue;
-    p.b_in_smem = pl[0];
-    p.use_tma = pl[1];
-    p.tc_flush = (tc_ok && !pl[0]) ? 1 : 0;
-    p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
-    smem = qmcgb::move_smem_bytes(p, es);
-    if (optin <= 0 || smem <= (size_t)optin) {
-      placed = true;
-      break;
-    }
-  }
-  if (!placed && tc_ok) {  // without the tensor-core stage
+  // the first plan that fits for delay rank k (sets p.k, p.ks and the plan's fields)
+  auto place = [&](int k) -> bool {
+    p.k = k;
+    p.ks = k + 1;
     for (const auto& pl : plans) {
-      if (pl[0] || (pl[1] && !tma_ok)) continue;
-      p.b_in_smem = 0;
+      if (pl[1] && !tma_ok) continue;
+      p.b_in_smem = pl[0];
       p.use_tma = pl[1];
-      p.tc_flush = 0;
+      p.tc_flush = (tc_ok && !pl[0]) ? 1 : 0;
       p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
       smem = qmcgb::move_smem_bytes(p, es);
-      if (optin <= 0 || smem <= (size_t)optin) {
+      if (optin <= 0 || smem <= (size_t)optin) return true;
+    }
+    if (tc_ok) {  // without the tensor-core stage
+      for (const auto& pl : plans) {
+        if (pl[0] || (pl[1] && !tma_ok)) continue;
+        p.b_in_smem = 0;
+        p.use_tma = pl[1];
+        p.tc_flush = 0;
+        p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
+        smem = qmcgb::move_smem_bytes(p, es);
+        if (optin <= 0 || smem <= (size_t)optin) return true;
+      }
+    }
+    return false;
+  };
+  bool placed = false;
+  if (run->update == QMC_UPDATE_DELAYED && run->delay_rank == 0) {
+    // the library's pick (measured optima on GB300): the largest rank up to 32 that fits
+    // with the inverse in global memory; 8 when the inverse fits in shared memory
+    for (int k : {32, 16, 8, 4, 2, 1}) {
+      if (place(k)) {
         placed = true;
         break;
       }
     }
+    if (placed && p.k > 8 && p.b_in_smem) placed = place(8);
+    c->run.delay_rank = p.k;
+  } else {
+    placed = place(p.k);
   }
   if (!placed) {
     delete c;
@@ -897,6 +911,13 @@ int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, 
   if (b_in_smem) *b_in_smem = c->p.b_in_smem;
   if (stencil_tma) *stencil_tma = c->p.use_tma;
   if (smem_bytes) *smem_bytes = (int)c->smem;
+  return QMC_OK;
+}
+
+int qmc_get_update(const qmc_crowd* c, int* update, int* delay_rank) {
+  if (!c || !update || !delay_rank) return QMC_ERR_INVALID_ARG;
+  *update = c->run.update;
+  *delay_rank = c->run.update == QMC_UPDATE_DELAYED ? c->run.delay_rank : 1;
   return QMC_OK;
 }
 

@@ -38,7 +38,7 @@ EXPORTS = [
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
     "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
     "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count", "qmc_dmc_select",
-    "qmc_dmc_append", "qmc_load_nlpp", "qmc_load_coulomb",
+    "qmc_dmc_append", "qmc_load_nlpp", "qmc_load_coulomb", "qmc_get_update",
 ]
 
 
@@ -106,6 +106,7 @@ def _load():
         "qmc_batch_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
         "qmc_dmc_branch": [vp, vp, vp, i, C.c_double, C.POINTER(qmc_dmc_stats)],
         "qmc_get_walker_count": [vp, C.POINTER(C.c_int)],
+        "qmc_get_update": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "qmc_dmc_select": [vp, vp, i, i],
         "qmc_dmc_append": [vp, vp, i, i],
         "qmc_load_nlpp": [vp, i, vp, vp, C.c_double],
@@ -366,6 +367,13 @@ class Crowd:
         n_add = int(keep.shape[0])
         _check("qmc_dmc_append", lib.qmc_dmc_append(self.h, p, n_add, m))
         self.W += n_add
+
+    @property
+    def delay_rank(self) -> int:
+        """The delay rank in use (the library's pick when created with delay_rank=0)."""
+        u, k = C.c_int(), C.c_int()
+        _check("qmc_get_update", lib.qmc_get_update(self.h, C.byref(u), C.byref(k)))
+        return k.value
 
     @property
     def walker_count(self) -> int:

@@ -566,3 +566,28 @@ def _dmc1536():
     if "wl" not in _C5:
         _C5["wl"] = wl_mod.dmc1536()
     return _C5["wl"]
+
+
+@pytest.mark.parametrize("make,expect", [(wl_mod.pw128, 8), (wl_mod.pw512, 32)])
+def test_library_picks_the_delay_rank(Q, oracle_lib, make, expect):
+    """delay_rank = 0: the library picks k (8 with the inverse in shared memory, else the
+    largest rank up to 32 that fits) and the crowd sweeps as one created with that k."""
+    wl = make()
+    W = 4
+    R = np.ascontiguousarray(wl.positions(n_walkers=W))
+    auto = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=0,
+                                 n_walkers=W, n_recompute=0)
+    assert auto.delay_rank == expect
+    fixed = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=expect,
+                                  n_walkers=W, n_recompute=0)
+    assert auto.kernel_config == fixed.kernel_config
+    out = []
+    for c in (auto, fixed):
+        c.qmc_load_positions(R)
+        c.qmc_recompute()
+        e = np.zeros((2, W))
+        c.qmc_sweep(2, e)
+        out.append((e, c.qmc_get_positions()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    sm = Q.Crowd.from_workload(wl, precision="mixed", update="sm", n_walkers=W)
+    assert sm.delay_rank == 1
