@@ -935,7 +935,33 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
       for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
     }
   }
-  for (int it = c.tid + 4 * NT; it < 4 * n; it += NT) {  // items beyond four per thread
+  // items beyond four per thread, two per pass so that both items' loads are in flight
+  int it = c.tid + 4 * NT;
+  for (; it + NT < 4 * n; it += 2 * NT) {
+    const int j = it % n, a = it / n, j2 = (it + NT) % n, a2 = (it + NT) / n;
+    T cg[16];
+    if (tma) {
+      const T* sa = c.stc + (size_t)(a * 16) * n_pad + j;
+      const T* sb = c.stc + (size_t)(a2 * 16) * n_pad + j2;
+#pragma unroll
+      for (int bc = 0; bc < 16; ++bc) {
+        cf[bc] = sa[(size_t)bc * n_pad];
+        cg[bc] = sb[(size_t)bc * n_pad];
+      }
+    } else {
+      stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], j, a, cf);
+      stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], j2, a2, cg);
+    }
+    T o4[4], o4b[4];
+    stencil_reduce(cf, wts, o4);
+    stencil_reduce(cg, wts, o4b);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      c.part[(a * 4 + r) * n_pad + j] = o4[r];
+      c.part[(a2 * 4 + r) * n_pad + j2] = o4b[r];
+    }
+  }
+  for (; it < 4 * n; it += NT) {
     const int j = it % n, a = it / n;
     if (tma) {
       const T* sb = c.stc + (size_t)(a * 16) * n_pad + j;
