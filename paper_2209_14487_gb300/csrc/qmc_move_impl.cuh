@@ -935,33 +935,8 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
       for (int r = 0; r < 4; ++r) c.part[(a * 4 + r) * n_pad + j] = o4[r];
     }
   }
-  // items beyond four per thread, several per pass so that their loads are in flight
-  // together: four with the inverse in global memory (large n, one CTA per SM, the stencil
-  // from global memory), else two (a register budget the other kernels keep)
+  // items beyond four per thread, two per pass so that both items' loads are in flight
   int it = c.tid + 4 * NT;
-  for (; c.bsm == 2 && it + 3 * NT < 4 * n; it += 4 * NT) {
-    T cq[4][16];
-    int jq[4], aq[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      jq[u] = (it + u * NT) % n;
-      aq[u] = (it + u * NT) / n;
-      if (tma) {
-        const T* sb = c.stc + (size_t)(aq[u] * 16) * n_pad + jq[u];
-#pragma unroll
-        for (int bc = 0; bc < 16; ++bc) cq[u][bc] = sb[(size_t)bc * n_pad];
-      } else {
-        stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], jq[u], aq[u], cq[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      T o4[4];
-      stencil_reduce(cq[u], wts, o4);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) c.part[(aq[u] * 4 + r) * n_pad + jq[u]] = o4[r];
-    }
-  }
   for (; it + NT < 4 * n; it += 2 * NT) {
     const int j = it % n, a = it / n, j2 = (it + NT) % n, a2 = (it + NT) / n;
     T cg[16];
