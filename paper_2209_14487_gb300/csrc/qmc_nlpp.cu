@@ -10,11 +10,13 @@
 // orbitals' values at the point dotted with electron i's column of A^-1, times
 // exp(-(U_i(point) - U_i(r_i))).
 //
-// NL_SPLIT CTAs per walker (more CTAs than SMs, two resident per SM); one warp per
-// electron (the walker's 32 warps take electrons gw, gw + 32, ...), lanes over orbitals for
-// the determinant and over partners for the Jastrow sums.  Each CTA writes its FP64 sum
-// to a partial slot; a second kernel adds a walker's partials to E_L in a fixed order, so
-// E_L stays deterministic.  The mixed path works
+// NL_SPLIT CTAs per walker (more CTAs than SMs, two resident per SM).  A CTA's warps first
+// list the (electron, ion) pairs within the cutoff of their electrons (the walker's 32
+// warps take electrons gw, gw + 32, ...), then take the listed pairs' batches of quadrature
+// points in turn, so the few pairs spread evenly; lanes run over orbitals for the
+// determinant and over partners for the Jastrow sums.  Each CTA writes its FP64 sum to a
+// partial slot; a second kernel adds a walker's partials to E_L in a fixed order, so E_L
+// stays deterministic.  The mixed path works
 // in FP32 on 32-bit fixed-point positions like the move kernel; the FP64 path in double.
 #include <cmath>
 
@@ -28,6 +30,8 @@ constexpr int NL_NT = 256;
 constexpr int NL_NW = NL_NT / 32;
 constexpr int NL_SPLIT = 4;  // CTAs per walker
 constexpr int NL_QB = 2;     // quadrature points evaluated together
+constexpr int NL_NQB = 12 / NL_QB;
+constexpr int NL_SEG = 64;   // pairs a warp lists for the CTA (more: it does them itself)
 
 // Vertex q of the icosahedron: (0, +-1, +-phi) / sqrt(1 + phi^2) for q < 4 and its cyclic
 // shifts (+-1, +-phi, 0), (+-phi, 0, +-1) for q / 4 = 1, 2; bits 0 and 1 of q are the signs.
@@ -138,10 +142,76 @@ __device__ __forceinline__ void quad_point(const NlCtx<T>& c, const Pt<T>& ion, 
   }
 }
 
+// The contribution of quadrature points q0 .. q0 + NL_QB - 1 of the pair (electron i, ion
+// I), u0 = U_i at r_i: sum_l v_l(r) (2l+1) (1/12) sum_q P_l(d.u_q / r) Psi(q) / Psi, the
+// same on every lane.
+template <typename T>
+__device__ double pair_batch(const NlCtx<T>& c, const T* table, const T* Bw, int i, int I,
+                             T u0, int q0) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad, GP = p.GP, lane = c.lane;
+  const int s = i < p.n_up ? 0 : 1;
+  const T* bcol = Bw + ((size_t)s * n + (i - s * p.n_up)) * n;  // column of A^-1
+  T d[3], r;
+  disp(c, c.R[i], c.ion[I], d, r);  // r_i - R_I
+  const T rinv = T(1) / r;
+  T u[NL_QB][3];
+  Pt<T> xq[NL_QB];
+  int cell[NL_QB][3];
+  T wt[NL_QB][3][4];
+#pragma unroll
+  for (int b = 0; b < NL_QB; ++b) quad_point(c, c.ion[I], r, q0 + b, u[b], xq[b], cell[b], wt[b]);
+  // the orbitals' values at the points, dotted with the inverse's column
+  T det[NL_QB];
+#pragma unroll
+  for (int b = 0; b < NL_QB; ++b) det[b] = 0;
+  for (int j = lane; j < n; j += 32) {
+    const T bj = bcol[j];
+#pragma unroll
+    for (int b = 0; b < NL_QB; ++b) {
+      T v = 0;
+#pragma unroll 1
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+          const T* row = table + (((size_t)(cell[b][0] + a) * GP + cell[b][1] + bb) * GP +
+                                  cell[b][2]) * (size_t)n_pad + j;
+          const T wab = wt[b][0][a] * wt[b][1][bb];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v += wab * wt[b][2][e] * __ldg(row + (size_t)e * n_pad);
+        }
+      det[b] += v * bj;
+    }
+  }
+  T u1[NL_QB];
+  jastrow_sums<T, NL_QB>(c, i, xq, u1);
+  T acc0 = 0, acc1 = 0, acc2 = 0;
+#pragma unroll
+  for (int b = 0; b < NL_QB; ++b) {
+    const T dt = warp_sum(det[b]);
+    T rho;
+    if constexpr (IsMixed<T>::value) rho = dt * __expf(u0 - u1[b]);
+    else rho = dt * exp(u0 - u1[b]);
+    const T cth = (d[0] * u[b][0] + d[1] * u[b][1] + d[2] * u[b][2]) * rinv;
+    acc0 += rho;
+    acc1 += cth * rho;
+    acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
+  }
+  const double acc[3] = {(double)acc0, (double)acc1, (double)acc2};
+  const double r2 = (double)r * (double)r;
+  double e = 0.0;
+  for (int l = 0; l < p.nl_n; ++l)
+    e += p.nl_a[l] * exp(-r2 * p.nl_sinv2[l]) * (double)(2 * l + 1) * acc[l] / 12.0;
+  return e;
+}
+
+// A pair within the cutoff, listed for the CTA's warps: electron, ion, U_i at r_i.
+template <typename T> struct NlPair { int i, I; T u0; };
+
 // Shared-memory layout (byte offsets, each 16-byte aligned): electrons, ions, radial
 // coefficients, the warps' FP64 partial sums.
 struct NlLay {
-  size_t R, ion, jc, red, total;
+  size_t R, ion, jc, pairs, cnt, red, total;
 };
 
 __host__ __device__ inline size_t nl_al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -153,7 +223,9 @@ __host__ __device__ inline NlLay nl_lay(const Params& p) {
   L.R = 0;
   L.ion = nl_al16(L.R + (size_t)p.N * sizeof(Pt<T>));
   L.jc = nl_al16(L.ion + (size_t)p.n_ions * sizeof(Pt<T>));
-  L.red = nl_al16(L.jc + njc * sizeof(T));
+  L.pairs = nl_al16(L.jc + njc * sizeof(T));  // NL_SEG listed pairs per warp
+  L.cnt = nl_al16(L.pairs + (size_t)NL_NW * NL_SEG * sizeof(NlPair<T>));
+  L.red = nl_al16(L.cnt + NL_NW * sizeof(int));
   L.total = L.red + NL_NW * sizeof(double);
   return L;
 }
@@ -161,13 +233,15 @@ __host__ __device__ inline NlLay nl_lay(const Params& p) {
 template <typename T>
 __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* partial) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int w = blockIdx.x, N = p.N, NI = p.n_ions, n = p.n, n_pad = p.n_pad, GP = p.GP;
+  const int w = blockIdx.x, N = p.N, NI = p.n_ions, n = p.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.y * NL_NW + warp;  // this warp among the walker's
   const NlLay lay = nl_lay<T>(p);
   Pt<T>* R = reinterpret_cast<Pt<T>*>(smem + lay.R);
   Pt<T>* ion = reinterpret_cast<Pt<T>*>(smem + lay.ion);
   T* jc = reinterpret_cast<T*>(smem + lay.jc);
+  NlPair<T>* pairs = reinterpret_cast<NlPair<T>*>(smem + lay.pairs);
+  int* cnt = reinterpret_cast<int*>(smem + lay.cnt);
   double* red = reinterpret_cast<double*>(smem + lay.red);
   const int njc = 2 * (p.K2 + 3) + p.K1 + 3;
   const double* Rg = p.R + (size_t)w * N * 3;
@@ -185,72 +259,57 @@ __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* 
   const T* table = (const T*)p.table;
   const T* Bw = (const T*)p.binv + (size_t)w * 2 * n * n;
   double vsum = 0.0;  // lane 0 of each warp
+  // 1. each warp lists the pairs within the cutoff of its electrons (lanes over ions),
+  //    with U_i of each such electron; a warp with more than NL_SEG does the rest itself
+  int listed = 0;  // the same on every lane
   for (int i = gw; i < N; i += NL_NW * NL_SPLIT) {
-    const int s = i < p.n_up ? 0 : 1;
-    const T* bcol = Bw + ((size_t)s * n + (i - s * p.n_up)) * n;  // column of A^-1
     bool have_u0 = false;
     T u0 = 0;
-    for (int I = 0; I < NI; ++I) {
-      T d[3], r;
-      disp(c, R[i], ion[I], d, r);  // r_i - R_I
-      if (!(r < (T)p.nl_rc) || !(r > T(0))) continue;  // the same on every lane
-      if (!have_u0) {
+    for (int I0 = 0; I0 < NI; I0 += 32) {
+      const int I = I0 + lane;
+      bool in = false;
+      if (I < NI) {
+        T d[3], r;
+        disp(c, R[i], ion[I], d, r);  // r_i - R_I
+        in = r < (T)p.nl_rc && r > T(0);
+      }
+      unsigned m = __ballot_sync(0xffffffffu, in);
+      if (m && !have_u0) {
         jastrow_sums<T, 1>(c, i, &R[i], &u0);
         have_u0 = true;
       }
-      const T rinv = T(1) / r;
-      T acc0 = 0, acc1 = 0, acc2 = 0;
-      for (int q0 = 0; q0 < 12; q0 += NL_QB) {  // NL_QB points at once: independent chains
-        T u[NL_QB][3];
-        Pt<T> xq[NL_QB];
-        int cell[NL_QB][3];
-        T wt[NL_QB][3][4];
-#pragma unroll
-        for (int b = 0; b < NL_QB; ++b) quad_point(c, ion[I], r, q0 + b, u[b], xq[b], cell[b], wt[b]);
-        // the orbitals' values at the points, dotted with the inverse's column
-        T det[NL_QB];
-#pragma unroll
-        for (int b = 0; b < NL_QB; ++b) det[b] = 0;
-        for (int j = lane; j < n; j += 32) {
-          const T bj = bcol[j];
-#pragma unroll
-          for (int b = 0; b < NL_QB; ++b) {
-            T v = 0;
-#pragma unroll 1
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int bb = 0; bb < 4; ++bb) {
-                const T* row = table + (((size_t)(cell[b][0] + a) * GP + cell[b][1] + bb) * GP +
-                                        cell[b][2]) * (size_t)n_pad + j;
-                const T wab = wt[b][0][a] * wt[b][1][bb];
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                  v += wab * wt[b][2][e] * __ldg(row + (size_t)e * n_pad);
-              }
-            det[b] += v * bj;
+      while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        if (listed < NL_SEG) {
+          if (lane == 0) pairs[warp * NL_SEG + listed] = NlPair<T>{i, I0 + b, u0};
+          ++listed;
+        } else {
+          for (int qb = 0; qb < NL_NQB; ++qb) {
+            const double e = pair_batch(c, table, Bw, i, I0 + b, u0, qb * NL_QB);
+            if (lane == 0) vsum += e;
           }
         }
-        T u1[NL_QB];
-        jastrow_sums<T, NL_QB>(c, i, xq, u1);
-#pragma unroll
-        for (int b = 0; b < NL_QB; ++b) {
-          const T dt = warp_sum(det[b]);
-          T rho;
-          if constexpr (IsMixed<T>::value) rho = dt * __expf(u0 - u1[b]);
-          else rho = dt * exp(u0 - u1[b]);
-          const T cth = (d[0] * u[b][0] + d[1] * u[b][1] + d[2] * u[b][2]) * rinv;
-          acc0 += rho;
-          acc1 += cth * rho;
-          acc2 += (T(1.5) * cth * cth - T(0.5)) * rho;
-        }
-      }
-      if (lane == 0) {
-        const double acc[3] = {(double)acc0, (double)acc1, (double)acc2};
-        const double r2 = (double)r * (double)r;
-        for (int l = 0; l < p.nl_n; ++l)
-          vsum += p.nl_a[l] * exp(-r2 * p.nl_sinv2[l]) * (double)(2 * l + 1) * acc[l] / 12.0;
       }
     }
+  }
+  if (lane == 0) cnt[warp] = listed;
+  __syncthreads();
+  // 2. the listed pairs' quadrature batches, dealt to the warps in turn (in the order of
+  //    the warps' lists, so every E_L is the same from run to run)
+  int total = 0;
+#pragma unroll
+  for (int q = 0; q < NL_NW; ++q) total += cnt[q];
+  for (int k = warp; k < total * NL_NQB; k += NL_NW) {
+    int pidx = k / NL_NQB, seg = 0;
+    const int qb = k - pidx * NL_NQB;
+    while (pidx >= cnt[seg]) {
+      pidx -= cnt[seg];
+      ++seg;
+    }
+    const NlPair<T> pe = pairs[seg * NL_SEG + pidx];
+    const double e = pair_batch(c, table, Bw, pe.i, pe.I, pe.u0, qb * NL_QB);
+    if (lane == 0) vsum += e;
   }
   double v1[1] = {vsum};
   block_sum_to0<NL_NW, 1>(v1, red);
