@@ -199,8 +199,11 @@ def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0, nlpp=None, coul
 
 
 def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0, nlpp=None,
-              coulomb=None):
-    """Per-step CUDA-event timing of qmc_sweep(1) on torch's current stream."""
+              coulomb=None, energy=None):
+    """Per-step CUDA-event timing of qmc_sweep(1) on torch's current stream.  Then, outside
+    the timed region: the cost of a generation that carries the FP64 recompute (timed
+    alone, so that its share 1/n_recompute can be added to every step), and with `energy`
+    = (equilibration, generations) the E_L of an equilibrated chain of the same crowd."""
     import torch
     stream = torch.cuda.Stream()  # a real stream: torch's default is the legacy NULL stream
     torch.cuda.set_stream(stream)
@@ -213,6 +216,8 @@ def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     gens = []
+    guard = precision == "mixed"
+    rep0 = c.qmc_get_guard()[1] if guard else 0
     launches0 = c.launch_count
     for s in range(steps):
         flush_buf.add_(1.0)  # write 256 MiB on this stream: evicts the previous step from L2
@@ -222,16 +227,52 @@ def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     launches = c.launch_count - launches0
+    repairs = (c.qmc_get_guard()[1] - rep0) if guard else None
     ms = [a.elapsed_time(b) for a, b in ev]
     # steps without the FP64 recompute run exactly one launch of the fused move kernel
-    plain = [m for m, g in zip(ms, gens) if not (n_rc > 0 and (g + 1) % n_rc == 0)]
+    due = [n_rc > 0 and (g + 1) % n_rc == 0 for g in gens]
+    plain = [m for m, d in zip(ms, due) if not d]
     e = eloc[warmup:].double().cpu().numpy()
     # acceptance ratio of the chain (one more generation, after the timed region)
     c2 = c.qmc_sweep(2, None, stats=True)
     p_acc = c2.n_accept / max(1, c2.n_moves)
+    # a generation with the recompute (sweep without E_L, FP64 LU of every walker, E_L),
+    # timed alone under the same L2 flush, three times
+    rc_ms = []
+    if n_rc > 0:
+        g_next = c.generation
+        for _ in range(3):
+            c.generation = (c.generation // n_rc + 1) * n_rc - 1
+            flush_buf.add_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.qmc_sweep(1, None, stats=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rc_ms.append(a.elapsed_time(b))
+        c.generation = g_next
+    chain = None
+    if energy is not None:
+        n_eq, n_e = energy
+        c.qmc_sweep(n_eq, None, stats=False)
+        ech = torch.zeros((n_e, wl.n_walkers), dtype=torch.float64, device="cuda")
+        st = c.qmc_sweep(n_e, ech, stats=True)
+        chain = {"eloc": ech.cpu().numpy(), "repairs": getattr(st, "n_repair", 0)}
     c.close()
     torch.cuda.set_stream(torch.cuda.default_stream())
-    return {"ms": ms, "plain_ms": plain, "eloc": e, "p_acc": p_acc, "launches": launches}
+    return {"ms": ms, "plain_ms": plain, "eloc": e, "p_acc": p_acc, "launches": launches,
+            "due": due, "recompute_step_ms": rc_ms, "chain": chain, "repairs": repairs}
+
+
+def amortised(r, n_rc):
+    """Per-step times with the FP64 recompute's share: a timed step that carried no
+    recompute gets (recompute generation - plain generation) / n_recompute added; a timed
+    step that carried one keeps its own time (so no recompute is counted twice)."""
+    if n_rc <= 0 or not r["recompute_step_ms"]:
+        return list(r["ms"]), 0.0
+    plain = r["plain_ms"] or r["ms"]
+    extra = max(0.0, statistics.mean(r["recompute_step_ms"]) - statistics.mean(plain))
+    return [m if d else m + extra / n_rc for m, d in zip(r["ms"], r["due"])], extra
 
 
 def crowds_path(wl, n_crowds, update, k, steps, warmup, flush_buf, nt=0):
@@ -422,12 +463,13 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
     if ws > 1:
         e_trial, _ = population.global_estimate(float(cap), float(e_prev.sum()), cap)
     ev_s, ev_b, moves, sizes, e_est_hist = [], [], [], [], []
-    launches0 = None
+    launches0 = rep0 = None
     for g in range(warmup + steps):
         timed = g >= warmup
         if timed and launches0 is None:
             torch.cuda.synchronize()
             launches0 = c.launch_count
+            rep0 = c.qmc_get_guard()[1]
         e_new = np.zeros((1, c.W))
         if timed:
             flush_buf.add_(1.0)  # evicts the previous generation from L2
@@ -453,6 +495,7 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
             e_est_hist.append(e_est)
     torch.cuda.synchronize()
     launches = c.launch_count - launches0
+    repairs = c.qmc_get_guard()[1] - rep0
     st2 = c.qmc_sweep(1, None, stats=True)
     p_acc = st2.n_accept / max(1, st2.n_moves)
     c.close()
@@ -460,7 +503,7 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
     return {"ms": [a.elapsed_time(b) for a, b in ev_b],
             "sweep_ms": [a.elapsed_time(b) for a, b in ev_s], "moves": moves,
             "sizes": sizes, "e_est": e_est_hist, "p_acc": p_acc, "launches": launches,
-            "capacity": cap, "target": target}
+            "capacity": cap, "target": target, "repairs": repairs}
 
 
 def dmc_main(args, wl, ws, rank, cfg):
@@ -507,7 +550,9 @@ def dmc_main(args, wl, ws, rank, cfg):
                                                     zip(r["sweep_ms"], r["ms"])),
                   "walkers_min": min(r["sizes"]), "walkers_max": max(r["sizes"]),
                   "walkers_mean": statistics.mean(r["sizes"]),
-                  "e_est_mean": statistics.mean(r["e_est"]), "acceptance": r["p_acc"]}
+                  "e_est_mean": statistics.mean(r["e_est"]), "acceptance": r["p_acc"],
+                  "guard_repairs": r["repairs"],
+                  "walker_generations": int(sum(r["moves"]) / wl.n_el)}
     hbm, src = peaks()
     W_mean = statistics.mean(r["moves"]) / wl.n_el
     bpm = bytes_per_move(wl.n_orb, wl.n_el, 4, r["p_acc"], update, k)
@@ -528,11 +573,15 @@ def dmc_main(args, wl, ws, rank, cfg):
         print(json.dumps(out))
 
 
-def energy_stats(e: np.ndarray, n_blocks: int = 10):
-    blk = e.mean(axis=1)
-    nb = min(n_blocks, len(blk))
-    b = blk[: len(blk) // nb * nb].reshape(nb, -1).mean(axis=1)
-    return float(b.mean()), float(b.std(ddof=1) / math.sqrt(nb)) if nb > 1 else float("nan")
+def energy_stats(e: np.ndarray, block: int = 10):
+    """Mean of E_L [generations][walkers] and its error from blocks of `block` generations
+    (crowd averages per generation, then block means)."""
+    g = e.mean(axis=1)
+    nb = len(g) // block
+    if nb < 2:
+        return float(g.mean()), float("nan")
+    b = g[: nb * block].reshape(nb, block).mean(axis=1)
+    return float(b.mean()), float(b.std(ddof=1) / math.sqrt(nb))
 
 
 def e2e_run(wl, precision, update, k, steps, crowd_id, nt=0):
@@ -629,6 +678,12 @@ def main():
                     help="threads per walker CTA (0: tuned with --update auto, else the "
                          "library's choice)")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--equilibrate", type=int, default=100,
+                    help="untimed generations before the energy chain of each path")
+    ap.add_argument("--energy-gens", type=int, default=100,
+                    help="generations of the energy chain (0: no energy comparison)")
+    ap.add_argument("--energy-block", type=int, default=10,
+                    help="generations per block of the energy error")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dmc", action="store_true",
@@ -749,18 +804,20 @@ def main():
             args.cta_threads = tuned_nt
     barrier(ws)
     torch.cuda.synchronize()
+    energy = (args.equilibrate, args.energy_gens) if args.energy_gens > 0 else None
     with ClockSampler(uuid) as clk:
         mixed = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush,
-                          args.cta_threads)
+                          args.cta_threads, energy=energy)
         fp64 = None
         if not args.no_fp64:
             fp64 = time_path(wl, "fp64", "sm", 1, args.steps, args.warmup, rank, flush,
-                             args.cta_threads)
+                             args.cta_threads, energy=energy)
     torch.cuda.synchronize()
     barrier(ws)
 
     moves_step = wl.n_walkers * wl.n_el
-    value = aggregate_value(moves_step * args.steps, sum(mixed["ms"]) / 1000.0, ws)
+    ms_mixed, extra_mixed = amortised(mixed, wl.n_recompute)
+    value = aggregate_value(moves_step * args.steps, sum(ms_mixed) / 1000.0, ws)
     t_mixed = ws * moves_step * args.steps / value
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000.0 * t_mixed / args.steps,
@@ -773,16 +830,34 @@ def main():
     if tune_table is not None:
         out["autotune"] = {"ms_per_generation": tune_table,
                            "chosen": f"{update}:{k}:{args.cta_threads}"}
-    e_m, s_m = energy_stats(mixed["eloc"])
-    out["energy"] = {"mixed": {"mean": e_m, "sigma": s_m}}
+    out["recompute"] = {
+        "every": wl.n_recompute,
+        "recompute_ms": extra_mixed,
+        "recompute_step_ms": statistics.mean(mixed["recompute_step_ms"])
+        if mixed["recompute_step_ms"] else None,
+        "plain_step_ms": statistics.mean(mixed["plain_ms"] or mixed["ms"]),
+        "note": "recompute_ms = a generation carrying the FP64 recompute (sweep, LU of every "
+                "walker, E_L) minus a plain generation, timed alone; ms_per_step and value "
+                "include recompute_ms / every on each step that carried none"}
+    out["guard"] = {"tol": qmcgb.GUARD_TOL_DEFAULT, "repairs_in_timed_steps": mixed["repairs"],
+                    "walker_generations": wl.n_walkers * args.steps}
+    if energy is not None:
+        blk = args.energy_block
+        e_m, s_m = energy_stats(mixed["chain"]["eloc"], block=blk)
+        out["energy"] = {"equilibration_generations": args.equilibrate,
+                         "generations": args.energy_gens, "block_generations": blk,
+                         "mixed": {"mean": e_m, "sigma": s_m,
+                                   "guard_repairs": mixed["chain"]["repairs"]}}
     if fp64 is not None:
-        v64 = aggregate_value(moves_step * args.steps, sum(fp64["ms"]) / 1000.0, ws)
+        ms64, _ = amortised(fp64, wl.n_recompute)
+        v64 = aggregate_value(moves_step * args.steps, sum(ms64) / 1000.0, ws)
         t64 = ws * moves_step * args.steps / v64
-        e_d, s_d = energy_stats(fp64["eloc"])
         out["fp64"] = {"value": v64, "unit": UNIT,
                        "ms_per_step": 1000.0 * t64 / args.steps, "update": "sm"}
-        out["energy"]["fp64"] = {"mean": e_d, "sigma": s_d}
-        out["energy"]["diff_sigma"] = abs(e_m - e_d) / math.hypot(s_m, s_d)
+        if energy is not None:
+            e_d, s_d = energy_stats(fp64["chain"]["eloc"], block=args.energy_block)
+            out["energy"]["fp64"] = {"mean": e_d, "sigma": s_d}
+            out["energy"]["diff_sigma"] = abs(e_m - e_d) / math.hypot(s_m, s_d)
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["value"]
     # roofline of the dominant kernel (the fused move kernel, one launch per plain step)
     hbm, src = peaks()

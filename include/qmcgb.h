@@ -14,8 +14,9 @@
  * Wavefunction (the paper gives none; the library's reading):
  *   Psi(R) = det A_up det A_dn exp(-U),  A_s[l][j] = phi_j(r_l) (tricubic B-spline orbitals
  *   on a periodic G^3 grid), U = sum_{i<j} u2(r_ij) + sum_{i,I} u1(r_iI) (cubic B-spline
- *   radial functors, minimum image).  Moves: r' = r + tau grad log Psi + sqrt(tau) chi
- *   (or no drift), Metropolis(-Hastings) acceptance, counter-based Philox4x32-10 draws.
+ *   radial functors, minimum image).  Moves: r' = r + tau D + sqrt(tau) chi with the drift
+ *   D = grad log Psi limited near nodes (or unlimited, or none), Metropolis(-Hastings)
+ *   acceptance, counter-based Philox4x32-10 draws.
  *
  * Conventions:
  *  - Every call returns a qmc_status (QMC_OK = 0).  qmc_status_string() names it.
@@ -47,7 +48,7 @@ typedef enum qmc_status {
   QMC_ERR_CUDA = 3,        /* a CUDA runtime call failed                              */
   QMC_ERR_SINGULAR = 4,    /* zero pivot in the FP64 recompute                         */
   QMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out                            */
-  QMC_ERR_NAN = 6,         /* non-finite local energy or ratio                         */
+  QMC_ERR_NAN = 6,         /* non-finite local energy or ratio (the move is rejected)  */
   QMC_ERR_STATE = 7,       /* call out of order (accept without propose, no orbitals)  */
   QMC_ERR_UNSUPPORTED = 8  /* valid request this build does not serve (size limits)    */
 } qmc_status;
@@ -82,7 +83,11 @@ typedef struct qmc_run_desc {
                      * inverse in global memory, 8 when the inverse fits in shared       *
                      * memory: the measured optima on GB300); qmc_get_update reports it  */
   int n_recompute;  /* generations between FP64 recomputes of A^-1; 0 = never        */
-  int drift;        /* 1: drift-diffusion proposal with Metropolis-Hastings            */
+  int drift;        /* proposal r' = r + tau D + sqrt(tau) chi with Metropolis-Hastings  *
+                     * acceptance and D from F = grad log Psi: 1: D = 2 F / (1 +        *
+                     * sqrt(1 + 2 tau |F|^2)), the drift limited as in Umrigar,         *
+                     * Nightingale, Runge (1993), so tau |D| < sqrt(2 tau) near nodes;  *
+                     * 2: D = F (unlimited); 0: no drift (plain Metropolis)             */
   int potential;    /* 1: add the model potential to E_L                              */
   int staging;      /* QMC_STAGING_AUTO (0): each move's 4x4x4 x n orbital stencil is  *
                      * copied to shared memory with one TMA tensor copy when it fits;  *
@@ -99,6 +104,15 @@ typedef struct qmc_run_desc {
                      * changes the sign of the determinant is rejected) and population *
                      * branching by qmc_dmc_branch; n_walkers is then the capacity     */
   int reserved;     /* 0                                                              */
+  double guard_tol; /* mixed path: inverse guard bound (0: the library's 0.1; < 0:      *
+                     * off).  After each sweep every walker's FP32 inverses are probed   *
+                     * with a fixed sign vector v (v_l = -1 where bit 31 of             *
+                     * (l + 1) * 0x9E3779B1 mod 2^32 is set, else +1):                   *
+                     * g_s = max over k of |(v^T (A_s B_s - I))_k|; a spin whose g_s   *
+                     * exceeds guard_tol (or is not finite) has its inverse, log|det|   *
+                     * and sign recomputed in FP64 (LU with partial pivoting) before    *
+                     * the walker's E_L -- an early instance of the periodic recompute  *
+                     * (Alg. 1 line 3).  Ignored by the FP64 path.                      */
 } qmc_run_desc;
 
 /* Per-call statistics of qmc_sweep, accumulated in FP64 over walkers and generations. */
@@ -108,6 +122,7 @@ typedef struct qmc_stats {
   long long n_samples;   /* walkers x generations                                      */
   long long n_accept;    /* accepted moves                                             */
   long long n_moves;     /* proposed moves = W x N x generations                       */
+  long long n_repair;    /* walkers the guard repaired (one or both inverses recomputed) */
 } qmc_stats;
 
 typedef struct qmc_crowd qmc_crowd;
@@ -245,6 +260,28 @@ typedef struct qmc_dmc_stats {
 
 int qmc_dmc_branch(qmc_crowd* crowd, const double* e_prev, double* e_new, int mem,
                    double e_trial, qmc_dmc_stats* out);
+/* The mixed path's inverse guard (run.guard_tol): values [W] (host, may be NULL) receives
+ * max(g_up, g_dn) of every walker's last sweep (before any repair; walker slots as they
+ * were at that sweep, so a DMC branch since then reorders them), n_repair (host, may be
+ * NULL) the walkers repaired since the crowd was created.  Synchronous.  Errors: INVALID_ARG; STATE (an
+ * FP64 crowd or a crowd created with the guard off). */
+int qmc_get_guard(qmc_crowd* crowd, double* values, long long* n_repair);
+/* Records the accept decisions of qmc_sweep (on = 1) or stops recording (on = 0).  While
+ * on, every sweep generation writes walker w's decision for electron i (1 accepted, 0
+ * rejected) to entry [w][i] of a library-owned record, which qmc_get_accept_trace copies
+ * out: out uint8 [W][N] (host), the decisions of the last generation swept.  Synchronous.
+ * Errors: INVALID_ARG; OOM; STATE (qmc_get_accept_trace while not recording). */
+int qmc_trace_accepts(qmc_crowd* crowd, int on);
+int qmc_get_accept_trace(qmc_crowd* crowd, uint8_t* out);
+/* Failure-detection test hook.  Every device wait of the move kernel (a stencil copy, a
+ * tensor-core product) is bounded: after about one second the kernel records
+ * QMC_ERR_TIMEOUT, leaves the generation, and the crowd rebuilds its rows and inverses
+ * from the stored positions at the next call.  With on = 1 the kernel stops issuing its
+ * stencil copies but still waits for them, so that a test can make the wait run out with
+ * no copy in flight (the next sweep then takes about two seconds and returns
+ * QMC_ERR_TIMEOUT); on = 0 issues them again.  Needs a crowd whose stencil arrives by TMA
+ * (qmc_get_kernel_config).  Errors: INVALID_ARG (no TMA staging, on not 0 or 1). */
+int qmc_test_skip_stencil_copy(qmc_crowd* crowd, int on);
 /* Active walkers of the crowd (n_walkers unless DMC branching changed it). */
 int qmc_get_walker_count(const qmc_crowd* crowd, int* count);
 /* The crowd's update scheme and delay rank (the library's pick when run.delay_rank was 0;

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
 CPU-baseline leg use it; the product path never imports it.  The C source shares nothing
-with the CUDA path.  `build()` compiles it with gcc (-O2, OpenMP over walkers as in the
+with the CUDA path.  `build()` compiles it with gcc (-O3, OpenMP over walkers as in the
 paper's Alg. 2); the library is rebuilt when the source is newer.
 """
 from __future__ import annotations
@@ -22,7 +22,7 @@ _lib = None
 def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp,
+        subprocess.run(["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp,
                         _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB

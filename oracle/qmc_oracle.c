@@ -38,7 +38,8 @@
 /* ------------------------------------------------------------------------------------ */
 typedef struct or_system {
   int n_up, n_dn, n_orb, n_ions, grid;
-  int drift;        /* 1: r' = r + tau F + sqrt(tau) chi (Metropolis-Hastings); 0: no drift */
+  int drift;        /* r' = r + tau D(F) + sqrt(tau) chi (Metropolis-Hastings) with the     *
+                     * drift D(F) of drift_vector: 1 limited, 2 D = F; 0: no drift          */
   int potential;    /* 1: add the model potential V(R) to E_L                               */
   int update;       /* 0: Sherman-Morrison; 1: delayed rank-k (Woodbury)                    */
   int delay_rank;   /* k for update == 1                                                    */
@@ -937,8 +938,24 @@ static void walker_accept(or_crowd* c, or_walker* wk, int w, int i) {
   for (int k = 0; k < 3; ++k) R[3 * i + k] = wk->rp[k];
 }
 
+/* The drift D(F) of the proposal r' = r + tau D(F) + sqrt(tau) chi (Alg. 1 line 5, read as
+ * drift-diffusion).  drift == 1: the drift limited as in Umrigar, Nightingale and Runge
+ * (J. Chem. Phys. 99, 2865 (1993)) with a = 1, D = F (-1 + sqrt(1 + 2 tau F^2)) /
+ * (tau F^2), written as 2 F / (1 + sqrt(1 + 2 tau F^2)): D ~ F where tau F^2 is small and
+ * tau |D| < sqrt(2 tau) however large F grows near a node.  drift == 2: D = F. */
+static void drift_vector(const or_system* s, const double* F, double* D) {
+  double scale = 0.0;
+  if (s->drift == 1) {
+    double f2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    scale = 2.0 / (1.0 + sqrt(1.0 + 2.0 * s->tau * f2));
+  } else if (s->drift == 2) {
+    scale = 1.0;
+  }
+  for (int k = 0; k < 3; ++k) D[k] = scale * F[k];
+}
+
 /* Metropolis(-Hastings) test, reading: A = rho^2 G(r<-r')/G(r'<-r) with
- * G(b<-a) = exp(-|b - a - tau F(a)|^2 / (2 tau)) when drifting, A = rho^2 otherwise;
+ * G(b<-a) = exp(-|b - a - tau D(F(a))|^2 / (2 tau)) when drifting, A = rho^2 otherwise;
  * accept iff u < A (strict); rho = 0 or non-finite rejects. */
 static int metropolis(const or_system* s, const or_walker* wk, double u) {
   double rho = wk->rho;
@@ -946,9 +963,10 @@ static int metropolis(const or_system* s, const or_walker* wk, double u) {
   if (s->dmc && wk->rhoD < 0.0) return 0;  /* fixed node: no crossing of a nodal surface */
   double A;
   if (s->drift) {
-    double gb = 0.0;
+    double gb = 0.0, Dp[3];
+    drift_vector(s, wk->Fp, Dp);
     for (int k = 0; k < 3; ++k) {
-      double x = -wk->disp[k] - s->tau * wk->Fp[k];
+      double x = -wk->disp[k] - s->tau * Dp[k];
       gb += x * x;
     }
     double logGb = -gb / (2.0 * s->tau);
@@ -968,14 +986,15 @@ static int walker_sweep(or_crowd* c, int w, uint32_t gen) {
   int nacc = 0;
   double sqt = sqrt(s->tau);
   for (int i = 0; i < c->N; ++i) {
-    double chi[3], u, F[3] = {0, 0, 0};
+    double chi[3], u, F[3] = {0, 0, 0}, D[3];
     if (s->drift) walker_grad(c, wk, w, i, F);
+    drift_vector(s, F, D);
     or_move_draws(s->seed, (uint32_t)w, gen, (uint32_t)i, chi, &u);
     double rp[3], gf = 0.0;
     for (int k = 0; k < 3; ++k) {
-      wk->disp[k] = (s->drift ? s->tau * F[k] : 0.0) + sqt * chi[k];
+      wk->disp[k] = s->tau * D[k] + sqt * chi[k];
       rp[k] = R[3 * i + k] + wk->disp[k];
-      double x = wk->disp[k] - s->tau * F[k] * (s->drift ? 1.0 : 0.0);
+      double x = wk->disp[k] - s->tau * D[k];
       gf += x * x;
       wk->F[k] = F[k];
     }
@@ -1037,8 +1056,9 @@ void or_crowd_propose(or_crowd* c, int iel, const double* rnew, double* ratio, d
   for (int w = 0; w < c->W; ++w) {
     or_walker* wk = &c->wk[w];
     double* R = c->R + (size_t)w * c->N * 3;
-    double rp[3], F[3] = {0, 0, 0};
+    double rp[3], F[3] = {0, 0, 0}, D[3];
     if (s->drift) walker_grad(c, wk, w, iel, F);
+    drift_vector(s, F, D);
     if (rnew) {
       double d[3];
       min_image(rnew + 3 * w, R + 3 * iel, s->L, d);
@@ -1047,13 +1067,13 @@ void or_crowd_propose(or_crowd* c, int iel, const double* rnew, double* ratio, d
       double chi[3], u;
       or_move_draws(s->seed, (uint32_t)w, c->gen, (uint32_t)iel, chi, &u);
       for (int k = 0; k < 3; ++k) {
-        wk->disp[k] = (s->drift ? s->tau * F[k] : 0.0) + sqt * chi[k];
+        wk->disp[k] = s->tau * D[k] + sqt * chi[k];
         rp[k] = R[3 * iel + k] + wk->disp[k];
       }
     }
     double gf = 0.0;
     for (int k = 0; k < 3; ++k) {
-      double x = wk->disp[k] - (s->drift ? s->tau * F[k] : 0.0);
+      double x = wk->disp[k] - s->tau * D[k];
       gf += x * x;
       wk->F[k] = F[k];
     }

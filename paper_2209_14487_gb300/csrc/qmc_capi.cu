@@ -101,6 +101,9 @@ struct qmc_crowd {
   int eloc_cap = 0;
   unsigned long long* d_nacc = nullptr;
   int* d_status = nullptr;
+  float* d_guard = nullptr;     // [cap] inverse-guard probe of each walker's last sweep
+  unsigned long long* d_nrep = nullptr;  // [2] guard repairs: since creation, this call
+  uint8_t* d_trace = nullptr;   // [cap][N] accept decisions of the last sweep generation
   double* d_io = nullptr;       // staging for host I/O, 12 W doubles
   uint8_t* d_io8 = nullptr;     // 2 W bytes
   // host state
@@ -110,11 +113,17 @@ struct qmc_crowd {
   bool has_orbitals = false, has_positions = false, stale = true;
   uint32_t gen = 0;
   unsigned long long launches = 0;
+  int test_no_copy = 0;             // failure-detection test hook (stencil copies not issued)
   CUtensorMap tmap;  // (128-byte aligned type) the padded table as a 4-D tensor, for the stencil copy
   size_t smem = 0;               // dynamic shared memory of the move kernel
 };
 
 namespace {
+
+// Default bound of the mixed path's inverse guard, max_k |(v^T (A B - I))_k| after a
+// sweep: above the largest value of healthy walkers measured at n = 64, 256 and 768
+// (6.5e-5, 1.5e-2, 2.4e-3), below those of drifted inverses (0.19 and more).
+constexpr double kGuardTolDefault = 0.1;
 
 // The last CUDA error a call of this thread returned as QMC_ERR_CUDA.
 thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -149,7 +158,7 @@ void free_all(qmc_crowd* c) {
                   c->d_io, c->d_io8, c->d_jgl, c->d_jvalid, c->d_flush, c->d_R2,
                   c->d_rows2, c->d_binv2, c->d_jgl2, c->d_logdet2, c->d_sign2, c->d_jvalid2,
                   c->d_mult, c->d_src, c->d_bout, c->d_bsums, c->d_e, c->d_coul_m,
-                  c->d_coul_c, c->d_nlpart};
+                  c->d_coul_c, c->d_nlpart, c->d_guard, c->d_nrep, c->d_trace};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -175,6 +184,11 @@ void sync_params(qmc_crowd* c) {
   p.pend = c->d_pend;
   p.status = c->d_status;
   p.n_accept = c->d_nacc;
+  p.guard_val = c->d_guard;
+  p.n_repair = c->d_nrep;
+  p.lu_ws = c->d_ws;
+  p.accept_trace = c->d_trace;
+  p.test_no_copy = c->test_no_copy;
   p.K2 = c->K2;
   p.K1 = (c->K1 > 0 && c->sys.n_ions > 0) ? c->K1 : 0;
   p.rc2 = c->rc2;
@@ -260,6 +274,9 @@ int read_status(qmc_crowd* c) {
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st) CK(cudaMemset(c->d_status, 0, sizeof(int)));
+  // a generation cut short by a timed-out wait may have updated rows and inverses of
+  // moves whose positions it did not store: everything is rebuilt from the positions
+  if (st & qmcgb::ST_TIMEOUT) c->stale = true;
   if (st & qmcgb::ST_SINGULAR) return QMC_ERR_SINGULAR;
   if (st & qmcgb::ST_NAN) return QMC_ERR_NAN;
   if (st & qmcgb::ST_STATE) return QMC_ERR_STATE;
@@ -361,6 +378,8 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
       run->cta_threads != 256)
     return QMC_ERR_INVALID_ARG;
   if (run->engine != QMC_ENGINE_AUTO && run->engine != QMC_ENGINE_SIMT) return QMC_ERR_INVALID_ARG;
+  if (std::isnan(run->guard_tol)) return QMC_ERR_INVALID_ARG;
+  if (run->drift < 0 || run->drift > 2) return QMC_ERR_INVALID_ARG;
   if (sys->n_dn != sys->n_up) return QMC_ERR_UNSUPPORTED;
   if (sys->n_up > 1024 || sys->grid > 1024) return QMC_ERR_UNSUPPORTED;
 
@@ -391,7 +410,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.n_ions = sys->n_ions;
   p.G = sys->grid;
   p.GP = sys->grid + 3;
-  p.drift = run->drift ? 1 : 0;
+  p.drift = run->drift;
   p.dmc = run->dmc ? 1 : 0;
   p.potential = run->potential ? 1 : 0;
   p.update = run->update;
@@ -406,6 +425,10 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   p.fx_scale = 4294967296.0 / sys->L;
   p.fx_unit = sys->L / 4294967296.0;
   p.seed = run->seed;
+  // inverse guard of the mixed path: on unless guard_tol < 0
+  const bool guard = run->precision == QMC_PREC_MIXED && run->guard_tol >= 0.0;
+  p.guard_tol = guard ? (float)(run->guard_tol > 0.0 ? run->guard_tol : kGuardTolDefault) : 0.0f;
+  c->run.guard_tol = guard ? (double)p.guard_tol : -1.0;
   const int es = c->es;
 
   // Shared-memory plan, first that fits: the moving spin's inverse and the TMA-staged
@@ -509,6 +532,10 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   st |= dmalloc((void**)&c->d_ws, sizeof(double) * W * 2 * 2 * n * n);
   st |= dmalloc((void**)&c->d_nacc, sizeof(unsigned long long));
   st |= dmalloc((void**)&c->d_status, sizeof(int));
+  if (guard) {
+    st |= dmalloc((void**)&c->d_guard, sizeof(float) * W);
+    st |= dmalloc((void**)&c->d_nrep, sizeof(unsigned long long) * 2);
+  }
   st |= dmalloc((void**)&c->d_io, sizeof(double) * 12 * W);
   st |= dmalloc((void**)&c->d_io8, 2 * (size_t)W);
   if (st) {
@@ -522,6 +549,10 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   cudaMemsetAsync(c->d_pend, 0, sizeof(double) * W * qmcgb::PEND_STRIDE, c->stream);
   cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), c->stream);
   cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+  if (guard) {
+    cudaMemsetAsync(c->d_guard, 0, sizeof(float) * W, c->stream);
+    cudaMemsetAsync(c->d_nrep, 0, sizeof(unsigned long long) * 2, c->stream);
+  }
   cudaMemsetAsync(c->d_table, 0, (size_t)es * GP * GP * GP * p.n_pad, c->stream);
   cudaMemsetAsync(c->d_logdet, 0, sizeof(double) * W * 2, c->stream);
   cudaMemsetAsync(c->d_sign, 0, sizeof(int) * W * 2, c->stream);
@@ -767,6 +798,8 @@ int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) 
     c->eloc_cap = n_gen;
   }
   if (stats) CK(cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), c->stream));
+  if (stats && c->d_nrep)
+    CK(cudaMemsetAsync(c->d_nrep + 1, 0, sizeof(unsigned long long), c->stream));
   for (int g = 0; g < n_gen; ++g) {
     sync_params(c);
     Params& p = c->p;
@@ -800,8 +833,10 @@ int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) 
     std::vector<double> h((size_t)n_gen * W);
     CK(cudaMemcpyAsync(h.data(), c->d_eloc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                        c->stream));
-    unsigned long long na = 0;
+    unsigned long long na = 0, nr = 0;
     CK(cudaMemcpyAsync(&na, c->d_nacc, sizeof(na), cudaMemcpyDeviceToHost, c->stream));
+    if (c->d_nrep)
+      CK(cudaMemcpyAsync(&nr, c->d_nrep + 1, sizeof(nr), cudaMemcpyDeviceToHost, c->stream));
     st = read_status(c);
     double s1 = 0.0, s2 = 0.0;
     for (double e : h) {
@@ -813,6 +848,7 @@ int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) 
     stats->n_samples = (long long)h.size();
     stats->n_accept = (long long)na;
     stats->n_moves = (long long)n_gen * W * c->p.N;
+    stats->n_repair = (long long)nr;
     return st;
   }
   if (eloc && mem == QMC_MEM_HOST) return read_status(c);
@@ -918,6 +954,54 @@ int qmc_get_update(const qmc_crowd* c, int* update, int* delay_rank) {
   if (!c || !update || !delay_rank) return QMC_ERR_INVALID_ARG;
   *update = c->run.update;
   *delay_rank = c->run.update == QMC_UPDATE_DELAYED ? c->run.delay_rank : 1;
+  return QMC_OK;
+}
+
+int qmc_get_guard(qmc_crowd* c, double* values, long long* n_repair) {
+  if (!c) return QMC_ERR_INVALID_ARG;
+  if (!c->d_guard) return QMC_ERR_STATE;
+  const int W = c->p.W;
+  std::vector<float> h(W);
+  unsigned long long nr = 0;
+  if (values)
+    CK(cudaMemcpyAsync(h.data(), c->d_guard, sizeof(float) * W, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaMemcpyAsync(&nr, c->d_nrep, sizeof(nr), cudaMemcpyDeviceToHost, c->stream));
+  const int st = read_status(c);
+  if (values)
+    for (int w = 0; w < W; ++w) values[w] = (double)h[w];
+  if (n_repair) *n_repair = (long long)nr;
+  return st;
+}
+
+int qmc_trace_accepts(qmc_crowd* c, int on) {
+  if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
+  if (on && !c->d_trace) {
+    CK(cudaStreamSynchronize(c->stream));
+    if (dmalloc((void**)&c->d_trace, (size_t)c->run.n_walkers * c->p.N)) return QMC_ERR_OOM;
+    CK(cudaMemsetAsync(c->d_trace, 0, (size_t)c->run.n_walkers * c->p.N, c->stream));
+  } else if (!on && c->d_trace) {
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_trace);
+    c->d_trace = nullptr;
+  }
+  sync_params(c);
+  return QMC_OK;
+}
+
+int qmc_get_accept_trace(qmc_crowd* c, uint8_t* out) {
+  if (!c || !out) return QMC_ERR_INVALID_ARG;
+  if (!c->d_trace) return QMC_ERR_STATE;
+  CK(cudaMemcpyAsync(out, c->d_trace, (size_t)c->p.W * c->p.N, cudaMemcpyDeviceToHost,
+                     c->stream));
+  return read_status(c);
+}
+
+int qmc_test_skip_stencil_copy(qmc_crowd* c, int on) {
+  if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
+  if (on && !c->p.use_tma) return QMC_ERR_INVALID_ARG;
+  c->test_no_copy = on;
+  sync_params(c);
   return QMC_OK;
 }
 
@@ -1342,8 +1426,11 @@ int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* sta
     }
   };
   if (stats)
-    for (qmc_crowd* c : b->crowds)
+    for (qmc_crowd* c : b->crowds) {
       CK(cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), b->stream));
+      if (c->d_nrep)
+        CK(cudaMemsetAsync(c->d_nrep + 1, 0, sizeof(unsigned long long), b->stream));
+    }
   auto due = [&](qmc_crowd* c, int g) {
     return c->run.n_recompute > 0 && ((c->gen + (uint32_t)g + 1) % (uint32_t)c->run.n_recompute) == 0;
   };
@@ -1429,8 +1516,10 @@ int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* sta
         s1 += e;
         s2 += e * e;
       }
-      unsigned long long na = 0;
+      unsigned long long na = 0, nr = 0;
       CK(cudaMemcpy(&na, c->d_nacc, sizeof(na), cudaMemcpyDeviceToHost));
+      if (c->d_nrep) CK(cudaMemcpy(&nr, c->d_nrep + 1, sizeof(nr), cudaMemcpyDeviceToHost));
+      stats[i].n_repair = (long long)nr;
       stats[i].e_sum = s1;
       stats[i].e2_sum = s2;
       stats[i].n_samples = (long long)cnt;

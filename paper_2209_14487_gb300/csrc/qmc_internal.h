@@ -80,6 +80,14 @@ struct Params {
   void* jgl;                // [W][N][4] T: Jastrow grad U (3) and lap U of every electron
   int* jvalid;              // [W]: jgl holds the walker's current values
   double* pend;             // [W][PEND_STRIDE]
+  // inverse guard (mixed sweep): a walker whose probe of A B - I exceeds guard_tol gets
+  // its inverses recomputed by the FP64 LU before its E_L
+  float guard_tol;
+  float* guard_val;         // [W] probe value of the last sweep; null: no guard
+  unsigned long long* n_repair;  // [2]: repairs since creation, since the call began
+  double* lu_ws;            // [W][2][2 n^2] FP64 workspace of the repair's LU
+  uint8_t* accept_trace;    // [W][N]: a sweep's accept decisions (null: not recorded)
+  int test_no_copy;         // failure-detection test: stencil copies are not issued
   int iel;
   const double* rnew_in;    // [W][3] or null
   double* ratio_out;

@@ -5,6 +5,7 @@
 
 #include "qmc_device.cuh"
 #include "qmc_internal.h"
+#include "qmc_lu.cuh"
 
 namespace qmcgb {
 
@@ -63,73 +64,21 @@ template <typename T>
 __global__ void __launch_bounds__(LA_NT) recompute_kernel(const Params p, double* ws, int w0) {
   extern __shared__ __align__(16) unsigned char smem[];
   int* piv = (int*)smem;  // [n]
-  __shared__ double red_v[LA_NWARP];
-  __shared__ int red_i[LA_NWARP];
-  __shared__ int s_piv, s_sing, s_sign;
-  __shared__ double s_logabs;
+  __shared__ LuShared<LA_NT> sh;
   const int ws_id = blockIdx.x, s = ws_id & 1, w = w0 + (ws_id >> 1);
   const int n = p.n, n_pad = p.n_pad;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* LU = ws + (size_t)ws_id * 2 * n * n;
+  const int tid = threadIdx.x;
+  double* LU = ws + (size_t)(w - w0) * 4 * n * n + (size_t)s * 2 * n * n;
   double* X = LU + (size_t)n * n;
   const T* rows = (const T*)p.rows + (size_t)w * p.N * 5 * n_pad;
   for (int e = tid; e < n * n; e += LA_NT) {
     const int l = e / n, j = e - l * n;
     LU[e] = (double)rows[((size_t)(s * p.n_up + l)) * 5 * n_pad + j];
   }
-  if (tid == 0) { s_sing = 0; s_sign = 1; s_logabs = 0.0; }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + tid; i < n; i += LA_NT) {
-      const double v = fabs(LU[(size_t)i * n + k]);
-      if (v > best) { best = v; bi = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      double b = red_v[0];
-      int ib = red_i[0];
-      for (int q = 1; q < LA_NWARP; ++q)
-        if (red_v[q] > b || (red_v[q] == b && red_i[q] < ib)) { b = red_v[q]; ib = red_i[q]; }
-      piv[k] = ib;
-      s_piv = ib;
-      if (!(b > 0.0)) s_sing = 1;
-    }
-    __syncthreads();
-    if (s_sing) break;
-    const int pk = s_piv;
-    if (pk != k) {
-      for (int j = tid; j < n; j += LA_NT) {
-        const double t = LU[(size_t)k * n + j];
-        LU[(size_t)k * n + j] = LU[(size_t)pk * n + j];
-        LU[(size_t)pk * n + j] = t;
-      }
-    }
-    __syncthreads();
-    const double akk = LU[(size_t)k * n + k];
-    if (tid == 0) {
-      if (pk != k) s_sign = -s_sign;
-      if (akk < 0.0) s_sign = -s_sign;
-      s_logabs += log(fabs(akk));
-    }
-    for (int i = k + 1 + tid; i < n; i += LA_NT) LU[(size_t)i * n + k] /= akk;
-    __syncthreads();
-    const int m = n - k - 1;
-    for (int e = tid; e < m * m; e += LA_NT) {
-      const int i = k + 1 + e / m, j = k + 1 + (e - (e / m) * m);
-      LU[(size_t)i * n + j] -= LU[(size_t)i * n + k] * LU[(size_t)k * n + j];
-    }
-    __syncthreads();
-  }
-  if (s_sing) {
+  double logabs;
+  int sign;
+  if (!lu_invert_cta<LA_NT>(LU, X, n, piv, &sh, logabs, sign)) {
     if (tid == 0) {
       atomicOr(p.status, ST_SINGULAR);
       p.logdet[w * 2 + s] = -INFINITY;
@@ -137,36 +86,14 @@ __global__ void __launch_bounds__(LA_NT) recompute_kernel(const Params p, double
     }
     return;
   }
-  for (int col = tid; col < n; col += LA_NT) {
-    for (int i = 0; i < n; ++i) X[(size_t)i * n + col] = (i == col) ? 1.0 : 0.0;
-    for (int k = 0; k < n; ++k) {
-      const int pk = piv[k];
-      if (pk != k) {
-        const double t = X[(size_t)k * n + col];
-        X[(size_t)k * n + col] = X[(size_t)pk * n + col];
-        X[(size_t)pk * n + col] = t;
-      }
-    }
-    for (int i = 0; i < n; ++i) {
-      double acc = X[(size_t)i * n + col];
-      for (int j = 0; j < i; ++j) acc -= LU[(size_t)i * n + j] * X[(size_t)j * n + col];
-      X[(size_t)i * n + col] = acc;
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double acc = X[(size_t)i * n + col];
-      for (int j = i + 1; j < n; ++j) acc -= LU[(size_t)i * n + j] * X[(size_t)j * n + col];
-      X[(size_t)i * n + col] = acc / LU[(size_t)i * n + i];
-    }
-  }
-  __syncthreads();
   T* Bg = (T*)p.binv + ((size_t)w * 2 + s) * n * n;
   for (int e = tid; e < n * n; e += LA_NT) {
     const int k = e / n, i = e - k * n;  // B^T[k][i] = (A^-1)[i][k]
     Bg[e] = (T)X[(size_t)i * n + k];
   }
   if (tid == 0) {
-    p.logdet[w * 2 + s] = s_logabs;
-    p.sign[w * 2 + s] = s_sign;
+    p.logdet[w * 2 + s] = logabs;
+    p.sign[w * 2 + s] = sign;
     if (p.win_m) p.win_m[w * 2 + s] = 0;
   }
 }

@@ -29,6 +29,7 @@
 
 #include "qmc_device.cuh"
 #include "qmc_internal.h"
+#include "qmc_lu.cuh"
 
 namespace qmcgb {
 namespace QMCGB_MOVE_NS {
@@ -751,15 +752,38 @@ __device__ void eval_grad(Ctx<T>& c, int i, const T* pf, bool use_pf, T* uo, T* 
   for (int k = 0; k < 3; ++k) F[k] = v[k] - v[3 + k];
 }
 
-// The proposal r' (given, or r + tau F + sqrt(tau) chi), its spline cell and the forward
-// Green's-function exponent.
+// The drift D(F) = scale F of the proposal (Alg. 1 line 5 read as drift-diffusion): with
+// drift == 1 limited as in Umrigar, Nightingale and Runge (1993) with a = 1, scale =
+// 2 / (1 + sqrt(1 + 2 tau |F|^2)), so tau |D| < sqrt(2 tau) near a node; drift == 2: D = F;
+// drift == 0: no drift.
+// The mixed path forms it as 2 r / (1 + r) with r = 1 / sqrt(1 + 2 tau |F|^2) from the
+// approximate reciprocal square root and division (a few ulps; the forward and the
+// reverse Green's function use the same function, so the Metropolis-Hastings balance is
+// exact for it).
+template <typename T>
+__device__ __forceinline__ T drift_scale(int drift, T tau, const T* F) {
+  if (drift == 1) {
+    const T f2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    if constexpr (sizeof(T) == 4) {
+      const float r = rsqrtf(1.0f + 2.0f * tau * f2);
+      return __fdividef(2.0f * r, 1.0f + r);
+    } else {
+      return T(2) / (T(1) + sqrt(T(1) + T(2) * tau * f2));
+    }
+  }
+  return drift == 2 ? T(1) : T(0);
+}
+
+// The proposal r' (given, or r + tau D(F) + sqrt(tau) chi), its spline cell and the
+// forward Green's-function exponent.
 template <typename T>
 __device__ __forceinline__ void make_proposal(const Ctx<T>& c, int i, const T* F, const T* chi,
                                               const double* rgiven, Prop<T>& pr) {
   const Params& p = c.p;
   const T tau = c.k.tau, stau = c.k.stau;
   T gf = 0;
-  for (int k = 0; k < 3; ++k) pr.F[k] = p.drift ? F[k] : T(0);
+  const T sc = drift_scale(p.drift, tau, F);
+  for (int k = 0; k < 3; ++k) pr.F[k] = sc * F[k];
   if constexpr (IsMixed<T>::value) {
     const uint32_t* qi = c.Rq + 3 * i;
     if (!rgiven) {
@@ -841,7 +865,7 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   T cf[16];
   const bool tma = p.use_tma;
   if (tma) {
-    if (c.tid == 0) {  // the whole 4x4x4 x n_pad stencil in one copy
+    if (c.tid == 0 && !p.test_no_copy) {  // the whole 4x4x4 x n_pad stencil in one copy
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(c.bar, (uint32_t)p.stencil_bytes);
       tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
@@ -1017,25 +1041,67 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   return true;
 }
 
-// Metropolis(-Hastings): A = rho^2 G(r<-r')/G(r'<-r) with drift, rho^2 without;
-// accept iff u < A; rho = 0 or non-finite rejects, and with DMC (fixed node) so does a
-// change of the determinant's sign.
-template <typename T>
-__device__ __forceinline__ int metropolis(const Params& p, const Cst<T>& k, const Prop<T>& pr,
-                                          const Res<T>& rs, T u) {
-  const T rho = rs.rho;
-  if (!(rho != T(0)) || !isfinite(rho)) return 0;
-  if (p.dmc && rs.rhoD < T(0)) return 0;  // fixed node: no crossing of a nodal surface
-  T A;
-  if (p.drift) {
-    T gb = 0;
+// Metropolis(-Hastings): A = rho^2 G(r<-r')/G(r'<-r) with drift (G(b<-a) =
+// exp(-|b - a - tau D(F(a))|^2 / (2 tau))), rho^2 without;
+// accept iff u < A; rho = 0 or non-finite rejects (a non-finite ratio also sets the NaN
+// status), and with DMC (fixed node) so does a change of the determinant's sign.  The decision is that of FP64 arithmetic on the
+// move's ratio, displacement and drifts with the 53-bit uniform of the Philox draw
+// (walker w, electron i): the mixed path evaluates A in FP32 with the 24-bit uniform of
+// the same draw, and only where u lies within those roundings of A (about one move in
+// 10^5) does every thread take the decision again in FP64.
+// (Everything by value: taking the address of the kernel parameter block or of register
+// values would move them to local memory for the whole kernel.)
+static __device__ __noinline__ int metropolis_fp64_redo(uint64_t seed, uint32_t gen, int drift,
+                                                        double tau, float3 disp, float3 Fp,
+                                                        float rho, float logGf, int w, int i) {
+  const double u = accept_uniform(seed, (uint32_t)w, gen, (uint32_t)i);
+  double A = (double)rho * (double)rho;
+  if (drift) {
+    const double F[3] = {(double)Fp.x, (double)Fp.y, (double)Fp.z};
+    const double d[3] = {(double)disp.x, (double)disp.y, (double)disp.z};
+    const double sc = drift_scale(drift, tau, F);
+    double gb = 0.0;
     for (int q = 0; q < 3; ++q) {
-      const T x = -pr.disp[q] - k.tau * rs.Fp[q];
+      const double x = -d[q] - tau * sc * F[q];
       gb += x * x;
     }
-    A = rho * rho * exp(-gb / (T(2) * k.tau) - pr.logGf);
+    A *= exp(-gb / (2.0 * tau) - (double)logGf);
+  }
+  return u < A ? 1 : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ int metropolis(const Params& p, const Cst<T>& k, const Prop<T>& pr,
+                                          const Res<T>& rs, T u, int w, int i) {
+  const T rho = rs.rho;
+  if (!isfinite(rho)) {  // rejected, and reported as a non-finite ratio
+    if (threadIdx.x == 0) atomicOr(p.status, ST_NAN);
+    return 0;
+  }
+  if (rho == T(0)) return 0;
+  if (p.dmc && rs.rhoD < T(0)) return 0;  // fixed node: no crossing of a nodal surface
+  T A, scale = T(1);
+  if (p.drift) {
+    T gb = 0;
+    const T sc = drift_scale(p.drift, k.tau, rs.Fp);
+    for (int q = 0; q < 3; ++q) {
+      const T x = -pr.disp[q] - k.tau * sc * rs.Fp[q];
+      gb += x * x;
+    }
+    const T e1 = gb / (T(2) * k.tau);
+    A = rho * rho * exp(-e1 - pr.logGf);
+    scale += e1 + fabs(pr.logGf);
   } else {
     A = rho * rho;
+  }
+  if constexpr (IsMixed<T>::value) {
+    // |A32 - A| <= 2^-19 (1 + |exponent terms|) A, |u24 - u53| <= 2^-24
+    const float margin = 0x1p-19f * scale * A + 0x1p-23f;
+    if (!(fabsf(u - A) > margin))
+      return metropolis_fp64_redo(p.seed, p.gen, p.drift, p.tau,
+                                  make_float3(pr.disp[0], pr.disp[1], pr.disp[2]),
+                                  make_float3(rs.Fp[0], rs.Fp[1], rs.Fp[2]), rho, pr.logGf,
+                                  w, i);
   }
   return u < A ? 1 : 0;
 }
@@ -1387,7 +1453,7 @@ struct IncOut {
 // after this move (`pf`: that electron's dA entries for orbital j = tid).
 template <typename T>
 __device__ __forceinline__ void stencil_issue(Ctx<T>& c, const Prop<T>& pr) {
-  if (c.p.use_tma && c.tid == 0) {  // the whole 4x4x4 x n_pad stencil in one copy
+  if (c.p.use_tma && c.tid == 0 && !c.p.test_no_copy) {  // the whole stencil in one copy
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(c.bar, (uint32_t)c.p.stencil_bytes);
     tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
@@ -1719,6 +1785,164 @@ __device__ double local_energy_inc(Ctx<T>& c) {
   return v2[0] + v2[1];  // meaningful on thread 0
 }
 
+// ---------------------------------------------------------------------------------------
+// Inverse guard (mixed path).  After a sweep each spin's FP32 inverse B is probed with the
+// sign vector v (v_l = +-1): y = A^T v, then z_k = B^T[k] . y - v_k = (v^T (A B - I))_k,
+// a random-sign combination of column k of the residual, for every k at O(n^2) cost.
+// Double-float (Neumaier) sums keep z accurate to FP32 relative precision, so the probe
+// measures the stored inverse rather than its own rounding.  A spin whose max |z_k|
+// exceeds p.guard_tol (or is not finite) has its inverse recomputed by the FP64 LU before
+// the walker's E_L, as an early instance of the periodic recompute (Alg. 1 line 3).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool probe_negative(int l) {
+  return (((uint32_t)(l + 1) * 0x9E3779B1u) >> 31) != 0u;
+}
+
+// s + c += x with the rounding error of the addition kept in c (Neumaier).
+__device__ __forceinline__ void nsum(float& s, float& c, float x) {
+  const float t = s + x;
+  c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+  s = t;
+}
+
+__device__ __forceinline__ float nan_max(float a, float b) { return (b > a || b != b) ? b : a; }
+
+// g[s] = max_k |(v^T (A_s B_s - I))_k| for both spins; every thread receives them.  Both
+// passes serve both spins at once (one column of A, then one row of B^T, per thread), with
+// the loads of a thread issued in batches ahead of their sums.
+template <typename T>
+__device__ void inverse_probe(Ctx<T>& c, float* g) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad;
+  float* yhi = (float*)c.part;  // [2][n_pad]: y_s as an unevaluated sum hi + lo
+  float* ylo = yhi + 2 * n_pad;
+  float* red = (float*)c.red1;  // [2][NWARP]
+  constexpr int U = 8;
+  for (int t = c.tid; t < 2 * n; t += NT) {
+    const int s = t >= n ? 1 : 0, j = t - s * n;
+    const T* a = c.rows + (size_t)s * p.n_up * 5 * n_pad + j;  // A_s[l][j] at a + 5 n_pad l
+    float sm0 = 0.0f, cm0 = 0.0f, sm1 = 0.0f, cm1 = 0.0f;
+    int l = 0;
+    for (; l + U <= n; l += U) {
+      float x[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) x[q] = (float)a[(size_t)(l + q) * 5 * n_pad];
+#pragma unroll
+      for (int q = 0; q < U; q += 2) {
+        nsum(sm0, cm0, probe_negative(l + q) ? -x[q] : x[q]);
+        nsum(sm1, cm1, probe_negative(l + q + 1) ? -x[q + 1] : x[q + 1]);
+      }
+    }
+    for (; l < n; ++l) {
+      const float x = (float)a[(size_t)l * 5 * n_pad];
+      nsum(sm0, cm0, probe_negative(l) ? -x : x);
+    }
+    nsum(sm0, cm0, sm1);
+    cm0 += cm1;
+    const float hi = sm0 + cm0;
+    yhi[s * n_pad + j] = hi;
+    ylo[s * n_pad + j] = cm0 - (hi - sm0);
+  }
+  __syncthreads();
+  float worst0 = 0.0f, worst1 = 0.0f;
+  for (int t = c.tid; t < 2 * n; t += NT) {
+    const int s = t >= n ? 1 : 0, k = t - s * n;
+    const T* b = c.Bg + ((size_t)s * n + k) * n;
+    const float* yh = yhi + s * n_pad;
+    const float* yl = ylo + s * n_pad;
+    float sm[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    auto term = [&](int q, float bj, int j) {
+      const float h = yh[j], pr = bj * h;
+      const float er = fmaf(bj, h, -pr);
+      nsum(sm[q], cm[q], pr);
+      cm[q] += er + bj * yl[j];
+    };
+    int j = 0;
+    if constexpr (sizeof(T) == 4) {
+      if ((n & 3) == 0) {
+        const float4* b4 = reinterpret_cast<const float4*>(b);
+        for (; j + 4 * U <= n; j += 4 * U) {
+          float4 x[U];
+#pragma unroll
+          for (int q = 0; q < U; ++q) x[q] = b4[(j >> 2) + q];
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            term(0, x[q].x, j + 4 * q);
+            term(1, x[q].y, j + 4 * q + 1);
+            term(2, x[q].z, j + 4 * q + 2);
+            term(3, x[q].w, j + 4 * q + 3);
+          }
+        }
+      }
+    }
+    for (; j < n; ++j) term(0, (float)b[j], j);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      nsum(sm[0], cm[0], sm[q]);
+      cm[0] += cm[q];
+    }
+    nsum(sm[0], cm[0], probe_negative(k) ? 1.0f : -1.0f);
+    const float z = fabsf(sm[0] + cm[0]);
+    if (s == 0) worst0 = nan_max(worst0, z);
+    else worst1 = nan_max(worst1, z);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    worst0 = nan_max(worst0, __shfl_xor_sync(0xffffffffu, worst0, o));
+    worst1 = nan_max(worst1, __shfl_xor_sync(0xffffffffu, worst1, o));
+  }
+  if (c.lane == 0) {
+    red[c.warp] = worst0;
+    red[NWARP + c.warp] = worst1;
+  }
+  __syncthreads();
+  for (int s = 0; s < 2; ++s) {
+    float m = red[s * NWARP];
+#pragma unroll
+    for (int q = 1; q < NWARP; ++q) m = nan_max(m, red[s * NWARP + q]);
+    g[s] = m;
+  }
+  __syncthreads();  // red and the y buffers are free again
+}
+
+// FP64 recompute of spin s of this walker (the move kernel's share of the periodic
+// recompute): A_s from the current orbital rows, LU with partial pivoting in the walker's
+// slice of the workspace, B^T, log|det| and sign replaced.
+template <typename T>
+__device__ void repair_inverse(Ctx<T>& c, int s) {
+  const Params& p = c.p;
+  const int n = p.n, n_pad = p.n_pad;
+  int* piv = (int*)c.part;
+  LuShared<NT>* sh = (LuShared<NT>*)c.red0;
+  {
+    double* LU = p.lu_ws + (size_t)c.w * 4 * n * n + (size_t)s * 2 * n * n;
+    double* X = LU + (size_t)n * n;
+    const T* A = c.rows + (size_t)s * p.n_up * 5 * n_pad;
+    for (int e = c.tid; e < n * n; e += NT) {
+      const int l = e / n, j = e - l * n;
+      LU[e] = (double)A[(size_t)l * 5 * n_pad + j];
+    }
+    __syncthreads();
+    double logabs;
+    int sgn;
+    const bool ok = lu_invert_cta<NT>(LU, X, n, piv, sh, logabs, sgn);
+    if (ok) {
+      T* Bt = c.Bg + (size_t)s * n * n;
+      for (int e = c.tid; e < n * n; e += NT) {
+        const int k = e / n, i = e - k * n;  // B^T[k][i] = (A^-1)[i][k]
+        Bt[e] = (T)X[(size_t)i * n + k];
+      }
+    }
+    if (c.tid == 0) {
+      if (!ok) atomicOr(p.status, ST_SINGULAR);
+      c.sc->logdet[s] = logabs;
+      c.sc->sign[s] = sgn;
+      c.sc->lsum[s] = c.sc->lcomp[s] = 0.0f;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void prefetch_grad_rows(const Ctx<T>& c, int i, T* pf) {
   if (i < c.p.N && c.tid < c.p.n) {
@@ -1911,8 +2135,9 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
               c.failed = true;
               break;
             }
-            const int acc = metropolis(p, c.k, pr, rs, c.du[i]);
+            const int acc = metropolis(p, c.k, pr, rs, c.du[i], w, i);
             nacc += acc;
+            if (p.accept_trace && c.tid == 0) p.accept_trace[(size_t)w * N + i] = (uint8_t)acc;
             if (acc) {
               accept_inc(c, i, io);
               if (c.tid == 0)
@@ -1959,17 +2184,18 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
         }
         int acc;
         if constexpr (IsMixed<T>::value) {
-          acc = metropolis(p, c.k, pr, rs, c.du[i]);
+          acc = metropolis(p, c.k, pr, rs, c.du[i], w, i);
         } else {
           if (c.tid == 0) {
             sc->rs = rs;
-            sc->accept = metropolis(p, c.k, pr, rs, c.du[i]);
+            sc->accept = metropolis(p, c.k, pr, rs, c.du[i], w, i);
           }
           __syncthreads();
           rs = sc->rs;
           acc = sc->accept;
         }
         nacc += acc;
+        if (p.accept_trace && c.tid == 0) p.accept_trace[(size_t)w * N + i] = (uint8_t)acc;
         if (acc) accept_update(c, i, s, pp, pr, rs.rhoD);
         if (c.failed) break;  // a tensor-core flush timed out
       }
@@ -1980,6 +2206,24 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     }
     if (c.failed) return;
     moved = true;
+    if constexpr (IsMixed<T>::value) {
+      if (p.guard_val && !p.skip_eloc) {
+        float g[2];
+        inverse_probe(c, g);
+        if (c.tid == 0) p.guard_val[w] = (g[1] > g[0] || g[1] != g[1]) ? g[1] : g[0];
+        bool rep = false;
+        for (int s = 0; s < 2; ++s) {
+          if (!(g[s] <= p.guard_tol)) {  // uniform; a NaN repairs too
+            repair_inverse(c, s);
+            rep = true;
+          }
+        }
+        if (rep && c.tid == 0 && p.n_repair) {
+          atomicAdd(p.n_repair, 1ull);
+          atomicAdd(p.n_repair + 1, 1ull);
+        }
+      }
+    }
     if (!p.skip_eloc) {
       double e;
       if constexpr (IsMixed<T>::value && UPD == 0)
@@ -2081,7 +2325,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
       if (p.accept_in) acc = p.accept_in[w] != 0;
       else
         acc = metropolis(p, c.k, pr, rs,
-                         accept_uniform_t<T>(p.seed, (uint32_t)w, p.gen, (uint32_t)i));
+                         accept_uniform_t<T>(p.seed, (uint32_t)w, p.gen, (uint32_t)i), w, i);
       sc->accept = acc;
       if (p.accept_out) p.accept_out[w] = (uint8_t)acc;
       pd[P_VALID] = 0.0;

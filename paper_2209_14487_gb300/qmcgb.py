@@ -24,6 +24,7 @@ QMC_J1, QMC_J2_UU, QMC_J2_UD = 0, 1, 2
 QMC_DTYPE_F64, QMC_DTYPE_F32 = 0, 1
 QMC_STAGING_AUTO, QMC_STAGING_LDG = 0, 1
 QMC_ENGINE_AUTO, QMC_ENGINE_SIMT = 0, 1
+GUARD_TOL_DEFAULT = 0.1  # the library's inverse-guard bound (run.guard_tol = 0)
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA",
                 4: "QMC_ERR_SINGULAR", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_NAN",
                 7: "QMC_ERR_STATE", 8: "QMC_ERR_UNSUPPORTED"}
@@ -38,7 +39,8 @@ EXPORTS = [
     "qmc_crowd_restore", "qmc_status_string", "qmc_inverse_noalloc", "qmc_get_kernel_config",
     "qmc_last_cuda_error", "qmc_batch_create", "qmc_batch_destroy", "qmc_batch_sweep",
     "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count", "qmc_dmc_select",
-    "qmc_dmc_append", "qmc_load_nlpp", "qmc_load_coulomb", "qmc_get_update",
+    "qmc_dmc_append", "qmc_load_nlpp", "qmc_load_coulomb", "qmc_get_update", "qmc_get_guard",
+    "qmc_trace_accepts", "qmc_get_accept_trace", "qmc_test_skip_stencil_copy",
 ]
 
 
@@ -52,7 +54,7 @@ class qmc_run_desc(C.Structure):
                 ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("drift", C.c_int),
                 ("potential", C.c_int), ("staging", C.c_int), ("tau", C.c_double),
                 ("seed", C.c_uint64), ("cta_threads", C.c_int), ("engine", C.c_int),
-                ("dmc", C.c_int), ("reserved", C.c_int)]
+                ("dmc", C.c_int), ("reserved", C.c_int), ("guard_tol", C.c_double)]
 
 
 class qmc_dmc_stats(C.Structure):
@@ -62,7 +64,8 @@ class qmc_dmc_stats(C.Structure):
 
 class qmc_stats(C.Structure):
     _fields_ = [("e_sum", C.c_double), ("e2_sum", C.c_double), ("n_samples", C.c_longlong),
-                ("n_accept", C.c_longlong), ("n_moves", C.c_longlong)]
+                ("n_accept", C.c_longlong), ("n_moves", C.c_longlong),
+                ("n_repair", C.c_longlong)]
 
 
 class QmcError(RuntimeError):
@@ -107,6 +110,10 @@ def _load():
         "qmc_dmc_branch": [vp, vp, vp, i, C.c_double, C.POINTER(qmc_dmc_stats)],
         "qmc_get_walker_count": [vp, C.POINTER(C.c_int)],
         "qmc_get_update": [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "qmc_get_guard": [vp, vp, C.POINTER(C.c_longlong)],
+        "qmc_trace_accepts": [vp, i],
+        "qmc_get_accept_trace": [vp, vp],
+        "qmc_test_skip_stencil_copy": [vp, i],
         "qmc_dmc_select": [vp, vp, i, i],
         "qmc_dmc_append": [vp, vp, i, i],
         "qmc_load_nlpp": [vp, i, vp, vp, C.c_double],
@@ -170,18 +177,18 @@ class Crowd:
     def __init__(self, n_up, n_dn, n_orb, n_ions, grid, L, n_walkers, tau, precision="fp64",
                  update="sm", delay_rank=1, n_recompute=0, drift=True, potential=True,
                  seed=14487, stream=None, staging="auto", cta_threads=0, engine="auto",
-                 dmc=False):
+                 dmc=False, guard_tol=0.0):
         self.sys = qmc_system_desc(n_up=n_up, n_dn=n_dn, n_orb=n_orb, n_ions=n_ions, grid=grid,
                                    reserved=0, L=L)
         self.run = qmc_run_desc(
             n_walkers=n_walkers,
             precision=QMC_PREC_MIXED if precision == "mixed" else QMC_PREC_FP64,
             update=QMC_UPDATE_DELAYED if update == "delayed" else QMC_UPDATE_SM,
-            delay_rank=delay_rank, n_recompute=n_recompute, drift=int(drift),
+            delay_rank=delay_rank, n_recompute=n_recompute, drift=int(drift),  # True: limited
             potential=int(potential), staging=QMC_STAGING_LDG if staging == "ldg" else QMC_STAGING_AUTO,
             tau=tau, seed=seed, cta_threads=cta_threads,
             engine=QMC_ENGINE_SIMT if engine == "simt" else QMC_ENGINE_AUTO,
-            dmc=int(bool(dmc)), reserved=0)
+            dmc=int(bool(dmc)), reserved=0, guard_tol=float(guard_tol))
         self.W, self.N, self.n = n_walkers, n_up + n_dn, n_up
         self.capacity = n_walkers
         h = C.c_void_p()
@@ -192,14 +199,15 @@ class Crowd:
     @classmethod
     def from_workload(cls, wl, precision="fp64", update="sm", delay_rank=1, n_walkers=None,
                       stream=None, n_recompute=None, staging="auto", cta_threads=0,
-                      engine="auto", dmc=False, tau=None):
+                      engine="auto", dmc=False, tau=None, guard_tol=0.0):
         c = cls(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L,
                 wl.n_walkers if n_walkers is None else n_walkers,
                 wl.tau if tau is None else tau, precision=precision,
                 update=update, delay_rank=delay_rank,
                 n_recompute=wl.n_recompute if n_recompute is None else n_recompute,
                 drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream,
-                staging=staging, cta_threads=cta_threads, engine=engine, dmc=dmc)
+                staging=staging, cta_threads=cta_threads, engine=engine, dmc=dmc,
+                guard_tol=guard_tol)
         if wl.n_ions:
             c.qmc_load_ions(np.ascontiguousarray(wl.ions, dtype=np.float64))
         if wl.j2_uu is not None:
@@ -374,6 +382,27 @@ class Crowd:
         u, k = C.c_int(), C.c_int()
         _check("qmc_get_update", lib.qmc_get_update(self.h, C.byref(u), C.byref(k)))
         return k.value
+
+    def qmc_get_guard(self):
+        """(probe value of every walker's last sweep [W], repairs since creation)."""
+        v = np.zeros(self.W)
+        nr = C.c_longlong()
+        _check("qmc_get_guard", lib.qmc_get_guard(self.h, v.ctypes.data, C.byref(nr)))
+        return v, nr.value
+
+    def qmc_trace_accepts(self, on: bool = True):
+        _check("qmc_trace_accepts", lib.qmc_trace_accepts(self.h, int(bool(on))))
+
+    def qmc_get_accept_trace(self):
+        """Accept decisions [W][N] (uint8) of the last generation swept while recording."""
+        out = np.zeros((self.W, self.N), dtype=np.uint8)
+        _check("qmc_get_accept_trace", lib.qmc_get_accept_trace(self.h, out.ctypes.data))
+        return out
+
+    def qmc_test_skip_stencil_copy(self, on: bool):
+        """Failure-detection test hook: stencil copies not issued (their waits run out)."""
+        _check("qmc_test_skip_stencil_copy",
+               lib.qmc_test_skip_stencil_copy(self.h, int(bool(on))))
 
     @property
     def walker_count(self) -> int:

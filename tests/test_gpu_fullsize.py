@@ -21,15 +21,6 @@ def Q():
     return qmcgb
 
 
-def _resid(gpu, walkers, n):
-    out = {}
-    A = [gpu.qmc_get_slater_matrix(s) for s in range(2)]
-    B = [gpu.qmc_get_inverse(s) for s in range(2)]
-    for w in walkers:
-        out[w] = max(np.abs(B[s][w] @ A[s][w] - np.eye(n)).max() for s in range(2))
-    return out
-
-
 def test_pw512_bench_configuration(Q, oracle_lib):
     wl = wl_mod.pw512()
     gpu = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=32,
@@ -76,8 +67,9 @@ def test_mixed_size_batch_bench_configuration(Q, oracle_lib):
 
 
 def test_dmc1536_bench_configuration(Q, oracle_lib):
-    """A DMC generation and its branching at full size; E_L to 1e-3 where the walker's
-    FP32 inverse is accurate to 1e-3 (the conditioning reading), log|Psi| to 1e-4."""
+    """A DMC generation and its branching at full size; E_L to 1e-3 and log|Psi| to 1e-4
+    for every sampled walker of the new population (the inverse guard recomputes in FP64
+    any inverse that drifted during the generation, before its E_L)."""
     wl = wl_mod.dmc1536()
     gpu = Q.Crowd.from_workload(wl, precision="mixed", update="delayed", delay_rank=32,
                                 cta_threads=128, dmc=True)
@@ -88,7 +80,9 @@ def test_dmc1536_bench_configuration(Q, oracle_lib):
     e_prev = np.zeros(wl.n_walkers)
     gpu.qmc_local_energy_batch(e_prev)
     e_new = np.zeros((1, wl.n_walkers))
-    gpu.qmc_sweep(1, e_new)
+    sw = gpu.qmc_sweep(1, e_new)
+    g, n_rep = gpu.qmc_get_guard()
+    assert sw.n_repair == n_rep == int(np.sum(~(g <= 0.1)))
     st, e_next = gpu.qmc_dmc_branch(e_prev, e_new[0], float(e_prev.mean()))
     assert st.n_before == wl.n_walkers and 0 < st.n_after <= wl.n_walkers
     assert gpu.walker_count == st.n_after == len(e_next)
@@ -98,15 +92,10 @@ def test_dmc1536_bench_configuration(Q, oracle_lib):
     gpu.qmc_dmc_select(sample)
     R = gpu.qmc_get_positions()
     la, _ = gpu.qmc_get_logpsi()
-    res = _resid(gpu, range(3), wl.n_up)
     osys = oracle_lib.OracleSystem(wl)
-    good = 0
     for w in range(3):
         ref, _ = osys.logpsi(R[w])
         assert abs(la[w] - ref) < 1e-4 * max(1.0, abs(ref)), (w, la[w], ref)
-        if res[w] <= 1e-3:
-            good += 1
-            e_ref = osys.local_energy(R[w])[0]
-            e_gpu = e_next[sample[w]]
-            assert abs(e_gpu - e_ref) < 1e-3 * abs(e_ref), (w, e_gpu, e_ref)
-    assert good >= 1, res
+        e_ref = osys.local_energy(R[w])[0]
+        e_gpu = e_next[sample[w]]
+        assert abs(e_gpu - e_ref) < 1e-3 * abs(e_ref), (w, e_gpu, e_ref)

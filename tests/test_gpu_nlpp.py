@@ -97,3 +97,29 @@ def test_nlpp_arguments_and_batches(Q):
     c2 = Q.Crowd.from_workload(wl, precision="mixed")
     with pytest.raises(Q.QmcError):
         Q.Batch([c, c2])
+
+
+def test_nlpp_pair_list_overflow_matches_oracle(Q, oracle_lib):
+    """A warp lists at most 64 (electron, ion) pairs within the cutoff for the CTA and
+    evaluates the rest itself: 96 electrons (three per warp of the walker's 32), 64 ions and
+    a cutoff of 0.45 L give some warps more than 64 pairs; E_L still equals the oracle's to
+    1e-10 in FP64."""
+    wl = wl_mod.make_workload("nl96", n_el=96, n_orb=48, grid=20, n_walkers=4, n_gen=1,
+                              n_ions=64, tau=0.3, j1_knots=6, j2_knots=8)
+    rc = 0.45 * wl.L
+    R = np.ascontiguousarray(wl.positions())
+    # pairs per warp (warp g takes electrons g, g + 32, g + 64), counted on the host
+    d = R[:, :, None, :] - wl.ions[None, None, :, :]
+    d -= wl.L * np.round(d / wl.L)
+    within = (np.sqrt((d * d).sum(-1)) < rc).sum(-1)          # [W][N]
+    per_warp = np.stack([within[:, g::32].sum(-1) for g in range(32)], axis=1)
+    assert per_warp.max() > 64, per_warp.max()
+    gpu = Q.Crowd.from_workload(wl, precision="fp64")
+    gpu.qmc_load_nlpp(AMPS, WIDTHS, rc)
+    gpu.qmc_load_positions(R)
+    gpu.qmc_recompute()
+    e = np.zeros(wl.n_walkers)
+    gpu.qmc_local_energy_batch(e)
+    osys = oracle_lib.OracleSystem(wl, nlpp=(AMPS, WIDTHS, rc))
+    ref = np.array([osys.local_energy(R[w])[0] for w in range(wl.n_walkers)])
+    assert np.allclose(e, ref, rtol=1e-10, atol=1e-10), np.abs(e - ref).max()

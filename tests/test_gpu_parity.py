@@ -331,14 +331,23 @@ def test_pw512_inverse_in_global_memory(Q, oracle_lib, precision, nt):
     wl = wl_mod.pw512()
     W = 3
     gpu, orc, osys, R = _pair(Q, oracle_lib, wl, precision=precision, W=W, nt=nt)
+    osys_abs = oracle_lib.OracleSystem(wl, table=np.abs(wl.table()))
     rng = np.random.default_rng(12)
+    n, eps32 = wl.n_up, 2.0 ** -24
     for iel in [0, 255, 256, 511, 17]:
         rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.4, size=(W, 3)), wl.L)
         lr, grad = np.zeros(W), np.zeros((W, 3))
         gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, grad, lr)
         _, o_grad, o_lr, _ = orc.propose(iel, rnew)
-        tol = 1e-10 if precision == "fp64" else 2e-4
-        assert np.all(np.abs(lr - o_lr) <= tol * np.maximum(1.0, np.abs(o_lr))), (lr, o_lr)
+        if precision == "fp64":
+            assert np.all(np.abs(lr - o_lr) <= 1e-10 * np.maximum(1.0, np.abs(o_lr))), (lr, o_lr)
+        else:  # the mixed path's bound: 1e-5, or 8 eps32 times the ratio's condition number
+            s = 0 if iel < n else 1
+            for w in range(W):
+                kap = _ratio_sensitivity(osys_abs, R[w], s * n, orc, w, s, iel - s * n,
+                                         rnew[w], n)
+                bound = max(1e-5 * max(1.0, abs(o_lr[w])), 8 * eps32 * kap)
+                assert abs(lr[w] - o_lr[w]) <= bound, (iel, w, lr[w], o_lr[w], kap)
         acc = np.array([1, 0, 1], dtype=np.uint8)
         gpu.qmc_accept_reject_batch(iel, acc)
         orc.accept(iel, acc)
@@ -468,13 +477,19 @@ def test_pw512_tensor_flush_fine_grained_and_rank_64(Q, oracle_lib, k):
                               nt=128)
     cfg = gpu.kernel_config
     assert cfg["tc_flush"] == 1 and cfg["stencil_tma"] == 1, cfg
+    osys_abs = oracle_lib.OracleSystem(wl, table=np.abs(wl.table()))
     rng = np.random.default_rng(21)
+    n, eps32 = wl.n_up, 2.0 ** -24
     for iel in [0, 9, 255, 300, 17, 511, 256, 40, 77, 300]:
         rnew = np.mod(R[:, iel, :] + rng.normal(0, 0.3, size=(W, 3)), wl.L)
         lr = np.zeros(W)
         gpu.qmc_propose_move_batch(iel, np.ascontiguousarray(rnew), None, None, lr)
         _, _, o_lr, _ = orc.propose(iel, rnew)
-        assert np.all(np.abs(lr - o_lr) <= 2e-4 * np.maximum(1.0, np.abs(o_lr))), (iel, lr, o_lr)
+        s = 0 if iel < n else 1
+        for w in range(W):
+            kap = _ratio_sensitivity(osys_abs, R[w], s * n, orc, w, s, iel - s * n, rnew[w], n)
+            bound = max(1e-5 * max(1.0, abs(o_lr[w])), 8 * eps32 * kap)
+            assert abs(lr[w] - o_lr[w]) <= bound, (iel, w, lr[w], o_lr[w], kap)
         acc = np.ones(W, dtype=np.uint8)
         gpu.qmc_accept_reject_batch(iel, acc)
         orc.accept(iel, acc)
@@ -499,9 +514,11 @@ def test_dmc1536_mixed_sampled(Q, oracle_lib, update, k):
     four and Jastrow partners beyond its cached slots.  Proposals meet the mixed-path bound
     against the oracle; after a fixed-node generation log|Psi| agrees with the oracle's FP64
     recompute at the GPU's positions (a repeated accept included), no walker changed its
-    sign, E_L agrees to 1e-3 for every walker whose FP32 inverse is accurate to 1e-3
-    (max|A^-1 A - I|; an ill-conditioned walker's FP32 inverse is not), and after the GPU's
-    own FP64 recompute every walker's E_L agrees to 1e-5."""
+    sign, and every walker's E_L agrees with the oracle to 1e-3: walker 1 starts at a
+    configuration where cond(A_up) ~ 4e7, its FP32 inverse drifts during the generation
+    (the probe g reaches ~0.08 with Sherman-Morrison, several units with the delayed
+    update), and the inverse guard recomputes it in FP64 before its E_L where g > 0.1.  After the GPU's own FP64 recompute every
+    walker's E_L agrees to 1e-5."""
     wl = _dmc1536()
     W = 2
     R = np.ascontiguousarray(wl.positions(n_walkers=W))
@@ -535,23 +552,18 @@ def test_dmc1536_mixed_sampled(Q, oracle_lib, update, k):
     e = np.zeros((1, W))
     st = gpu.qmc_sweep(1, e)
     assert 0.5 < st.n_accept / st.n_moves <= 1.0  # tau = 0.01: almost every move accepted
+    g, _ = gpu.qmc_get_guard()
+    assert st.n_repair == int(np.sum(~(g <= 0.1))), (st.n_repair, g)
     Rg = gpu.qmc_get_positions()
     la, sg = gpu.qmc_get_logpsi()
     assert np.array_equal(sg, sign0)  # fixed node
-    resid = np.zeros(W)
-    for s in range(2):
-        A, B = gpu.qmc_get_slater_matrix(s), gpu.qmc_get_inverse(s)
-        for w in range(W):
-            resid[w] = max(resid[w], np.abs(B[w] @ A[w] - np.eye(n)).max())
     e_ref = np.zeros(W)
     for w in range(W):
         ref, rs = osys.logpsi(Rg[w])
         assert abs(la[w] - ref) < 1e-4 * max(1, abs(ref)), (w, la[w], ref)
         assert sg[w] == rs
         e_ref[w] = osys.local_energy(Rg[w])[0]
-    good = resid <= 1e-3
-    assert good.any(), resid
-    assert np.all(np.abs(e[0] - e_ref)[good] < 1e-3 * np.abs(e_ref)[good]), (e[0], e_ref, resid)
+    assert np.all(np.abs(e[0] - e_ref) < 1e-3 * np.abs(e_ref)), (e[0], e_ref, g)
     gpu.qmc_recompute()
     e2 = np.zeros(W)
     gpu.qmc_local_energy_batch(e2)

@@ -63,3 +63,30 @@ def test_inverse_noalloc_limits_and_singular():
     with pytest.raises(qmcgb.QmcError) as ei:
         qmcgb.qmc_inverse_noalloc(big, torch.empty_like(big), ld[:1], sg[:1])
     assert ei.value.status == 8
+
+
+def test_inverse_noalloc_several_launches():
+    """A batch larger than the static workspace holds (2^21 doubles: 8 matrices of 512 x 512)
+    runs as several launches in stream order on the reused workspace: 9 matrices, two
+    launches, each inverse, log|det| and sign against numpy."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_14487_gb300 import qmcgb
+    n, batch = 512, 9
+    rng = np.random.default_rng(7)
+    A = rng.normal(size=(batch, n, n)) + 4.0 * np.sqrt(n) * np.eye(n) * rng.choice([-1.0, 1.0],
+                                                                               size=(batch, 1, 1))
+    a = torch.from_numpy(A).cuda()
+    inv = torch.empty_like(a)
+    ld = torch.empty(batch, dtype=torch.float64, device="cuda")
+    sg = torch.empty(batch, dtype=torch.int32, device="cuda")
+    for _ in range(2):   # two calls in a row on the shared workspace
+        qmcgb.qmc_inverse_noalloc(a, inv, ld, sg)
+        torch.cuda.synchronize()
+        got = inv.cpu().numpy()
+        ref = np.linalg.inv(A)
+        assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+        s_ref, l_ref = np.linalg.slogdet(A)
+        assert np.allclose(ld.cpu().numpy(), l_ref, rtol=1e-12, atol=1e-9)
+        assert np.array_equal(sg.cpu().numpy(), s_ref.astype(np.int32))
