@@ -70,3 +70,27 @@ def test_concurrent_crowds_match_sequential(Q):
         assert np.array_equal(a, b)
     for a, b in zip(seq[2], con[2]):
         assert np.array_equal(a, b)
+
+
+def test_concurrent_fp64_crowds_follow_oracle(Q, oracle_lib):
+    """Four FP64 crowds (different starting walkers) swept concurrently from host threads,
+    each on its own stream, next to a mixed crowd sharing the GPU: every FP64 crowd's
+    trajectory and E_L equal those of an oracle crowd with the same walkers and RNG streams
+    (a decision can flip only where u lies within rounding of the acceptance: at most one
+    walker per crowd), as in the single-crowd trajectory test."""
+    # without drift the trajectories depend on the decisions only, not on the rounding of
+    # the drift (which a few hundred dependent moves can amplify past 1e-9)
+    wl = dataclasses.replace(wl_mod.pw128(), n_walkers=8, n_recompute=0, drift=False)
+    n_gen = 2
+    specs = [(wl, "fp64", "sm", 1)] * 4 + [(dataclasses.replace(wl, n_walkers=64), "mixed",
+                                            "sm", 1)]
+    out, R, _ = _run(Q, specs, concurrent=True, n_gen=n_gen)
+    osys = oracle_lib.OracleSystem(wl)
+    for i in range(4):
+        orc = oracle_lib.OracleCrowd(osys, np.ascontiguousarray(wl.positions(crowd_id=i)))
+        e_or, _ = orc.sweep(n_gen)
+        d = np.abs(R[i] - orc.positions())
+        same = np.all(np.minimum(d, wl.L - d) < 1e-9, axis=(1, 2))
+        assert same.sum() >= wl.n_walkers - 1, (i, same)
+        rel = np.abs(out[i][:, same] - e_or[:, same]) / np.abs(e_or[:, same])
+        assert np.all(rel < 1e-9), (i, rel.max())
