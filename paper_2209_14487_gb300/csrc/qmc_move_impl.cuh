@@ -504,6 +504,125 @@ __device__ __forceinline__ void tc_release(Ctx<T>& c) {
   if (c.warp == 0) tmem_dealloc(c.sc->tmem, TC_COLS);
 }
 
+// One row tile of the flush for a window of mp <= 32 columns, the X accumulator of rows
+// r0..r0+127 in TMEM columns 0..mp-1: Y = (X - P) S^-T by the warps of the four lane
+// quadrants, one row per thread, written as the update's A operand (hi/lo, K = mp); then
+// B^T[r0..][j0..] -= Y snap[.][j0..] for every 128-column tile j0 (K = mp in one chunk),
+// snap's rows j read as float4 runs of the [n][mp] snapshot, the tile's B^T loaded before
+// the MMAs and read-modify-written after them.  False (TMEM released) if a wait ran out.
+template <typename T>
+__device__ bool flush_tile_update_tc(Ctx<T>& c, int r0, uint32_t tm, uint32_t lane_base,
+                                     uint32_t id2, const float* snapt) {
+  const Params& p = c.p;
+  const int m = c.sc->m, n = p.n, bs = c.bs;
+  const int mp = (m + 15) & ~15;
+  float* st = c.tcs;
+  float* ahi = st;
+  float* alo = st + TC_TILE * TC_KC;
+  float* bhi = st + 2 * TC_TILE * TC_KC;
+  float* blo = st + 3 * TC_TILE * TC_KC;
+  if (c.warp < 4) {
+    // 16 columns of Y at a time from 16 columns of X at a time (registers stay few: the
+    // flush runs inside the move loop)
+    const int rr = c.warp * 32 + c.lane, r = r0 + rr;
+    for (int bh = 0; bh < mp; bh += 16) {
+      float y[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) y[q] = 0.f;
+      for (int lc = 0; lc < mp; lc += 16) {
+        float x[16];
+        tmem_ld16(tm + lane_base + (uint32_t)lc, x);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int l = lc + q;
+          x[q] = (l < m && r < n) ? x[q] - ((r == c.wP[l]) ? 1.f : 0.f) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          if (bh + b < m) {
+            const float* srow = c.wS + (size_t)(bh + b) * p.ks + lc;
+            float acc = y[b];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (lc + q < m) acc += x[q] * srow[q];
+            y[b] = acc;
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int e = ((rr >> 3) << 6) | (((bh >> 2) + g) << 3) | (rr & 7);
+        tc_store_split(ahi, alo, e, make_float4(y[4 * g], y[4 * g + 1], y[4 * g + 2], y[4 * g + 3]));
+      }
+    }
+  }
+  tc_fence_before_sync();  // X is read from TMEM before the update's MMAs overwrite it
+  constexpr int EP_STEP = (NWARP / 4) * 16;
+  constexpr int EP_IT = TC_TILE / EP_STEP;
+  constexpr int EP_PF = NT >= 256 ? EP_IT / 2 : EP_IT;
+  const int r = r0 + (c.warp & 3) * 32 + c.lane;
+  for (int j0 = 0; j0 < n; j0 += TC_TILE) {
+    const int jb = j0 + (c.warp >> 2) * 16;
+    float4 bt[EP_PF][4];
+#pragma unroll
+    for (int it = 0; it < EP_PF; ++it) {
+      const int j = jb + it * EP_STEP;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)  // n % 4 == 0: whole float4 groups in or out
+        bt[it][q] = (r < n && j + 4 * q < n)
+                        ? __ldcg(reinterpret_cast<const float4*>(c.B + (size_t)r * bs + j) + q)
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // snap as the B operand: rows j, K = b; all of this thread's runs loaded first
+    float4 z[TC_PER_T];
+#pragma unroll
+    for (int q = 0; q < TC_PER_T; ++q) {
+      int rr, b;
+      tc_slot(c.tid + q * NT, rr, b);
+      const int j = j0 + rr;
+      z[q] = (j < n && b < mp)
+                 ? __ldcg(reinterpret_cast<const float4*>(snapt + (size_t)j * mp + b))
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < TC_PER_T; ++q) {
+      int rr, b;
+      tc_slot(c.tid + q * NT, rr, b);
+      if (b < mp) tc_store_split(bhi, blo, c.tid + q * NT, z[q]);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (c.tid == 0) tc_issue_chunk(st, tm, id2, mp / 8, true, c.bar + 1);
+    if (!tc_wait(c)) {
+      tc_release(c);
+      return false;
+    }
+    tc_fence_after_sync();
+#pragma unroll
+    for (int it = 0; it < EP_IT; ++it) {
+      const int c0 = (c.warp >> 2) * 16 + it * EP_STEP;
+      float d[16];
+      tmem_ld16(tm + lane_base + (uint32_t)c0, d);
+      const int j = j0 + c0;
+      float4* brow = reinterpret_cast<float4*>(c.B + (size_t)r * bs + j);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (r < n && j + 4 * q < n) {
+          float4 bv = it < EP_PF ? bt[it < EP_PF ? it : 0][q] : __ldcg(brow + q);
+          bv.x -= d[4 * q];
+          bv.y -= d[4 * q + 1];
+          bv.z -= d[4 * q + 2];
+          bv.w -= d[4 * q + 3];
+          brow[q] = bv;
+        }
+      }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+  }
+  return true;
+}
+
 // The window's rows of B^T before the update (snap), X^T and Y^T live in the walker's
 // global scratch [3][k][n] (L2-resident), which keeps the flush's shared memory to the
 // operand stages: delay ranks up to 64 fit next to the staged stencil.
@@ -519,11 +638,25 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     float* snapg = scr;                      // [m][n]: B^T[p_b][j]
     float* xt = scr + (size_t)p.k * n;       // [m][n]: X^T[l][r]
     float* yt = scr + (size_t)2 * p.k * n;   // [m][n]: Y^T[b][r]
+    // Row tiles one at a time when the window has at most 32 columns (and the scratch holds
+    // the snapshot as [n][mp]): Y's rows depend on X's same rows only, so each tile goes
+    // X -> Y (from TMEM into registers, S^-1 from shared memory) -> B^T -= Y snap while
+    // its rows of B^T are still in L2
+    const bool fused = mp <= TC_KC && mp <= 3 * p.k;
     if (c.warp == 0) tmem_alloc(&c.sc->tmem, TC_COLS);
-    // snapshot of the window's rows of B^T before the update
-    for (int e = c.tid; e < m * n; e += NT) {
-      const int l = e / n, j = e - l * n;
-      snapg[e] = c.B[(size_t)c.wP[l] * bs + j];
+    // snapshot of the window's rows of B^T before the update ([m][n], or [n][mp] with the
+    // columns m..mp-1 zero when fused, so that a row of the update's B operand is one
+    // contiguous run)
+    if (fused) {
+      for (int e = c.tid; e < mp * n; e += NT) {
+        const int l = e / n, j = e - l * n;
+        snapg[(size_t)j * mp + l] = l < m ? c.B[(size_t)c.wP[l] * bs + j] : 0.f;
+      }
+    } else {
+      for (int e = c.tid; e < m * n; e += NT) {
+        const int l = e / n, j = e - l * n;
+        snapg[e] = c.B[(size_t)c.wP[l] * bs + j];
+      }
     }
     tc_fence_before_sync();
     __syncthreads();
@@ -538,6 +671,7 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     // ---- X = B^T Phi^T - P (per 128-row tile, K = n in chunks of 32; the B^T chunks are
     // loaded two ahead, so two of them are in flight while a chunk's MMAs run)
     const uint32_t id1 = tc_idesc_tf32((uint32_t)mp);
+    const uint32_t id2 = tc_idesc_tf32((uint32_t)TC_TILE);
     for (int r0 = 0; r0 < n; r0 += TC_TILE) {
       // stages chunk k0 from v, issues its MMAs, reloads v with chunk k0 + 2 TC_KC, waits
       auto x_chunk = [&](int k0, float4 (&v)[TC_PER_T]) -> bool {
@@ -576,6 +710,10 @@ __device__ void flush_window_tc(Ctx<T>& c) {
         return;
       }
       tc_fence_after_sync();
+      if (fused) {
+        if (!flush_tile_update_tc(c, r0, tm, lane_base, id2, snapg)) return;
+        continue;
+      }
       // epilogue: row r of the tile is TMEM lane r; warps of one lane quadrant split columns
       const int r = r0 + (c.warp & 3) * 32 + c.lane;
       for (int c0 = (c.warp >> 2) * 16; c0 < mp; c0 += (NWARP / 4) * 16) {
@@ -592,6 +730,12 @@ __device__ void flush_window_tc(Ctx<T>& c) {
       tc_fence_before_sync();
       __syncthreads();
     }
+    if (fused) {
+      tc_release(c);
+      if (c.tid == 0) c.sc->m = 0;
+      __syncthreads();
+      return;
+    }
     // ---- Y = X S^-T (m x m on the CUDA cores; X^T rows from the L2-resident scratch)
     for (int e = c.tid; e < n * m; e += NT) {
       const int b = e / n, r = e - b * n;
@@ -602,7 +746,6 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     }
     __syncthreads();
     // ---- B^T -= Y snap (per 128 x 128 output tile, K = mp in chunks of 32)
-    const uint32_t id2 = tc_idesc_tf32((uint32_t)TC_TILE);
     // epilogue geometry: row r of the tile is TMEM lane r; the warps of one lane quadrant
     // split the columns into EP_IT groups of 16 per thread
     constexpr int EP_STEP = (NWARP / 4) * 16;
