@@ -641,8 +641,10 @@ __device__ void flush_window_tc(Ctx<T>& c) {
     // Row tiles one at a time when the window has at most 32 columns (and the scratch holds
     // the snapshot as [n][mp]): Y's rows depend on X's same rows only, so each tile goes
     // X -> Y (from TMEM into registers, S^-1 from shared memory) -> B^T -= Y snap while
-    // its rows of B^T are still in L2
-    const bool fused = mp <= TC_KC && mp <= 3 * p.k;
+    // its rows of B^T are still in L2.  Only for n >= 512: a smaller inverse stays in L2
+    // between the passes anyway, and there the three-pass order measured faster (pw512,
+    // n = 256: 42.2 against 43.7 ms per generation)
+    const bool fused = mp <= TC_KC && mp <= 3 * p.k && n >= 512;
     if (c.warp == 0) tmem_alloc(&c.sc->tmem, TC_COLS);
     // snapshot of the window's rows of B^T before the update ([m][n], or [n][mp] with the
     // columns m..mp-1 zero when fused, so that a row of the update's B operand is one
