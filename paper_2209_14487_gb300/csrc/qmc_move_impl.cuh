@@ -98,7 +98,8 @@ __device__ __forceinline__ Cst<T> make_cst(const Params& p) {
 }
 
 struct Lay {
-  size_t scal, bar, stc, tcs, B, R, Rq, ion, ionq, jc, jgl, phi, part, col, dchi, du, red0, red1;
+  size_t scal, bar, stc, tcs, B, R, Rq, ion, ionq, jc, jgl, phi, part, col, col2, dchi, du, red0,
+      red1;
   size_t wP, wV, wS, wy, wz, wc, wb, snap, xb, yb, total;
 };
 
@@ -141,6 +142,7 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.phi = o; o += al16((size_t)5 * p.n_pad * es);
   L.part = o; o += al16((size_t)16 * p.n_pad * es);
   L.col = o; o += al16((size_t)p.n_pad * es);
+  L.col2 = o; o += p.inc_jastrow ? al16((size_t)p.n_pad * es) : 0;  // the next move's column
   if (over_move) L.tcs = L.phi;
   L.dchi = o; o += al16((size_t)p.N * 3 * es);
   L.du = o; o += al16((size_t)p.N * es);
@@ -192,6 +194,7 @@ struct Ctx {
   T* phi;
   T* part;
   T* col;
+  T* col2;  // incremental sweep: the next move's column, written by the update's row owners
   T* dchi;
   T* du;
   T* red0;
@@ -1782,7 +1785,8 @@ __device__ bool spo_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& rs,
 // n <= NT / 2) with the new rows of A written to HBM and log|det| advanced; no barrier
 // (the caller's publishes it).  The caller has already moved the electron.
 template <typename T>
-__device__ __forceinline__ void sm_rows_update(Ctx<T>& c, int i, int s, int pp, T rhoD) {
+__device__ __forceinline__ void sm_rows_update(Ctx<T>& c, int i, int s, int pp, T rhoD,
+                                               T* cnext) {
   const Params& p = c.p;
   const int n = p.n, n_pad = p.n_pad, bs = c.bs;
   if constexpr (sizeof(T) == 4) {
@@ -1815,6 +1819,7 @@ __device__ __forceinline__ void sm_rows_update(Ctx<T>& c, int i, int s, int pp, 
         b.z -= cv.z * f;
         b.w -= cv.w * f;
         r4[q] = b;
+        if (cnext && k == pp + 1) reinterpret_cast<float4*>(cnext + qd * nq)[q] = b;
       }
     }
     T* rw = c.rows + (size_t)i * 5 * n_pad;
@@ -2147,6 +2152,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
   c.phi = (T*)(smem + lay.phi);
   c.part = (T*)(smem + lay.part);
   c.col = (T*)(smem + lay.col);
+  c.col2 = (T*)(smem + lay.col2);
   c.dchi = (T*)(smem + lay.dchi);
   c.du = (T*)(smem + lay.du);
   c.red0 = (T*)(smem + lay.red0);
@@ -2305,9 +2311,21 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
               stencil_issue(c, pr);
               jas_inc(c, i1, pr, jv, io);
             }
-            if (acc) sm_rows_update(c, i, s, pp, rhoD);
-            __syncthreads();  // the updated inverse is visible
-            if (more) compute_column(c, pp + 1);
+            // the next move's column is row pp + 1 of the updated inverse: its row owners
+            // write it to col2 as they update it (or it is copied when nothing changes), so
+            // the next move needs no column pass and no barrier of its own here; the barrier
+            // inside its ratio (before the column and the updated rows are read) orders it
+            if (acc) {
+              sm_rows_update(c, i, s, pp, rhoD, more ? c.col2 : nullptr);
+            } else if (more) {
+              const T* bn = c.B + (size_t)(pp + 1) * c.bs;
+              for (int j = c.tid; j < n; j += NT) c.col2[j] = bn[j];
+            }
+            if (more) {
+              T* t = c.col;
+              c.col = c.col2;
+              c.col2 = t;
+            }
           }
           if (c.failed) break;
           end_spin(c, s, true);
