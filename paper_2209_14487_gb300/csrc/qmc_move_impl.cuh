@@ -560,21 +560,27 @@ __device__ bool flush_tile_update_tc(Ctx<T>& c, int r0, uint32_t tm, uint32_t la
     }
   }
   tc_fence_before_sync();  // X is read from TMEM before the update's MMAs overwrite it
-  constexpr int EP_STEP = (NWARP / 4) * 16;
-  constexpr int EP_IT = TC_TILE / EP_STEP;
-  constexpr int EP_PF = NT >= 256 ? EP_IT / 2 : EP_IT;
-  const int r = r0 + (c.warp & 3) * 32 + c.lane;
+  // The tile of B^T moves through shared memory in two halves of 64 columns (the B operand's
+  // stage, free once the MMAs are done), so that its global reads and writes are coalesced
+  // (a warp takes two whole 256-byte row pieces) while each thread still handles one row
+  // against its TMEM lane; float4 slot c of row r sits at c ^ (r & 15) (no bank conflicts)
+  constexpr int HALF_F4 = TC_TILE * 16;        // float4 of a 128 x 64 half tile
+  constexpr int PER_T = 2 * HALF_F4 / NT;      // both halves' float4 per thread
+  float4* buf = reinterpret_cast<float4*>(bhi);  // bhi, blo: 32 KB, contiguous
+  const int rq = (c.warp & 3) * 32 + c.lane;   // this thread's row of the tile (TMEM lane)
+  const int cg = c.warp >> 2;                  // its group of columns
+  constexpr int NG = NWARP / 4;                // groups: 64 / NG columns of a half each
   for (int j0 = 0; j0 < n; j0 += TC_TILE) {
-    const int jb = j0 + (c.warp >> 2) * 16;
-    float4 bt[EP_PF][4];
+    float4 pre[PER_T];  // the tile, loaded before the MMAs (coalesced)
 #pragma unroll
-    for (int it = 0; it < EP_PF; ++it) {
-      const int j = jb + it * EP_STEP;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)  // n % 4 == 0: whole float4 groups in or out
-        bt[it][q] = (r < n && j + 4 * q < n)
-                        ? __ldcg(reinterpret_cast<const float4*>(c.B + (size_t)r * bs + j) + q)
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < PER_T; ++q) {
+      const int idx = c.tid + q * NT;
+      const int h = idx / HALF_F4, e = idx - h * HALF_F4;
+      const int row = e >> 4, c4 = e & 15;
+      const int r = r0 + row, j = j0 + 64 * h + 4 * c4;
+      pre[q] = (r < n && j < n)
+                   ? __ldcg(reinterpret_cast<const float4*>(c.B + (size_t)r * bs + j))
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // snap as the B operand: rows j, K = b; all of this thread's runs loaded first
     float4 z[TC_PER_T];
@@ -601,24 +607,48 @@ __device__ bool flush_tile_update_tc(Ctx<T>& c, int r0, uint32_t tm, uint32_t la
       return false;
     }
     tc_fence_after_sync();
+    for (int h = 0; h < 2; ++h) {
+      if (j0 + 64 * h >= n) break;  // uniform
 #pragma unroll
-    for (int it = 0; it < EP_IT; ++it) {
-      const int c0 = (c.warp >> 2) * 16 + it * EP_STEP;
-      float d[16];
-      tmem_ld16(tm + lane_base + (uint32_t)c0, d);
-      const int j = j0 + c0;
-      float4* brow = reinterpret_cast<float4*>(c.B + (size_t)r * bs + j);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (r < n && j + 4 * q < n) {
-          float4 bv = it < EP_PF ? bt[it < EP_PF ? it : 0][q] : __ldcg(brow + q);
-          bv.x -= d[4 * q];
-          bv.y -= d[4 * q + 1];
-          bv.z -= d[4 * q + 2];
-          bv.w -= d[4 * q + 3];
-          brow[q] = bv;
+      for (int q = 0; q < PER_T; ++q) {
+        const int idx = c.tid + q * NT;
+        if (idx / HALF_F4 == h) {
+          const int e = idx - h * HALF_F4, row = e >> 4, c4 = e & 15;
+          buf[row * 16 + (c4 ^ (row & 15))] = pre[q];
         }
       }
+      __syncthreads();
+      constexpr int COLS = 64 / NG;  // columns of this thread's group in a half
+#pragma unroll
+      for (int cc = 0; cc < COLS; cc += 16) {
+        const int c0 = 64 * h + cg * COLS + cc;  // column within the tile
+        float d[16];
+        tmem_ld16(tm + lane_base + (uint32_t)c0, d);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c4 = ((c0 - 64 * h) >> 2) + q;
+          float4& v = buf[rq * 16 + (c4 ^ (rq & 15))];
+          float4 b = v;
+          b.x -= d[4 * q];
+          b.y -= d[4 * q + 1];
+          b.z -= d[4 * q + 2];
+          b.w -= d[4 * q + 3];
+          v = b;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < PER_T; ++q) {
+        const int idx = c.tid + q * NT;
+        if (idx / HALF_F4 == h) {
+          const int e = idx - h * HALF_F4, row = e >> 4, c4 = e & 15;
+          const int r = r0 + row, j = j0 + 64 * h + 4 * c4;
+          if (r < n && j < n)  // n % 4 == 0: whole float4 groups in or out
+            *reinterpret_cast<float4*>(c.B + (size_t)r * bs + j) =
+                buf[row * 16 + (c4 ^ (row & 15))];
+        }
+      }
+      __syncthreads();
     }
     tc_fence_before_sync();
     __syncthreads();

@@ -400,16 +400,24 @@ def test_tma_staged_stencil_matches_plain_loads(Q, make, precision, W):
     assert np.array_equal(a[3], b[3])
 
 
-@pytest.mark.parametrize("nt", [256, 128])
-def test_tensor_core_flush_matches_simt_flush(Q, oracle_lib, nt):
-    """n = 256, inverse in global memory, delayed rank 16: windows flushed by tcgen05
-    3xTF32 MMAs give the same trajectories as the CUDA-core flush, an inverse as accurate
-    (max|A^-1 A - I| and ||A^-1 A - I||_F within twice the CUDA-core flush's: at n = 256
-    an FP32 inverse updated in place over a generation sits at 1e-4..5e-4 element-wise
-    with either engine), and log|Psi| equal to the oracle's FP64 recompute."""
-    wl = wl_mod.pw512()
+def _pw1024():
+    # n = 512 per spin: the flush by row tiles (X, Y from TMEM, the tile's update through
+    # shared memory); 1024 electrons at the density of the other systems, no ions
+    return wl_mod.make_workload("pw1024", n_el=1024, n_orb=512, grid=40, n_walkers=2,
+                                n_gen=1, tau=0.5, n_recompute=0, j2_knots=10)
+
+
+@pytest.mark.parametrize("make,nt", [(wl_mod.pw512, 256), (wl_mod.pw512, 128), (_pw1024, 128)])
+def test_tensor_core_flush_matches_simt_flush(Q, oracle_lib, make, nt):
+    """Inverse in global memory, delayed rank 16: windows flushed by tcgen05 3xTF32 MMAs
+    (n = 256: three passes over B; n = 512: by row tiles) give the same trajectories as the
+    CUDA-core flush, an inverse as accurate (max|A^-1 A - I| and ||A^-1 A - I||_F within
+    twice the CUDA-core flush's: an FP32 inverse updated in place over a generation sits at
+    1e-4..5e-4 element-wise with either engine at n = 256), and log|Psi| equal to the
+    oracle's FP64 recompute."""
+    wl = make()
     wl.drift = False  # trajectories depend on decisions only, not on rounding of the drift
-    W = 4
+    W = 4 if wl.n_up <= 256 else 2
     R = np.ascontiguousarray(wl.positions(n_walkers=W))
     res = {}
     for engine in ("auto", "simt"):
@@ -436,7 +444,7 @@ def test_tensor_core_flush_matches_simt_flush(Q, oracle_lib, nt):
             mt, ms = max(mt, np.abs(Et).max()), max(ms, np.abs(Es).max())
             ft, fs = max(ft, np.linalg.norm(Et)), max(fs, np.linalg.norm(Es))
     assert mt < 2 * ms and ft < 2 * fs, (mt, ms, ft, fs)
-    assert mt < 1e-3
+    assert mt < (1e-3 if wl.n_up <= 256 else 1e-2)
     osys = oracle_lib.OracleSystem(wl)
     for w in np.nonzero(same)[0][:2]:
         ref, _ = osys.logpsi(Rt[w])
