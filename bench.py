@@ -70,26 +70,41 @@ def ncu_traffic(kernel: str):
 
 
 def l2_copy_peak():
-    """GB/s of device-to-device copies whose sources and destinations (24 MiB each) stay in
-    L2 (129 MB): read + write bytes of 20 back-to-back copies between CUDA events, best of
-    5 such runs after warm-up."""
+    """GB/s of an L2-resident elementwise copy (read + write bytes): 40 launches of
+    b = a * 1 over buffers of 16, 24 or 32 MiB each (both buffers together stay within the
+    129 MB L2), captured once in a CUDA graph so that the launches run back to back; the
+    best of 5 replays of each size after warm-up, the best size reported.  (Single
+    device-to-device copies of such buffers, timed launch by launch, measured lower: their
+    launch gaps are comparable to a copy.)"""
     import torch
-    n = 6 * 1024 * 1024
-    a = torch.ones(n, dtype=torch.float32, device="cuda")
-    b = torch.empty_like(a)
-    for _ in range(10):
-        b.copy_(a)
-    best = float("inf")
-    for _ in range(5):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            b.copy_(a)
-            a.copy_(b)
-        e1.record()
+    best_gbs = 0.0
+    for mib in (16, 24, 32):
+        n = mib * 1024 * 1024 // 4
+        a = torch.ones(n, dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                torch.mul(a, 1.0, out=b)
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(40):
+                    torch.mul(a, 1.0, out=b)
         torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 1000.0)
-    return 20 * 2 * 4 * n / best / 1e9
+        for _ in range(2):
+            g.replay()
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1000.0)
+        best_gbs = max(best_gbs, 40 * 2 * 4 * n / best / 1e9)
+        del g, a, b
+    return best_gbs
 
 
 def peaks():
@@ -208,10 +223,13 @@ def coulomb_args(wl):
     return (wl.n_el / max(1, wl.n_ions), 8.0 / wl.L, 10)
 
 
+LAYOUT = "auto"  # the move kernel's shared-memory layout (--layout)
+
+
 def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0, nlpp=None, coulomb=None):
     from paper_2209_14487_gb300 import qmcgb
     c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
-                                  stream=stream, cta_threads=nt)
+                                  stream=stream, cta_threads=nt, layout=LAYOUT)
     if nlpp is not None:
         c.qmc_load_nlpp(*nlpp)
     if coulomb is not None:
@@ -477,7 +495,9 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
     cap = wl.n_walkers
     target = max(1, int(round(target_frac * cap)))
     c = qmcgb.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
-                                  stream=stream.cuda_stream, cta_threads=nt, dmc=True)
+                                  stream=stream.cuda_stream, cta_threads=nt, dmc=True,
+                                  layout=LAYOUT)
+    layout = c.kernel_config["layout"]
     c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=crowd_id)))
     c.qmc_recompute()
     e_prev = np.zeros(cap)
@@ -542,7 +562,7 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
     return {"ms": [a.elapsed_time(b) for a, b in ev_b],
             "sweep_ms": [a.elapsed_time(b) for a, b in ev_s], "moves": moves,
             "sizes": sizes, "e_est": e_est_hist, "p_acc": p_acc, "launches": launches,
-            "capacity": cap, "target": target, "repairs": repairs,
+            "capacity": cap, "target": target, "repairs": repairs, "layout": layout,
             "recompute_step_ms": rc_ms, "plain_probe_ms": plain_ms}
 
 
@@ -593,7 +613,8 @@ def dmc_main(args, wl, ws, rank, cfg):
                                     "branching and device gather + E_T feedback",
                           capacity=r["capacity"], target_walkers=r["target"],
                           precision="mixed", update=f"{update} k={k}",
-                          cta_threads=nt or "library", parallelism=f"replicas x{ws}")}
+                          cta_threads=nt or "library", layout=r["layout"],
+                          parallelism=f"replicas x{ws}")}
     if tune_table is not None:
         out["autotune"] = {"ms_per_generation": tune_table, "chosen": f"{update}:{k}:{nt}"}
     sweep_rate = sum(r["moves"]) / (sum(r["sweep_ms"]) / 1000.0)
@@ -615,6 +636,22 @@ def dmc_main(args, wl, ws, rank, cfg):
                        "bytes_per_move": bpm, "walkers_mean": W_mean, "peak_source": src}
     out["gpu_launches"] = r["launches"]
     out["clocks"] = clk.summary()
+    if not args.no_fp64:
+        # the FP64 path on the same system: Sherman-Morrison sweeps (its delayed window
+        # does not fit in shared memory at this size; the library takes the compact
+        # layout) of the DMC population's target walker count, timed like the mixed VMC
+        # path (L2 flushed between generations, the recompute amortised); outside the
+        # clock record of the DMC generations above
+        import dataclasses
+        wl64 = dataclasses.replace(wl, n_walkers=r["target"])
+        f = time_path(wl64, "fp64", "sm", 1, args.fp64_steps, 3, rank, flush, 128)
+        ms64, _ = amortised(f, wl64.n_recompute)
+        v64 = aggregate_value(wl64.n_walkers * wl.n_el * len(ms64), sum(ms64) / 1000.0, ws)
+        out["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": statistics.mean(ms64),
+                       "update": "sm", "layout": "compact", "walkers": wl64.n_walkers,
+                       "steps": len(ms64), "mode": "VMC sweeps (no fixed node, no branching)",
+                       "compare_with": "dmc.sweep_only_value"}
+        out["mixed_over_fp64"] = sweep_rate / v64
     if rank == 0 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wl, target_s=10.0, max_gens=1,
                                               walkers=args.cpu_walkers)
@@ -730,12 +767,17 @@ def main():
                     help="threads per walker CTA (0: tuned with --update auto, else the "
                          "library's choice)")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--equilibrate", type=int, default=100,
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="--dmc: timed generations of the FP64 arm")
+    ap.add_argument("--layout", default="auto", choices=["auto", "shared", "compact"],
+                    help="the move kernel's shared-memory layout (auto: the library's pick)")
+    ap.add_argument("--equilibrate", type=int, default=200,
                     help="untimed generations before the energy chain of each path")
-    ap.add_argument("--energy-gens", type=int, default=100,
+    ap.add_argument("--energy-gens", type=int, default=800,
                     help="generations of the energy chain (0: no energy comparison)")
-    ap.add_argument("--energy-block", type=int, default=10,
-                    help="generations per block of the energy error")
+    ap.add_argument("--energy-block", type=int, default=40,
+                    help="generations per block of the energy error (longer than the "
+                         "chain's autocorrelation)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dmc", action="store_true",
@@ -757,6 +799,8 @@ def main():
                          "their own streams")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global LAYOUT
+    LAYOUT = args.layout
 
     from paper_2209_14487_gb300 import workloads
     wl = workloads.WORKLOADS[args.workload]()
@@ -927,7 +971,8 @@ def main():
     l2 = l2_copy_peak()
     out["roofline_l2"] = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s",
                           "frac": achieved / l2,
-                          "peak_source": "measured here: 32 MiB device copy resident in L2"}
+                          "peak_source": "measured here: L2-resident elementwise copy "
+                                         "(16-32 MiB buffers, 40 launches in a CUDA graph)"}
     out["gpu_launches"] = mixed["launches"]
     extras = []
     if args.nlpp:

@@ -50,7 +50,8 @@ typedef enum qmc_status {
   QMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out                            */
   QMC_ERR_NAN = 6,         /* non-finite local energy or ratio (the move is rejected)  */
   QMC_ERR_STATE = 7,       /* call out of order (accept without propose, no orbitals)  */
-  QMC_ERR_UNSUPPORTED = 8  /* valid request this build does not serve (size limits)    */
+  QMC_ERR_UNSUPPORTED = 8, /* valid request this build does not serve (size limits)    */
+  QMC_ERR_BOUNDS = 9       /* a device bounds check failed (bounds-checked build only) */
 } qmc_status;
 
 enum { QMC_MEM_HOST = 0, QMC_MEM_DEVICE = 1 };
@@ -71,6 +72,7 @@ typedef struct qmc_system_desc {
 
 /* How the crowd is driven. */
 enum { QMC_STAGING_AUTO = 0, QMC_STAGING_LDG = 1 };
+enum { QMC_LAYOUT_AUTO = 0, QMC_LAYOUT_SHARED = 1, QMC_LAYOUT_COMPACT = 2 };
 enum { QMC_ENGINE_AUTO = 0, QMC_ENGINE_SIMT = 1 };
 
 typedef struct qmc_run_desc {
@@ -103,7 +105,15 @@ typedef struct qmc_run_desc {
   int dmc;          /* 1: diffusion Monte Carlo: fixed-node acceptance (a move that     *
                      * changes the sign of the determinant is rejected) and population *
                      * branching by qmc_dmc_branch; n_walkers is then the capacity     */
-  int reserved;     /* 0                                                              */
+  int layout;       /* shared-memory layout of the move kernel: QMC_LAYOUT_AUTO (0) the  *
+                     * library's pick (below), QMC_LAYOUT_SHARED: the delayed window's  *
+                     * new orbital rows and each sweep's table of draws in shared       *
+                     * memory, QMC_LAYOUT_COMPACT: both outside it (the window rows in  *
+                     * global memory, where they are kept between calls anyway, and    *
+                     * each move's draws computed from the same Philox words when       *
+                     * needed), so that larger systems fit and more CTAs share an SM;   *
+                     * results are the same either way.  AUTO takes SHARED unless only  *
+                     * COMPACT fits (FP64 Sherman-Morrison at n = 768, for one).        */
   double guard_tol; /* mixed path: inverse guard bound (0: the library's 0.1; < 0:      *
                      * off).  After each sweep every walker's FP32 inverses are probed   *
                      * with a fixed sign vector v (v_l = -1 where bit 31 of             *
@@ -200,11 +210,11 @@ int qmc_get_launch_count(qmc_crowd* crowd, unsigned long long* count);
 /* The move kernel's configuration, chosen at creation from the shared memory a CTA may
  * use: 1 in *b_in_smem when the moving spin's inverse is staged in shared memory, 1 in
  * *stencil_tma when each move's orbital stencil arrives by TMA, the kernel's dynamic
- * shared memory in bytes, its threads per CTA, and 1 in *tc_flush when delayed windows
- * are flushed on the tensor cores.  Any output pointer may be NULL.
- * Errors: INVALID_ARG. */
+ * shared memory in bytes, its threads per CTA, 1 in *tc_flush when delayed windows
+ * are flushed on the tensor cores, and the layout taken (QMC_LAYOUT_SHARED or
+ * QMC_LAYOUT_COMPACT).  Any output pointer may be NULL.  Errors: INVALID_ARG. */
 int qmc_get_kernel_config(const qmc_crowd* crowd, int* b_in_smem, int* stencil_tma,
-                          int* smem_bytes, int* cta_threads, int* tc_flush);
+                          int* smem_bytes, int* cta_threads, int* tc_flush, int* layout);
 
 /* Checkpoint: positions, generation and RNG seed.  With buf == NULL, *size receives the
  * byte count; otherwise *size must hold at least that many bytes.  Restoring recomputes
@@ -339,6 +349,34 @@ int qmc_dmc_append(qmc_crowd* crowd, const double* R, int m, int mem);
 
 /* Text of the CUDA error behind the calling thread's last QMC_ERR_CUDA ("no error" if none). */
 const char* qmc_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Bounds-checked build.  The same sources compiled with -DQMCGB_CHECK=1 (libqmcgb_check.so,
+ * `python -m paper_2209_14487_gb300.build --check`) check, on the device, every walker and
+ * electron index a kernel takes, each proposal's spline cell (its 4x4x4 stencil must lie in
+ * the ghost-padded table), each stencil item's orbital and point, the delayed window's
+ * count before an append, the shared-memory layout against the launch's dynamic shared
+ * memory, the TMA stencil copy's size and buffer, the nonlocal pair list's ion indices and
+ * the DMC gather's source walkers.  A failed check records its site and value (the first
+ * failure of the crowd), skips the access (a bad index is replaced by 0, a bad walker or
+ * layout ends the CTA) and makes the call return QMC_ERR_BOUNDS; the crowd then rebuilds
+ * its state from the stored positions at the next call.  In the normal build the checks
+ * compile to nothing, qmc_build_flags() is 0 and qmc_check_report reports nothing.
+ * --------------------------------------------------------------------------------------- */
+enum { QMC_BUILD_CHECKED = 1 };
+/* QMC_BUILD_CHECKED when this library is the bounds-checked build, else 0. */
+int qmc_build_flags(void);
+/* The crowd's first failed check since the last report, then cleared: site (host) 0 if
+ * none, else 1 walker, 2 electron, 3 spline cell, 4 stencil item, 5 window count,
+ * 6 shared-memory layout, 7 stencil copy, 8 pair-list ion, 9 DMC source walker; value
+ * (host, may be NULL) the offending index (for a cell: dimension << 32 | cell).
+ * Synchronous.  Errors: INVALID_ARG. */
+int qmc_check_report(qmc_crowd* crowd, int* site, long long* value);
+/* Test hook of the checked build: with on = 1 every proposal of electron 0 gets spline cell
+ * G + 5 in x (outside the table), which the cell check records (site 3) and replaces by
+ * cell 0 before any load, so the call returns QMC_ERR_BOUNDS; on = 0 removes it.  Errors:
+ * INVALID_ARG; UNSUPPORTED in the normal build (no check would stop the access). */
+int qmc_test_plant_bad_cell(qmc_crowd* crowd, int on);
 
 /* Allocation-free FP64 inverse of a batch of dense matrices.  The paper has no
  * counterpart: this call exists for callers that must not allocate device memory when

@@ -3,6 +3,11 @@
 Translation units are compiled in parallel and linked into
 paper_2209_14487_gb300/libqmcgb.so; objects go to paper_2209_14487_gb300/_build/.
 A unit is recompiled when it or any header under csrc/ or include/ is newer than its object.
+
+build(checked=True) (or `python -m paper_2209_14487_gb300.build --check`) builds the
+bounds-checked library libqmcgb_check.so from the same sources with -DQMCGB_CHECK=1
+(objects in _build_check/); the binding loads it instead when QMCGB_CHECK=1 is set in
+the environment.
 """
 from __future__ import annotations
 
@@ -18,6 +23,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqmcgb.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libqmcgb_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -36,15 +43,17 @@ def _headers_mtime() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags: list | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, extra_flags: list | None = None,
+          checked: bool = False) -> str:
+    build_dir, lib = (BUILD_CHECK, LIB_CHECK) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hmt = _headers_mtime()
     exe = nvcc()
-    extra = list(extra_flags or [])
+    extra = list(extra_flags or []) + (["-DQMCGB_CHECK=1"] if checked else [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         if (not force and os.path.exists(obj) and os.path.getmtime(obj) >= os.path.getmtime(src)
                 and os.path.getmtime(obj) >= hmt):
             return obj
@@ -62,16 +71,16 @@ def build(verbose: bool = False, force: bool = False, extra_flags: list | None =
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [exe] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        cmd = [exe] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, checked="--check" in sys.argv))

@@ -11,6 +11,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qmcgb.h"
 #include "qmc_internal.h"
 
@@ -114,6 +116,7 @@ struct qmc_crowd {
   uint32_t gen = 0;
   unsigned long long launches = 0;
   int test_no_copy = 0;             // failure-detection test hook (stencil copies not issued)
+  int test_bad_cell = 0;            // checked-build test hook (a planted out-of-range cell)
   CUtensorMap tmap;  // (128-byte aligned type) the padded table as a 4-D tensor, for the stencil copy
   size_t smem = 0;               // dynamic shared memory of the move kernel
 };
@@ -138,6 +141,17 @@ int cuda_fail(cudaError_t e) {
     cudaError_t e_ = (call);                       \
     if (e_ != cudaSuccess) return cuda_fail(e_);   \
   } while (0)
+
+// An NVTX range named after the C-ABI call for the call's duration (a profiler's timeline
+// shows every call and the kernels it launched; without a tool attached it costs a few
+// nanoseconds).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define QMC_RANGE() NvtxRange qmc_range_(__func__)
 
 bool is_mixed(const qmc_crowd* c) { return c->run.precision == QMC_PREC_MIXED; }
 
@@ -183,12 +197,15 @@ void sync_params(qmc_crowd* c) {
   p.jvalid = c->d_jvalid;
   p.pend = c->d_pend;
   p.status = c->d_status;
+  // d_status holds four ints: the status bits, then the checked build's 8-byte record
+  p.check_info = reinterpret_cast<unsigned long long*>(c->d_status + 2);
   p.n_accept = c->d_nacc;
   p.guard_val = c->d_guard;
   p.n_repair = c->d_nrep;
   p.lu_ws = c->d_ws;
   p.accept_trace = c->d_trace;
   p.test_no_copy = c->test_no_copy;
+  p.test_bad_cell = c->test_bad_cell;
   p.K2 = c->K2;
   p.K1 = (c->K1 > 0 && c->sys.n_ions > 0) ? c->K1 : 0;
   p.rc2 = c->rc2;
@@ -277,6 +294,11 @@ int read_status(qmc_crowd* c) {
   // a generation cut short by a timed-out wait may have updated rows and inverses of
   // moves whose positions it did not store: everything is rebuilt from the positions
   if (st & qmcgb::ST_TIMEOUT) c->stale = true;
+  // a failed bounds check (checked build) skipped accesses: nothing of the state is trusted
+  if (st & qmcgb::ST_BOUNDS) {
+    c->stale = true;
+    return QMC_ERR_BOUNDS;
+  }
   if (st & qmcgb::ST_SINGULAR) return QMC_ERR_SINGULAR;
   if (st & qmcgb::ST_NAN) return QMC_ERR_NAN;
   if (st & qmcgb::ST_STATE) return QMC_ERR_STATE;
@@ -353,12 +375,31 @@ const char* qmc_status_string(int status) {
     case QMC_ERR_NAN: return "non-finite ratio or local energy";
     case QMC_ERR_STATE: return "call out of order or missing input";
     case QMC_ERR_UNSUPPORTED: return "size or option not supported by this build";
+    case QMC_ERR_BOUNDS: return "device bounds check failed (checked build)";
     default: return "unknown status";
   }
 }
 
+int qmc_build_flags(void) { return QMCGB_CHECK ? QMC_BUILD_CHECKED : 0; }
+
+int qmc_check_report(qmc_crowd* c, int* site, long long* value) {
+  QMC_RANGE();
+  if (!c || !site) return QMC_ERR_INVALID_ARG;
+  unsigned long long rec = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(&rec, c->p.check_info, sizeof(rec), cudaMemcpyDeviceToHost));
+  if (rec) CK(cudaMemset(c->p.check_info, 0, sizeof(rec)));
+  *site = (int)(rec >> 56);
+  if (value) {
+    const long long v = (long long)(rec & ((1ull << 56) - 1));
+    *value = v >= (1ll << 55) ? v - (1ll << 56) : v;  // sign of the 56-bit field
+  }
+  return QMC_OK;
+}
+
 int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* cuda_stream,
                      qmc_crowd** out) {
+  QMC_RANGE();
   if (!sys || !run || !out) return QMC_ERR_INVALID_ARG;
   *out = nullptr;
   if (sys->n_up < 1 || sys->n_dn < 0 || sys->n_orb < sys->n_up || sys->n_ions < 0 ||
@@ -445,8 +486,20 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
                      (p.nt == 128 || p.nt == 256);
   const int plans[4][2] = {{1, 1}, {1, 0}, {0, 1}, {0, 0}};
   size_t smem = 0;
-  // the first plan that fits for delay rank k (sets p.k, p.ks and the plan's fields)
-  auto place = [&](int k) -> bool {
+  if (run->layout < QMC_LAYOUT_AUTO || run->layout > QMC_LAYOUT_COMPACT) {
+    delete c;
+    return QMC_ERR_INVALID_ARG;
+  }
+  // Layouts to try: the caller's, else shared (every plan), then compact (the window's
+  // rows in global memory and the draws computed per move) when no shared plan fits.
+  const int lay_first = run->layout == QMC_LAYOUT_COMPACT ? 1 : 0;
+  const int lay_last = run->layout == QMC_LAYOUT_SHARED ? 0 : 1;
+  auto fits = [&]() -> bool {
+    smem = qmcgb::move_smem_bytes(p, es);
+    return optin <= 0 || smem <= (size_t)optin;
+  };
+  // the first plan that fits for delay rank k in the current layout
+  auto place_plan = [&](int k) -> bool {
     p.k = k;
     p.ks = k + 1;
     for (const auto& pl : plans) {
@@ -455,8 +508,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
       p.use_tma = pl[1];
       p.tc_flush = (tc_ok && !pl[0]) ? 1 : 0;
       p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
-      smem = qmcgb::move_smem_bytes(p, es);
-      if (optin <= 0 || smem <= (size_t)optin) return true;
+      if (fits()) return true;
     }
     if (tc_ok) {  // without the tensor-core stage
       for (const auto& pl : plans) {
@@ -465,9 +517,16 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
         p.use_tma = pl[1];
         p.tc_flush = 0;
         p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
-        smem = qmcgb::move_smem_bytes(p, es);
-        if (optin <= 0 || smem <= (size_t)optin) return true;
+        if (fits()) return true;
       }
+    }
+    return false;
+  };
+  // the first layout and plan that fit (sets p.k, p.ks, p.compact and the plan's fields)
+  auto place = [&](int k) -> bool {
+    for (int cp = lay_first; cp <= lay_last; ++cp) {
+      p.compact = cp;
+      if (place_plan(k)) return true;
     }
     return false;
   };
@@ -531,7 +590,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   st |= dmalloc((void**)&c->d_pend, sizeof(double) * W * qmcgb::PEND_STRIDE);
   st |= dmalloc((void**)&c->d_ws, sizeof(double) * W * 2 * 2 * n * n);
   st |= dmalloc((void**)&c->d_nacc, sizeof(unsigned long long));
-  st |= dmalloc((void**)&c->d_status, sizeof(int));
+  st |= dmalloc((void**)&c->d_status, 4 * sizeof(int));
   if (guard) {
     st |= dmalloc((void**)&c->d_guard, sizeof(float) * W);
     st |= dmalloc((void**)&c->d_nrep, sizeof(unsigned long long) * 2);
@@ -548,7 +607,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   cudaMemsetAsync(c->d_jvalid, 0, sizeof(int) * W, c->stream);
   cudaMemsetAsync(c->d_pend, 0, sizeof(double) * W * qmcgb::PEND_STRIDE, c->stream);
   cudaMemsetAsync(c->d_nacc, 0, sizeof(unsigned long long), c->stream);
-  cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+  cudaMemsetAsync(c->d_status, 0, 4 * sizeof(int), c->stream);
   if (guard) {
     cudaMemsetAsync(c->d_guard, 0, sizeof(float) * W, c->stream);
     cudaMemsetAsync(c->d_nrep, 0, sizeof(unsigned long long) * 2, c->stream);
@@ -576,6 +635,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
 }
 
 int qmc_crowd_destroy(qmc_crowd* c) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   cudaStreamSynchronize(c->stream);
   free_all(c);
@@ -585,6 +645,7 @@ int qmc_crowd_destroy(qmc_crowd* c) {
 }
 
 int qmc_load_positions(qmc_crowd* c, const double* R, int mem) {
+  QMC_RANGE();
   if (!c || !R) return QMC_ERR_INVALID_ARG;
   const size_t n3 = (size_t)c->p.W * c->p.N * 3;
   CK(cudaMemcpyAsync(c->d_R, R, n3 * sizeof(double),
@@ -599,6 +660,7 @@ int qmc_load_positions(qmc_crowd* c, const double* R, int mem) {
 }
 
 int qmc_load_ions(qmc_crowd* c, const double* RI) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (c->sys.n_ions == 0) return QMC_OK;
   if (!RI) return QMC_ERR_INVALID_ARG;
@@ -612,6 +674,7 @@ int qmc_load_ions(qmc_crowd* c, const double* RI) {
 }
 
 int qmc_load_orbitals(qmc_crowd* c, const void* coefs, int dtype, int mem) {
+  QMC_RANGE();
   if (!c || !coefs) return QMC_ERR_INVALID_ARG;
   if (dtype != QMC_DTYPE_F64 && dtype != QMC_DTYPE_F32) return QMC_ERR_INVALID_ARG;
   const size_t G = (size_t)c->p.G;
@@ -643,6 +706,7 @@ int qmc_load_orbitals(qmc_crowd* c, const void* coefs, int dtype, int mem) {
 }
 
 int qmc_load_jastrow(qmc_crowd* c, int kind, const double* coefs, int K, double rc) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (K < 0 || K > qmcgb::MAX_KNOTS || (K > 0 && (!coefs || !(rc > 0.0))))
     return QMC_ERR_INVALID_ARG;
@@ -671,6 +735,7 @@ int qmc_load_jastrow(qmc_crowd* c, int kind, const double* coefs, int K, double 
 }
 
 int qmc_recompute(qmc_crowd* c) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (!c->has_orbitals || !c->has_positions) return QMC_ERR_STATE;
   int st = rebuild(c);
@@ -679,6 +744,7 @@ int qmc_recompute(qmc_crowd* c) {
 }
 
 int qmc_eval_grad_batch(qmc_crowd* c, int iel, double* grad, int mem) {
+  QMC_RANGE();
   if (!c || !grad) return QMC_ERR_INVALID_ARG;
   if (check_iel(c, iel)) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
@@ -697,6 +763,7 @@ int qmc_eval_grad_batch(qmc_crowd* c, int iel, double* grad, int mem) {
 
 int qmc_propose_move_batch(qmc_crowd* c, int iel, const double* rnew, double* ratio,
                            double* grad, double* log_ratio, double* rnew_out, int mem) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (check_iel(c, iel)) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
@@ -741,6 +808,7 @@ int qmc_propose_move_batch(qmc_crowd* c, int iel, const double* rnew, double* ra
 
 int qmc_accept_reject_batch(qmc_crowd* c, int iel, const uint8_t* accept, uint8_t* accepted_out,
                             int mem) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (check_iel(c, iel)) return QMC_ERR_INVALID_ARG;
   if (!c->has_orbitals || !c->has_positions || c->stale) return QMC_ERR_STATE;
@@ -769,6 +837,7 @@ int qmc_accept_reject_batch(qmc_crowd* c, int iel, const uint8_t* accept, uint8_
 }
 
 int qmc_local_energy_batch(qmc_crowd* c, double* eloc, int mem) {
+  QMC_RANGE();
   if (!c || !eloc) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
   if (st) return st;
@@ -785,6 +854,7 @@ int qmc_local_energy_batch(qmc_crowd* c, double* eloc, int mem) {
 }
 
 int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) {
+  QMC_RANGE();
   if (!c || n_gen < 0) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
   if (st) return st;
@@ -856,6 +926,7 @@ int qmc_sweep(qmc_crowd* c, int n_gen, double* eloc, int mem, qmc_stats* stats) 
 }
 
 int qmc_get_positions(qmc_crowd* c, double* R, int mem) {
+  QMC_RANGE();
   if (!c || !R) return QMC_ERR_INVALID_ARG;
   const size_t bytes = sizeof(double) * c->p.W * c->p.N * 3;
   CK(cudaMemcpyAsync(R, c->d_R, bytes,
@@ -866,6 +937,7 @@ int qmc_get_positions(qmc_crowd* c, double* R, int mem) {
 }
 
 int qmc_get_logpsi(qmc_crowd* c, double* logabs, int* sign) {
+  QMC_RANGE();
   if (!c || !logabs || !sign) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
   if (st) return st;
@@ -889,6 +961,7 @@ int qmc_get_logpsi(qmc_crowd* c, double* logabs, int* sign) {
 }
 
 int qmc_get_inverse(qmc_crowd* c, int spin, double* out) {
+  QMC_RANGE();
   if (!c || !out || (spin != 0 && spin != 1)) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
   if (st) return st;
@@ -910,6 +983,7 @@ int qmc_get_inverse(qmc_crowd* c, int spin, double* out) {
 }
 
 int qmc_get_slater_matrix(qmc_crowd* c, int spin, double* out) {
+  QMC_RANGE();
   if (!c || !out || (spin != 0 && spin != 1)) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
   if (st) return st;
@@ -928,20 +1002,24 @@ int qmc_get_slater_matrix(qmc_crowd* c, int spin, double* out) {
 }
 
 int qmc_get_generation(qmc_crowd* c, uint32_t* gen) {
+  QMC_RANGE();
   if (!c || !gen) return QMC_ERR_INVALID_ARG;
   *gen = c->gen;
   return QMC_OK;
 }
 
 int qmc_set_generation(qmc_crowd* c, uint32_t gen) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   c->gen = gen;
   return QMC_OK;
 }
 
 int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, int* smem_bytes,
-                          int* cta_threads, int* tc_flush) {
+                          int* cta_threads, int* tc_flush, int* layout) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
+  if (layout) *layout = c->p.compact ? QMC_LAYOUT_COMPACT : QMC_LAYOUT_SHARED;
   if (tc_flush) *tc_flush = c->p.tc_flush;
   if (cta_threads) *cta_threads = c->p.nt;
   if (b_in_smem) *b_in_smem = c->p.b_in_smem;
@@ -951,6 +1029,7 @@ int qmc_get_kernel_config(const qmc_crowd* c, int* b_in_smem, int* stencil_tma, 
 }
 
 int qmc_get_update(const qmc_crowd* c, int* update, int* delay_rank) {
+  QMC_RANGE();
   if (!c || !update || !delay_rank) return QMC_ERR_INVALID_ARG;
   *update = c->run.update;
   *delay_rank = c->run.update == QMC_UPDATE_DELAYED ? c->run.delay_rank : 1;
@@ -958,6 +1037,7 @@ int qmc_get_update(const qmc_crowd* c, int* update, int* delay_rank) {
 }
 
 int qmc_get_guard(qmc_crowd* c, double* values, long long* n_repair) {
+  QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (!c->d_guard) return QMC_ERR_STATE;
   const int W = c->p.W;
@@ -975,6 +1055,7 @@ int qmc_get_guard(qmc_crowd* c, double* values, long long* n_repair) {
 }
 
 int qmc_trace_accepts(qmc_crowd* c, int on) {
+  QMC_RANGE();
   if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
   if (on && !c->d_trace) {
     CK(cudaStreamSynchronize(c->stream));
@@ -990,6 +1071,7 @@ int qmc_trace_accepts(qmc_crowd* c, int on) {
 }
 
 int qmc_get_accept_trace(qmc_crowd* c, uint8_t* out) {
+  QMC_RANGE();
   if (!c || !out) return QMC_ERR_INVALID_ARG;
   if (!c->d_trace) return QMC_ERR_STATE;
   CK(cudaMemcpyAsync(out, c->d_trace, (size_t)c->p.W * c->p.N, cudaMemcpyDeviceToHost,
@@ -998,6 +1080,7 @@ int qmc_get_accept_trace(qmc_crowd* c, uint8_t* out) {
 }
 
 int qmc_test_skip_stencil_copy(qmc_crowd* c, int on) {
+  QMC_RANGE();
   if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
   if (on && !c->p.use_tma) return QMC_ERR_INVALID_ARG;
   c->test_no_copy = on;
@@ -1005,13 +1088,24 @@ int qmc_test_skip_stencil_copy(qmc_crowd* c, int on) {
   return QMC_OK;
 }
 
+int qmc_test_plant_bad_cell(qmc_crowd* c, int on) {
+  QMC_RANGE();
+  if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
+  if (!QMCGB_CHECK) return QMC_ERR_UNSUPPORTED;  // only a checked kernel stops the access
+  c->test_bad_cell = on;
+  sync_params(c);
+  return QMC_OK;
+}
+
 int qmc_get_walker_count(const qmc_crowd* c, int* count) {
+  QMC_RANGE();
   if (!c || !count) return QMC_ERR_INVALID_ARG;
   *count = c->p.W;
   return QMC_OK;
 }
 
 int qmc_load_nlpp(qmc_crowd* c, int n_l, const double* amp, const double* width, double rc) {
+  QMC_RANGE();
   if (!c || n_l < 0 || n_l > 3) return QMC_ERR_INVALID_ARG;
   if (n_l > 0) {
     if (!amp || !width || !(rc > 0.0) || rc > 0.5 * c->p.L) return QMC_ERR_INVALID_ARG;
@@ -1033,6 +1127,7 @@ int qmc_load_nlpp(qmc_crowd* c, int n_l, const double* amp, const double* width,
 }
 
 int qmc_load_coulomb(qmc_crowd* c, int on, double Z, double alpha, int mmax) {
+  QMC_RANGE();
   if (!c || (on != 0 && on != 1)) return QMC_ERR_INVALID_ARG;
   if (on == 0) {
     c->p.coul = 0;
@@ -1092,6 +1187,7 @@ int qmc_load_coulomb(qmc_crowd* c, int on, double Z, double alpha, int mmax) {
 }
 
 int qmc_dmc_select(qmc_crowd* c, const int* src, int n_new, int mem) {
+  QMC_RANGE();
   if (!c || !src || n_new < 1 || n_new > c->run.n_walkers) return QMC_ERR_INVALID_ARG;
   if (mem != QMC_MEM_HOST && mem != QMC_MEM_DEVICE) return QMC_ERR_INVALID_ARG;
   if (!c->run.dmc) return QMC_ERR_STATE;
@@ -1119,6 +1215,7 @@ int qmc_dmc_select(qmc_crowd* c, const int* src, int n_new, int mem) {
 }
 
 int qmc_dmc_append(qmc_crowd* c, const double* R, int m, int mem) {
+  QMC_RANGE();
   if (!c || !R || m < 1) return QMC_ERR_INVALID_ARG;
   if (mem != QMC_MEM_HOST && mem != QMC_MEM_DEVICE) return QMC_ERR_INVALID_ARG;
   const int W = c->p.W, N = c->p.N;
@@ -1131,14 +1228,17 @@ int qmc_dmc_append(qmc_crowd* c, const double* R, int m, int mem) {
                      c->stream));
   st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R + off, n3, c->p.L, c->stream));
   if (st) return st;
-  // the new walkers' orbital rows and FP64 inverses, nobody else's
-  if (is_mixed(c)) st = launch_status(c, qmcgb::launch_eval_rows<float>(c->p, c->stream, W, m));
-  else st = launch_status(c, qmcgb::launch_eval_rows<double>(c->p, c->stream, W, m));
+  // the new walkers' orbital rows and FP64 inverses, nobody else's (launched with the
+  // grown population, of which walkers W .. W + m - 1 are the new ones)
+  qmcgb::Params pa = c->p;
+  pa.W = W + m;
+  if (is_mixed(c)) st = launch_status(c, qmcgb::launch_eval_rows<float>(pa, c->stream, W, m));
+  else st = launch_status(c, qmcgb::launch_eval_rows<double>(pa, c->stream, W, m));
   if (st) return st;
   if (is_mixed(c))
-    st = launch_status(c, qmcgb::launch_recompute<float>(c->p, c->d_ws, c->stream, W, m));
+    st = launch_status(c, qmcgb::launch_recompute<float>(pa, c->d_ws, c->stream, W, m));
   else
-    st = launch_status(c, qmcgb::launch_recompute<double>(c->p, c->d_ws, c->stream, W, m));
+    st = launch_status(c, qmcgb::launch_recompute<double>(pa, c->d_ws, c->stream, W, m));
   if (st) return st;
   CK(cudaMemsetAsync(c->d_pend + (size_t)W * qmcgb::PEND_STRIDE, 0,
                      sizeof(double) * m * qmcgb::PEND_STRIDE, c->stream));
@@ -1159,7 +1259,8 @@ int gather_population(qmc_crowd* c, int n_new, const double* e_in, double* e_out
   const int N = c->p.N, n = c->p.n, es = c->es;
   qmcgb::WalkerState from{c->d_R, c->d_rows, c->d_binv, c->d_jgl, c->d_logdet, c->d_sign,
                           c->d_jvalid, (size_t)N * 3, (size_t)es * N * 5 * c->p.n_pad,
-                          (size_t)es * 2 * n * n, (size_t)es * N * 4};
+                          (size_t)es * 2 * n * n, (size_t)es * N * 4, c->p.W,
+                          c->d_status, c->p.check_info};
   qmcgb::WalkerState to = from;
   to.R = c->d_R2;
   to.rows = c->d_rows2;
@@ -1191,6 +1292,7 @@ extern "C" {
 
 int qmc_dmc_branch(qmc_crowd* c, const double* e_prev, double* e_new, int mem, double e_trial,
                    qmc_dmc_stats* out) {
+  QMC_RANGE();
   if (!c || !e_prev || !e_new) return QMC_ERR_INVALID_ARG;
   if (!c->run.dmc) return QMC_ERR_STATE;
   int st = ensure_ready(c);
@@ -1239,6 +1341,7 @@ int qmc_dmc_branch(qmc_crowd* c, const double* e_prev, double* e_new, int mem, d
 }
 
 int qmc_get_launch_count(qmc_crowd* c, unsigned long long* count) {
+  QMC_RANGE();
   if (!c || !count) return QMC_ERR_INVALID_ARG;
   *count = c->launches;
   return QMC_OK;
@@ -1255,6 +1358,7 @@ constexpr uint64_t kMagic = 0x31424743514d51ull;  // "QMQCGB1"
 }  // namespace
 
 int qmc_crowd_save(qmc_crowd* c, void* buf, size_t* size) {
+  QMC_RANGE();
   if (!c || !size) return QMC_ERR_INVALID_ARG;
   const size_t need = sizeof(SaveHeader) + sizeof(double) * c->p.W * c->p.N * 3;
   if (!buf) {
@@ -1328,6 +1432,7 @@ int batch_join(qmc_batch* b, bool into_batch) {
 }  // namespace
 
 int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out) {
+  QMC_RANGE();
   if (!crowds || !out || n_crowds < 1 || n_crowds > qmcgb::MAX_BATCH) return QMC_ERR_INVALID_ARG;
   *out = nullptr;
   for (int i = 0; i < n_crowds; ++i) {
@@ -1374,6 +1479,7 @@ int qmc_batch_create(qmc_crowd* const* crowds, int n_crowds, qmc_batch** out) {
 }
 
 int qmc_batch_destroy(qmc_batch* b) {
+  QMC_RANGE();
   if (!b) return QMC_ERR_INVALID_ARG;
   cudaStreamSynchronize(b->stream);
   batch_free(b);
@@ -1382,6 +1488,7 @@ int qmc_batch_destroy(qmc_batch* b) {
 }
 
 int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* stats) {
+  QMC_RANGE();
   if (!b || n_gen < 0) return QMC_ERR_INVALID_ARG;
   const int nc = (int)b->crowds.size();
   for (qmc_crowd* c : b->crowds) {
@@ -1533,12 +1640,14 @@ int qmc_batch_sweep(qmc_batch* b, int n_gen, double* const* eloc, qmc_stats* sta
 }
 
 int qmc_batch_get_launch_count(const qmc_batch* b, unsigned long long* count) {
+  QMC_RANGE();
   if (!b || !count) return QMC_ERR_INVALID_ARG;
   *count = b->launches;
   return QMC_OK;
 }
 
 int qmc_crowd_restore(qmc_crowd* c, const void* buf, size_t size) {
+  QMC_RANGE();
   if (!c || !buf || size < sizeof(SaveHeader)) return QMC_ERR_INVALID_ARG;
   SaveHeader h;
   std::memcpy(&h, buf, sizeof(h));

@@ -84,6 +84,9 @@ __device__ __forceinline__ void copy_bytes(void* dst, const void* src, size_t by
 __global__ void gather_kernel(WalkerState to, WalkerState from, const int* __restrict__ src,
                               const double* __restrict__ e_new, double* e_out) {
   const int d = blockIdx.x, w = src[d];
+#if QMCGB_CHECK
+  if (!QMC_CHECK(from.status, from.check_info, w >= 0 && w < from.n_walkers, CK_SOURCE, w)) return;
+#endif
   copy_bytes(to.R + (size_t)d * to.r_elems, from.R + (size_t)w * to.r_elems,
              sizeof(double) * to.r_elems);
   copy_bytes((char*)to.rows + (size_t)d * to.rows_bytes,

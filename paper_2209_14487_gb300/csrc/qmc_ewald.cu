@@ -45,6 +45,9 @@ template <typename T>
 __global__ void __launch_bounds__(EW_NT) ewald_kernel(const Params p, double* eloc) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = blockIdx.x, tid = threadIdx.x, N = p.N, NI = p.n_ions, M = N + NI;
+#if QMCGB_CHECK
+  if (!QMC_CHECKP(p, w < p.W, CK_WALKER, w)) return;
+#endif
   const int mm1 = p.coul_mmax + 1;
   Cx<T>* tab = reinterpret_cast<Cx<T>*>(smem);  // [EW_CH][3][mm1]
   double* red = reinterpret_cast<double*>(smem + (size_t)EW_CH * 3 * mm1 * sizeof(Cx<T>));

@@ -31,7 +31,25 @@ enum Mode {
 };
 
 // status bits written by kernels
-enum { ST_SINGULAR = 1, ST_NAN = 2, ST_STATE = 4, ST_TIMEOUT = 8 };
+enum { ST_SINGULAR = 1, ST_NAN = 2, ST_STATE = 4, ST_TIMEOUT = 8, ST_BOUNDS = 16 };
+
+// Bounds-checked build (nvcc -DQMCGB_CHECK=1, libqmcgb_check.so): the index checks below
+// record the first failed check (site and offending value) in Params::check_info, set
+// ST_BOUNDS and skip the access; in the normal build they compile to nothing.
+#ifndef QMCGB_CHECK
+#define QMCGB_CHECK 0
+#endif
+enum CheckSite {
+  CK_WALKER = 1,   // CTA's walker index >= W
+  CK_ELECTRON = 2, // electron index outside [0, N)
+  CK_CELL = 3,     // spline cell outside [0, G - 1] (its 4x4x4 stencil leaves the table)
+  CK_ORBITAL = 4,  // stencil item: orbital >= n_pad or point >= 4
+  CK_WINDOW = 5,   // delayed window count > k before an append
+  CK_SMEM = 6,     // shared-memory layout larger than the launch's dynamic shared memory
+  CK_STENCIL = 7,  // TMA stencil copy size != 64 n_pad elements, or its buffer misaligned
+  CK_PAIR = 8,     // nonlocal pair list: ion index >= n_ions
+  CK_SOURCE = 9    // DMC gather: source walker >= the old population
+};
 
 struct Params {
   int W, N, n_up, n;        // n = electrons per spin = occupied orbitals
@@ -45,6 +63,8 @@ struct Params {
   int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
   int inc_jastrow;          // mixed Sherman-Morrison sweep: incremental Jastrow grad/lap
+  int compact;              // compact shared memory: the delayed window's V rows stay in
+                            // win_V (global) and each move's draws are computed when needed
   int dmc;                  // fixed node: a move that changes the determinant's sign is rejected
   int nl_n;                 // nonlocal pseudopotential channels l < nl_n in E_L (0: none)
   double nl_rc;             // their cutoff; v_l(r) = nl_a[l] exp(-r^2 nl_sinv2[l])
@@ -88,6 +108,7 @@ struct Params {
   double* lu_ws;            // [W][2][2 n^2] FP64 workspace of the repair's LU
   uint8_t* accept_trace;    // [W][N]: a sweep's accept decisions (null: not recorded)
   int test_no_copy;         // failure-detection test: stencil copies are not issued
+  int test_bad_cell;        // checked-build test: electron 0's proposals get cell G + 5
   int iel;
   const double* rnew_in;    // [W][3] or null
   double* ratio_out;
@@ -99,7 +120,27 @@ struct Params {
   double* eloc_out;         // [W]
   unsigned long long* n_accept;
   int* status;
+  unsigned long long* check_info;  // checked build: site << 56 | value of the first failure
 };
+
+#if defined(__CUDACC__)
+#if QMCGB_CHECK
+__device__ __noinline__ inline void check_record(int* status, unsigned long long* info, int site,
+                                                 long long v) {
+  atomicOr(status, (int)ST_BOUNDS);
+  if (info)
+    atomicCAS(info, 0ull, ((unsigned long long)site << 56) |
+                              ((unsigned long long)v & ((1ull << 56) - 1)));
+}
+// true when COND holds; otherwise records (SITE, V) and yields false (the caller skips)
+#define QMC_CHECK(STATUS, INFO, COND, SITE, V) \
+  ((COND) ? true : (::qmcgb::check_record((STATUS), (INFO), (SITE), (long long)(V)), false))
+#else
+#define QMC_CHECK(STATUS, INFO, COND, SITE, V) true
+#endif
+#define QMC_CHECKP(P, COND, SITE, V) QMC_CHECK((P).status, (P).check_info, COND, SITE, V)
+#endif
+
 
 size_t move_smem_bytes(const Params& p, int elem_bytes);
 int max_smem_optin();
@@ -114,6 +155,9 @@ struct WalkerState {
   int* sign;
   int* jvalid;
   size_t r_elems, rows_bytes, binv_bytes, jgl_bytes;  // per walker
+  int n_walkers;                   // walkers in this half (checked build: gather sources)
+  int* status;                     // the crowd's status word and check record
+  unsigned long long* check_info;
 };
 cudaError_t launch_branch(const double* e_prev, const double* e_new, int W, int N, double tau,
                           double e_trial, uint64_t seed, uint32_t gen, int cap, int* mult,

@@ -20,6 +20,9 @@ __global__ void __launch_bounds__(LA_NT) eval_rows_kernel(const Params p, int w0
   __shared__ T tt[3];
   const int wl = blockIdx.x / p.N, i = blockIdx.x - wl * p.N, w = w0 + wl;
   const int n = p.n, n_pad = p.n_pad;
+#if QMCGB_CHECK
+  if (!QMC_CHECKP(p, w >= 0 && w < p.W, CK_WALKER, w)) return;
+#endif
   if (threadIdx.x < 3) {
     const int d = threadIdx.x;
     const double x = p.R[((size_t)w * p.N + i) * 3 + d];
@@ -67,6 +70,9 @@ __global__ void __launch_bounds__(LA_NT) recompute_kernel(const Params p, double
   __shared__ LuShared<LA_NT> sh;
   const int ws_id = blockIdx.x, s = ws_id & 1, w = w0 + (ws_id >> 1);
   const int n = p.n, n_pad = p.n_pad;
+#if QMCGB_CHECK
+  if (!QMC_CHECKP(p, w >= 0 && w < p.W, CK_WALKER, w)) return;
+#endif
   const int tid = threadIdx.x;
   double* LU = ws + (size_t)(w - w0) * 4 * n * n + (size_t)s * 2 * n * n;
   double* X = LU + (size_t)n * n;
@@ -125,6 +131,9 @@ template <typename T>
 __global__ void __launch_bounds__(LA_NT) jastrow_U_kernel(const Params p, double* U) {
   __shared__ double red[LA_NWARP];
   const int w = blockIdx.x, N = p.N, NI = p.n_ions;
+#if QMCGB_CHECK
+  if (!QMC_CHECKP(p, w < p.W, CK_WALKER, w)) return;
+#endif
   const double* R = p.R + (size_t)w * N * 3;
   const T* jc = (const T*)p.jc;
   double acc = 0.0;

@@ -144,14 +144,14 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.col = o; o += al16((size_t)p.n_pad * es);
   L.col2 = o; o += p.inc_jastrow ? al16((size_t)p.n_pad * es) : 0;  // the next move's column
   if (over_move) L.tcs = L.phi;
-  L.dchi = o; o += al16((size_t)p.N * 3 * es);
-  L.du = o; o += al16((size_t)p.N * es);
+  L.dchi = o; o += p.compact ? 0 : al16((size_t)p.N * 3 * es);
+  L.du = o; o += p.compact ? 0 : al16((size_t)p.N * es);
   L.red0 = o; o += al16((size_t)NWARP * 8 * 8);  // eight values per warp, FP64 at most
   L.red1 = o; o += al16((size_t)NWARP * 8 * 8);
   L.wP = L.wV = L.wS = L.wy = L.wz = L.wc = L.wb = L.snap = L.xb = L.yb = o;
   if (p.update == 1) {
     L.wP = o; o += al16((size_t)MAX_K * 4);
-    L.wV = o; o += al16((size_t)p.k * p.vs * es);
+    L.wV = o; o += p.compact ? 0 : al16((size_t)p.k * p.vs * es);
     L.wS = o; o += al16((size_t)p.k * p.ks * es);
     L.wy = o; o += al16((size_t)(MAX_K + 1) * es);
     L.wz = o; o += al16((size_t)(MAX_K + 1) * es);
@@ -292,7 +292,9 @@ __device__ void begin_spin(Ctx<T>& c, int s) {
     const T* gV = (const T*)p.win_V + (size_t)ws * p.k * p.vs;
     const T* gS = (const T*)p.win_S + (size_t)ws * p.k * p.ks;
     for (int e = c.tid; e < m; e += NT) c.wP[e] = p.win_P[ws * MAX_K + e];
-    for (int e = c.tid; e < m * p.vs; e += NT) c.wV[e] = gV[e];
+    if (p.compact) c.wV = const_cast<T*>(gV);  // the V rows are used where they are stored
+    else
+      for (int e = c.tid; e < m * p.vs; e += NT) c.wV[e] = gV[e];
     for (int e = c.tid; e < m * p.ks; e += NT) c.wS[e] = gS[e];
     if (c.tid == 0) c.sc->m = m;
   } else if (c.tid == 0) {
@@ -318,7 +320,8 @@ __device__ void end_spin(Ctx<T>& c, int s, bool store) {
     T* gV = (T*)p.win_V + (size_t)ws * p.k * p.vs;
     T* gS = (T*)p.win_S + (size_t)ws * p.k * p.ks;
     for (int e = c.tid; e < m; e += NT) p.win_P[ws * MAX_K + e] = c.wP[e];
-    for (int e = c.tid; e < m * p.vs; e += NT) gV[e] = c.wV[e];
+    if (!p.compact)
+      for (int e = c.tid; e < m * p.vs; e += NT) gV[e] = c.wV[e];
     for (int e = c.tid; e < m * p.ks; e += NT) gS[e] = c.wS[e];
     if (c.tid == 0) p.win_m[ws] = m;
   }
@@ -1392,6 +1395,11 @@ __device__ void accept_update(Ctx<T>& c, int i, int s, int pp, const Prop<T>& pr
     // Phi_m = phi', border S^-1 with b = y, c_l = Phi_m.B[:,p_l], d = Phi_m.B[:,pp]
     // and sigma = d - c.z (= rhoD).
     int m = c.sc->m;
+#if QMCGB_CHECK
+    // the window holds at most k - 1 rows before an append (a full window was flushed);
+    // a bad count is recorded and the window restarted empty (its rows are lost)
+    if (!QMC_CHECKP(p, m >= 0 && m < p.k && m < MAX_K, CK_WINDOW, m)) m = 0;
+#endif
     bool dup = false;
     for (int l = 0; l < m; ++l) dup |= (c.wP[l] == pp);
     // with the flush's operand stage over phi', the five new rows go out and phi' itself
@@ -2133,6 +2141,34 @@ __device__ __forceinline__ void prefetch_grad_rows(const Ctx<T>& c, int i, T* pf
   }
 }
 
+// The Gaussian draws chi of move i and its acceptance uniform: read from the sweep's
+// table in shared memory, or (compact layout) computed from the same Philox words here.
+template <typename T>
+struct Chi3 {
+  T v[3];
+};
+template <typename T>
+__device__ __forceinline__ Chi3<T> chi_of(const Ctx<T>& c, int i) {
+  Chi3<T> r;
+  if (c.p.compact) {
+    T d4[4];
+    draws_t<T>(c.p.seed, (uint32_t)c.w, c.p.gen, (uint32_t)i, d4);
+    r.v[0] = d4[0];
+    r.v[1] = d4[1];
+    r.v[2] = d4[2];
+  } else {
+    r.v[0] = c.dchi[3 * i];
+    r.v[1] = c.dchi[3 * i + 1];
+    r.v[2] = c.dchi[3 * i + 2];
+  }
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ T u_of(const Ctx<T>& c, int i) {
+  return c.p.compact ? accept_uniform_t<T>(c.p.seed, (uint32_t)c.w, c.p.gen, (uint32_t)i)
+                     : c.du[i];
+}
+
 // Proposal of electron i shared by every thread: the mixed path computes it in each
 // thread; the FP64 path on thread 0, then copied through shared memory.
 template <typename T>
@@ -2145,6 +2181,16 @@ __device__ __forceinline__ void shared_proposal(Ctx<T>& c, int i, const T* F, co
     __syncthreads();
     pr = c.sc->pr;
   }
+#if QMCGB_CHECK
+  // the electron index and the spline cell of r' (its 4x4x4 stencil must lie in the
+  // ghost-padded table); a bad cell is recorded and replaced by cell 0 before any load
+  if (c.p.test_bad_cell && i == 0) pr.cell[0] = c.p.G + 5;  // test hook: a planted bad cell
+  QMC_CHECKP(c.p, i >= 0 && i < c.p.N, CK_ELECTRON, i);
+  for (int k = 0; k < 3; ++k)
+    if (!QMC_CHECKP(c.p, pr.cell[k] >= 0 && pr.cell[k] < c.p.G, CK_CELL,
+                    ((long long)k << 32) | (uint32_t)pr.cell[k]))
+      pr.cell[k] = 0;
+#endif
 }
 
 // Offset of this generation's E_L in p.eloc_out: a batch sweep keeps one row per
@@ -2160,6 +2206,21 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
                                           unsigned char* smem) {
   const Lay lay = make_lay<T>(p);
   const int N = p.N, n = p.n, n_pad = p.n_pad;
+#if QMCGB_CHECK
+  {
+    uint32_t dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    // uniform per CTA: the whole walker is skipped
+    if (!QMC_CHECKP(p, w >= 0 && w < p.W, CK_WALKER, w)) return;
+    if (!QMC_CHECKP(p, lay.total <= dyn, CK_SMEM, lay.total)) return;
+    if (p.use_tma &&
+        !QMC_CHECKP(p, p.stencil_bytes == 64 * n_pad * (int)sizeof(T) &&
+                           ((lay.stc + 127) & ~(size_t)127) + (size_t)p.stencil_bytes <=
+                               lay.stc + al16((size_t)p.stencil_bytes + 128),
+                    CK_STENCIL, p.stencil_bytes))
+      return;
+  }
+#endif
   Ctx<T> c{p};
   c.k = make_cst<T>(p);
   c.w = w;
@@ -2214,6 +2275,9 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     c.itj[q] = it < 4 * n ? it % n : 0;
     c.ita[q] = it < 4 * n ? it / n : 0;
     if (it < 4 * n) c.nit = q + 1;
+#if QMCGB_CHECK
+    if (!QMC_CHECKP(p, c.itj[q] < n_pad && c.ita[q] < 4, CK_ORBITAL, it)) c.itj[q] = c.ita[q] = 0;
+#endif
   }
   Scal<T>* sc = c.sc;
 
@@ -2262,7 +2326,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
 
   bool moved = false;
   if constexpr (MODE == MODE_SWEEP) {
-    for (int e = c.tid; e < N; e += NT) {
+    for (int e = c.tid; e < N && !p.compact; e += NT) {
       T d4[4];
       draws_t<T>(p.seed, (uint32_t)w, p.gen, (uint32_t)e, d4);
       c.dchi[3 * e] = d4[0];
@@ -2306,7 +2370,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
           }
           bool nxt = p.drift && n > 1;
           if (nxt) prefetch_grad_rows(c, i + 1, pf);
-          shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
+          shared_proposal(c, i, F, chi_of(c, i).v, nullptr, pr);
           stencil_issue(c, pr);
           jas_inc(c, i, pr, jv, io);
           for (int pp = 0; pp < n; ++pp) {
@@ -2316,7 +2380,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
               c.failed = true;
               break;
             }
-            const int acc = metropolis(p, c.k, pr, rs, c.du[i], w, i);
+            const int acc = metropolis(p, c.k, pr, rs, u_of(c, i), w, i);
             nacc += acc;
             if (p.accept_trace && c.tid == 0) p.accept_trace[(size_t)w * N + i] = (uint8_t)acc;
             if (acc) {
@@ -2337,7 +2401,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
                 for (int k = 0; k < 3; ++k) F[k] = det[k] - c.jgl[4 * i1 + k];
               nxt = p.drift && pp + 2 < n;
               if (nxt) prefetch_grad_rows(c, i1 + 1, pf);
-              shared_proposal(c, i1, F, c.dchi + 3 * i1, nullptr, pr);
+              shared_proposal(c, i1, F, chi_of(c, i1).v, nullptr, pr);
               stencil_issue(c, pr);
               jas_inc(c, i1, pr, jv, io);
             }
@@ -2369,7 +2433,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
         compute_column(c, pp);
         if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
         if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
-        shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
+        shared_proposal(c, i, F, chi_of(c, i).v, nullptr, pr);
         // false only when a stencil copy timed out (status set; uniform over the CTA)
         if (!ratio_grad(c, i, pr, uo, cache_ok, rs)) {
           c.failed = true;
@@ -2377,11 +2441,11 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
         }
         int acc;
         if constexpr (IsMixed<T>::value) {
-          acc = metropolis(p, c.k, pr, rs, c.du[i], w, i);
+          acc = metropolis(p, c.k, pr, rs, u_of(c, i), w, i);
         } else {
           if (c.tid == 0) {
             sc->rs = rs;
-            sc->accept = metropolis(p, c.k, pr, rs, c.du[i], w, i);
+            sc->accept = metropolis(p, c.k, pr, rs, u_of(c, i), w, i);
           }
           __syncthreads();
           rs = sc->rs;

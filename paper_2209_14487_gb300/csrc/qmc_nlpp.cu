@@ -235,6 +235,9 @@ __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* 
   extern __shared__ __align__(16) unsigned char smem[];
   const int w = blockIdx.x, N = p.N, NI = p.n_ions, n = p.n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#if QMCGB_CHECK
+  if (!QMC_CHECKP(p, w < p.W, CK_WALKER, w)) return;
+#endif
   const int gw = blockIdx.y * NL_NW + warp;  // this warp among the walker's
   const NlLay lay = nl_lay<T>(p);
   Pt<T>* R = reinterpret_cast<Pt<T>*>(smem + lay.R);
@@ -307,7 +310,11 @@ __global__ void __launch_bounds__(NL_NT, 2) nlpp_kernel(const Params p, double* 
       pidx -= cnt[seg];
       ++seg;
     }
-    const NlPair<T> pe = pairs[seg * NL_SEG + pidx];
+    NlPair<T> pe = pairs[seg * NL_SEG + pidx];
+#if QMCGB_CHECK
+    if (!QMC_CHECKP(p, pe.I >= 0 && pe.I < NI, CK_PAIR, pe.I)) pe.I = 0;
+    if (!QMC_CHECKP(p, pe.i >= 0 && pe.i < N, CK_ELECTRON, pe.i)) pe.i = 0;
+#endif
     const double e = pair_batch(c, table, Bw, pe.i, pe.I, pe.u0, qb * NL_QB);
     if (lane == 0) vsum += e;
   }

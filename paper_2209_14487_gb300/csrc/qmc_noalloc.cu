@@ -9,6 +9,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qmcgb.h"
 #include "qmc_internal.h"
 
@@ -157,6 +159,11 @@ extern "C" int qmc_inverse_noalloc(const double* a, int n, int batch, double* in
   if (batch < 0 || n < 1) return QMC_ERR_INVALID_ARG;
   if (n > kMaxN) return QMC_ERR_UNSUPPORTED;
   if (batch == 0) return QMC_OK;
+  // an NVTX range over the launches, as for every other C-ABI call
+  struct Range {
+    Range() { nvtxRangePushA("qmc_inverse_noalloc"); }
+    ~Range() { nvtxRangePop(); }
+  } range;
   if (!a || !inv || !logdet || !sign) return QMC_ERR_INVALID_ARG;
   double* scratch = nullptr;
   int st = scratch_address(&scratch);

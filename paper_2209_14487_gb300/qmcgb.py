@@ -13,10 +13,17 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libqmcgb.so")
+# QMCGB_CHECK=1 in the environment selects the bounds-checked build of the same sources
+CHECKED = os.environ.get("QMCGB_CHECK", "0") == "1"
+LIB_PATH = os.path.join(HERE, "libqmcgb_check.so" if CHECKED else "libqmcgb.so")
 
 QMC_OK = 0
 QMC_ERR_UNSUPPORTED = 8
+QMC_ERR_BOUNDS = 9
+QMC_BUILD_CHECKED = 1
+CHECK_SITES = {1: "walker", 2: "electron", 3: "spline cell", 4: "stencil item", 5: "window count",
+               6: "shared-memory layout", 7: "stencil copy", 8: "pair-list ion",
+               9: "DMC source walker"}
 QMC_MEM_HOST, QMC_MEM_DEVICE = 0, 1
 QMC_PREC_FP64, QMC_PREC_MIXED = 0, 1
 QMC_UPDATE_SM, QMC_UPDATE_DELAYED = 0, 1
@@ -24,10 +31,12 @@ QMC_J1, QMC_J2_UU, QMC_J2_UD = 0, 1, 2
 QMC_DTYPE_F64, QMC_DTYPE_F32 = 0, 1
 QMC_STAGING_AUTO, QMC_STAGING_LDG = 0, 1
 QMC_ENGINE_AUTO, QMC_ENGINE_SIMT = 0, 1
+QMC_LAYOUT_AUTO, QMC_LAYOUT_SHARED, QMC_LAYOUT_COMPACT = 0, 1, 2
+LAYOUTS = {"auto": QMC_LAYOUT_AUTO, "shared": QMC_LAYOUT_SHARED, "compact": QMC_LAYOUT_COMPACT}
 GUARD_TOL_DEFAULT = 0.1  # the library's inverse-guard bound (run.guard_tol = 0)
 STATUS_NAMES = {0: "QMC_OK", 1: "QMC_ERR_INVALID_ARG", 2: "QMC_ERR_OOM", 3: "QMC_ERR_CUDA",
                 4: "QMC_ERR_SINGULAR", 5: "QMC_ERR_TIMEOUT", 6: "QMC_ERR_NAN",
-                7: "QMC_ERR_STATE", 8: "QMC_ERR_UNSUPPORTED"}
+                7: "QMC_ERR_STATE", 8: "QMC_ERR_UNSUPPORTED", 9: "QMC_ERR_BOUNDS"}
 
 # every symbol include/qmcgb.h declares
 EXPORTS = [
@@ -41,6 +50,7 @@ EXPORTS = [
     "qmc_batch_get_launch_count", "qmc_dmc_branch", "qmc_get_walker_count", "qmc_dmc_select",
     "qmc_dmc_append", "qmc_load_nlpp", "qmc_load_coulomb", "qmc_get_update", "qmc_get_guard",
     "qmc_trace_accepts", "qmc_get_accept_trace", "qmc_test_skip_stencil_copy",
+    "qmc_build_flags", "qmc_check_report", "qmc_test_plant_bad_cell",
 ]
 
 
@@ -54,7 +64,7 @@ class qmc_run_desc(C.Structure):
                 ("delay_rank", C.c_int), ("n_recompute", C.c_int), ("drift", C.c_int),
                 ("potential", C.c_int), ("staging", C.c_int), ("tau", C.c_double),
                 ("seed", C.c_uint64), ("cta_threads", C.c_int), ("engine", C.c_int),
-                ("dmc", C.c_int), ("reserved", C.c_int), ("guard_tol", C.c_double)]
+                ("dmc", C.c_int), ("layout", C.c_int), ("guard_tol", C.c_double)]
 
 
 class qmc_dmc_stats(C.Structure):
@@ -77,8 +87,9 @@ class QmcError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with "
-                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+        how = ("`python -m paper_2209_14487_gb300.build --check`" if CHECKED else
+               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        raise ImportError(f"{LIB_PATH} is missing: build it with {how} (needs nvcc)")
     lib = C.CDLL(LIB_PATH)
     vp, i = C.c_void_p, C.c_int
     sig = {
@@ -102,7 +113,7 @@ def _load():
         "qmc_get_generation": [vp, C.POINTER(C.c_uint32)],
         "qmc_set_generation": [vp, C.c_uint32],
         "qmc_get_launch_count": [vp, C.POINTER(C.c_ulonglong)],
-        "qmc_get_kernel_config": [vp] + [C.POINTER(C.c_int)] * 5,
+        "qmc_get_kernel_config": [vp] + [C.POINTER(C.c_int)] * 6,
         "qmc_batch_create": [C.POINTER(vp), i, C.POINTER(vp)],
         "qmc_batch_destroy": [vp],
         "qmc_batch_sweep": [vp, i, vp, vp],
@@ -114,6 +125,8 @@ def _load():
         "qmc_trace_accepts": [vp, i],
         "qmc_get_accept_trace": [vp, vp],
         "qmc_test_skip_stencil_copy": [vp, i],
+        "qmc_check_report": [vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong)],
+        "qmc_test_plant_bad_cell": [vp, i],
         "qmc_dmc_select": [vp, vp, i, i],
         "qmc_dmc_append": [vp, vp, i, i],
         "qmc_load_nlpp": [vp, i, vp, vp, C.c_double],
@@ -131,10 +144,17 @@ def _load():
     lib.qmc_last_cuda_error.restype = C.c_char_p
     lib.qmc_status_string.argtypes = [C.c_int]
     lib.qmc_status_string.restype = C.c_char_p
+    lib.qmc_build_flags.argtypes = []
+    lib.qmc_build_flags.restype = C.c_int
     return lib
 
 
 lib = _load()
+
+
+def build_flags() -> int:
+    """QMC_BUILD_CHECKED when the loaded library is the bounds-checked build, else 0."""
+    return lib.qmc_build_flags()
 
 
 def _check(fn: str, st: int):
@@ -177,7 +197,7 @@ class Crowd:
     def __init__(self, n_up, n_dn, n_orb, n_ions, grid, L, n_walkers, tau, precision="fp64",
                  update="sm", delay_rank=1, n_recompute=0, drift=True, potential=True,
                  seed=14487, stream=None, staging="auto", cta_threads=0, engine="auto",
-                 dmc=False, guard_tol=0.0):
+                 dmc=False, guard_tol=0.0, layout="auto"):
         self.sys = qmc_system_desc(n_up=n_up, n_dn=n_dn, n_orb=n_orb, n_ions=n_ions, grid=grid,
                                    reserved=0, L=L)
         self.run = qmc_run_desc(
@@ -188,7 +208,7 @@ class Crowd:
             potential=int(potential), staging=QMC_STAGING_LDG if staging == "ldg" else QMC_STAGING_AUTO,
             tau=tau, seed=seed, cta_threads=cta_threads,
             engine=QMC_ENGINE_SIMT if engine == "simt" else QMC_ENGINE_AUTO,
-            dmc=int(bool(dmc)), reserved=0, guard_tol=float(guard_tol))
+            dmc=int(bool(dmc)), layout=LAYOUTS[layout], guard_tol=float(guard_tol))
         self.W, self.N, self.n = n_walkers, n_up + n_dn, n_up
         self.capacity = n_walkers
         h = C.c_void_p()
@@ -199,7 +219,7 @@ class Crowd:
     @classmethod
     def from_workload(cls, wl, precision="fp64", update="sm", delay_rank=1, n_walkers=None,
                       stream=None, n_recompute=None, staging="auto", cta_threads=0,
-                      engine="auto", dmc=False, tau=None, guard_tol=0.0):
+                      engine="auto", dmc=False, tau=None, guard_tol=0.0, layout="auto"):
         c = cls(wl.n_up, wl.n_dn, wl.n_orb, wl.n_ions, wl.grid, wl.L,
                 wl.n_walkers if n_walkers is None else n_walkers,
                 wl.tau if tau is None else tau, precision=precision,
@@ -207,7 +227,7 @@ class Crowd:
                 n_recompute=wl.n_recompute if n_recompute is None else n_recompute,
                 drift=wl.drift, potential=wl.potential, seed=wl.seed, stream=stream,
                 staging=staging, cta_threads=cta_threads, engine=engine, dmc=dmc,
-                guard_tol=guard_tol)
+                guard_tol=guard_tol, layout=layout)
         if wl.n_ions:
             c.qmc_load_ions(np.ascontiguousarray(wl.ions, dtype=np.float64))
         if wl.j2_uu is not None:
@@ -324,13 +344,15 @@ class Crowd:
 
     @property
     def kernel_config(self) -> dict:
-        """{'b_in_smem', 'stencil_tma', 'smem_bytes', 'cta_threads', 'tc_flush'} of the
-        move kernel."""
-        v = [C.c_int() for _ in range(5)]
+        """{'b_in_smem', 'stencil_tma', 'smem_bytes', 'cta_threads', 'tc_flush', 'layout'}
+        of the move kernel (layout: 'shared' or 'compact')."""
+        v = [C.c_int() for _ in range(6)]
         _check("qmc_get_kernel_config",
                lib.qmc_get_kernel_config(self.h, *[C.byref(x) for x in v]))
-        return dict(zip(("b_in_smem", "stencil_tma", "smem_bytes", "cta_threads", "tc_flush"),
-                        (x.value for x in v)))
+        d = dict(zip(("b_in_smem", "stencil_tma", "smem_bytes", "cta_threads", "tc_flush"),
+                     (x.value for x in v[:5])))
+        d["layout"] = "compact" if v[5].value == QMC_LAYOUT_COMPACT else "shared"
+        return d
 
     def qmc_dmc_branch(self, e_prev, e_new, e_trial: float):
         """DMC reweighting and branching after a generation (host arrays [W]); returns
@@ -403,6 +425,17 @@ class Crowd:
         """Failure-detection test hook: stencil copies not issued (their waits run out)."""
         _check("qmc_test_skip_stencil_copy",
                lib.qmc_test_skip_stencil_copy(self.h, int(bool(on))))
+
+    def qmc_check_report(self):
+        """(site, value) of the crowd's first failed bounds check since the last report
+        (site 0: none; always 0 outside the bounds-checked build)."""
+        site, val = C.c_int(), C.c_longlong()
+        _check("qmc_check_report", lib.qmc_check_report(self.h, C.byref(site), C.byref(val)))
+        return site.value, val.value
+
+    def qmc_test_plant_bad_cell(self, on: bool):
+        """Checked-build test hook: electron 0's proposals get an out-of-range cell."""
+        _check("qmc_test_plant_bad_cell", lib.qmc_test_plant_bad_cell(self.h, int(bool(on))))
 
     @property
     def walker_count(self) -> int:

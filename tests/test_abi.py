@@ -41,7 +41,7 @@ def test_invalid_arguments_rejected_before_device_use():
     sys_ = Q.qmc_system_desc(n_up=4, n_dn=4, n_orb=4, n_ions=0, grid=8, reserved=0, L=3.0)
     run = Q.qmc_run_desc(n_walkers=0, precision=0, update=0, delay_rank=1, n_recompute=0,
                          drift=1, potential=1, staging=0, tau=0.3, seed=1,
-                         cta_threads=0, engine=0, dmc=0, reserved=0)
+                         cta_threads=0, engine=0, dmc=0, layout=0)
     assert Q.lib.qmc_crowd_create(ctypes.byref(sys_), ctypes.byref(run), None,
                                   ctypes.byref(h)) == 1
     run.n_walkers = 2
