@@ -224,12 +224,14 @@ def coulomb_args(wl):
 
 
 LAYOUT = "auto"  # the move kernel's shared-memory layout (--layout)
+STAGING = "auto"  # how each move's orbital stencil reaches shared memory (--staging)
 
 
 def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0, nlpp=None, coulomb=None):
     from paper_2209_14487_gb300 import qmcgb
     c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
-                                  stream=stream, cta_threads=nt, layout=LAYOUT)
+                                  stream=stream, cta_threads=nt, layout=LAYOUT,
+                                  staging=STAGING)
     if nlpp is not None:
         c.qmc_load_nlpp(*nlpp)
     if coulomb is not None:
@@ -496,8 +498,10 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
     target = max(1, int(round(target_frac * cap)))
     c = qmcgb.Crowd.from_workload(wl, precision="mixed", update=update, delay_rank=k,
                                   stream=stream.cuda_stream, cta_threads=nt, dmc=True,
-                                  layout=LAYOUT)
+                                  layout=LAYOUT, staging=STAGING)
     layout = c.kernel_config["layout"]
+    staging = {0: "per-thread loads", 1: "one TMA copy per move",
+               2: "TMA ring"}[c.kernel_config["stencil_tma"]]
     c.qmc_load_positions(np.ascontiguousarray(wl.positions(crowd_id=crowd_id)))
     c.qmc_recompute()
     e_prev = np.zeros(cap)
@@ -563,6 +567,7 @@ def dmc_path(wl, update, k, steps, warmup, flush_buf, nt=0, target_frac=0.8, fee
             "sweep_ms": [a.elapsed_time(b) for a, b in ev_s], "moves": moves,
             "sizes": sizes, "e_est": e_est_hist, "p_acc": p_acc, "launches": launches,
             "capacity": cap, "target": target, "repairs": repairs, "layout": layout,
+            "staging": staging,
             "recompute_step_ms": rc_ms, "plain_probe_ms": plain_ms}
 
 
@@ -614,6 +619,7 @@ def dmc_main(args, wl, ws, rank, cfg):
                           capacity=r["capacity"], target_walkers=r["target"],
                           precision="mixed", update=f"{update} k={k}",
                           cta_threads=nt or "library", layout=r["layout"],
+                          stencil=r["staging"],
                           parallelism=f"replicas x{ws}")}
     if tune_table is not None:
         out["autotune"] = {"ms_per_generation": tune_table, "chosen": f"{update}:{k}:{nt}"}
@@ -769,6 +775,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="--dmc: timed generations of the FP64 arm")
+    ap.add_argument("--staging", default="auto", choices=["auto", "ldg"],
+                    help="stencil staging (auto: TMA where the library can; ldg: per-thread "
+                         "loads)")
     ap.add_argument("--layout", default="auto", choices=["auto", "shared", "compact"],
                     help="the move kernel's shared-memory layout (auto: the library's pick)")
     ap.add_argument("--equilibrate", type=int, default=200,
@@ -799,8 +808,9 @@ def main():
                          "their own streams")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    global LAYOUT
+    global LAYOUT, STAGING
     LAYOUT = args.layout
+    STAGING = args.staging
 
     from paper_2209_14487_gb300 import workloads
     wl = workloads.WORKLOADS[args.workload]()

@@ -20,7 +20,10 @@ using qmcgb::Params;
 
 namespace qmcgb {
 
-int stencil_tma_bytes(const Params& p, int elem_bytes) { return 64 * p.n_pad * elem_bytes; }
+// bytes of one stencil copy: the whole 4x4x4 x n_pad stencil, or one ring box
+int stencil_tma_bytes(const Params& p, int elem_bytes) {
+  return p.use_tma == 2 ? RING_ORB * 16 * elem_bytes : 64 * p.n_pad * elem_bytes;
+}
 
 size_t move_smem_bytes(const Params& p, int elem_bytes) {
   if (p.nt == 128) return nt128::move_smem_bytes(p, elem_bytes);
@@ -254,7 +257,9 @@ int add_nlpp(qmc_crowd* c) {
 }
 
 // The padded table [GP][GP][GP][n_pad] (x slowest) as a 4-D tensor, innermost first, with
-// a box of one full 4x4x4 stencil: one copy per move lands it in shared memory.
+// a box of one full 4x4x4 stencil (one copy per move lands it in shared memory), or for
+// the ring a box of RING_ORB orbitals x 4 x 4 x 1 (a box is at most 256 elements wide;
+// where it passes n_pad the copy fills zeros).
 bool encode_table_map(qmc_crowd* c) {
   const Params& p = c->p;
   const cuuint64_t es = (cuuint64_t)c->es;
@@ -262,6 +267,10 @@ bool encode_table_map(qmc_crowd* c) {
   cuuint64_t dims[4] = {np, GP, GP, GP};
   cuuint64_t strides[3] = {np * es, GP * np * es, GP * GP * np * es};  // bytes, dims 1..3
   cuuint32_t box[4] = {(cuuint32_t)np, 4, 4, 4};
+  if (p.use_tma == 2) {
+    box[0] = (cuuint32_t)qmcgb::RING_ORB;
+    box[3] = 1;
+  }
   cuuint32_t estr[4] = {1, 1, 1, 1};
   std::memset(&c->tmap, 0, sizeof(c->tmap));
   // the driver's encoder, looked up at run time so the library needs no driver at link
@@ -476,7 +485,10 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   // stencil, the inverse alone, the stencil alone, neither.  A TMA box is at most 256
   // elements wide, so the staged stencil needs n_pad <= 256.
   const int optin = qmcgb::max_smem_optin();
-  const bool tma_ok = run->staging == QMC_STAGING_AUTO && p.n_pad <= 256;
+  // n_pad > 256: the mixed path's ring of smaller boxes (128 or 256 threads, so that the
+  // threads split a box's 256 orbitals evenly)
+  const bool ring_ok = run->precision == QMC_PREC_MIXED && (p.nt == 128 || p.nt == 256);
+  const bool tma_ok = run->staging == QMC_STAGING_AUTO && (p.n_pad <= 256 || ring_ok);
   // The tensor-core flush (mixed delayed path, inverse in global memory, n % 4 == 0) adds
   // a 64 KB operand stage unless it can share the stencil buffer.
   // (its epilogue splits the four TMEM lane quadrants over groups of four warps, and
@@ -505,7 +517,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     for (const auto& pl : plans) {
       if (pl[1] && !tma_ok) continue;
       p.b_in_smem = pl[0];
-      p.use_tma = pl[1];
+      p.use_tma = pl[1] ? (p.n_pad <= 256 ? 1 : 2) : 0;
       p.tc_flush = (tc_ok && !pl[0]) ? 1 : 0;
       p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
       if (fits()) return true;
@@ -514,7 +526,7 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
       for (const auto& pl : plans) {
         if (pl[0] || (pl[1] && !tma_ok)) continue;
         p.b_in_smem = 0;
-        p.use_tma = pl[1];
+        p.use_tma = pl[1] ? (p.n_pad <= 256 ? 1 : 2) : 0;
         p.tc_flush = 0;
         p.stencil_bytes = qmcgb::stencil_tma_bytes(p, es);
         if (fits()) return true;
@@ -621,7 +633,17 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
     delete c;
     return QMC_ERR_CUDA;
   }
-  if (p.use_tma && !encode_table_map(c)) p.use_tma = 0;  // plain loads then
+  if (p.use_tma && !encode_table_map(c)) {  // plain loads then, if they fit
+    p.use_tma = 0;
+    p.stencil_bytes = 0;
+    c->smem = qmcgb::move_smem_bytes(p, c->es);
+    if (qmcgb::max_smem_optin() > 0 && c->smem > (size_t)qmcgb::max_smem_optin()) {
+      free_all(c);
+      if (c->own_stream) cudaStreamDestroy(c->stream);
+      delete c;
+      return QMC_ERR_UNSUPPORTED;
+    }
+  }
   sync_params(c);
   int js = upload_jastrow(c);
   if (js) {

@@ -13,6 +13,10 @@ constexpr int LA_NWARP = LA_NT / 32;
 constexpr int MAX_K = 64;          // largest delay rank
 constexpr int MAX_KNOTS = 64;      // largest radial functor (free coefficients)
 constexpr int PEND_STRIDE = 24;    // doubles of pending-proposal state per walker
+// Ring-staged stencil (n_pad > 256, mixed path): TMA boxes of RING_ORB orbitals x one
+// 4x4 (y, z) plane of the stencil, RING_SLOTS of them in flight per CTA
+constexpr int RING_ORB = 256;
+constexpr int RING_SLOTS = 3;
 
 // pending-proposal slots (doubles)
 enum {
@@ -60,7 +64,8 @@ struct Params {
   int b_in_smem;            // inverse of the moving spin staged in shared memory
   int skip_eloc;            // sweep without the local energy (a recompute comes first)
   int nt;                   // threads per CTA of the move kernel: 128, 160 or 256
-  int use_tma;              // stage each move's 4x4x4 x n_pad stencil with one TMA copy
+  int use_tma;              // 1: each move's 4x4x4 x n_pad stencil by one TMA copy; 2: by
+                            // a ring of TMA copies of RING_ORB orbitals x one x-plane
   int tc_flush;             // delayed windows flushed on the tensor cores (mixed, B global)
   int inc_jastrow;          // mixed Sherman-Morrison sweep: incremental Jastrow grad/lap
   int compact;              // compact shared memory: the delayed window's V rows stay in

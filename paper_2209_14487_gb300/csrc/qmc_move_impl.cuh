@@ -118,15 +118,19 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   Lay L{};
   size_t o = 0;
   L.scal = o; o += al16(sizeof(Scal<T>));
-  L.bar = o; o += 16;
-  L.stc = o; o += p.use_tma ? al16((size_t)p.stencil_bytes + 128) : 0;  // +128: alignment slack
+  L.bar = o; o += 32;  // stencil copies (ring slot 0), tensor-core MMAs, ring slots 1 and 2
+  // +128: alignment slack
+  L.stc = o; o += p.use_tma == 1 ? al16((size_t)p.stencil_bytes + 128) : 0;
+  // the ring's boxes take the place of the partial sums (its consumer combines the four
+  // x-planes in registers)
+  const size_t part_bytes = p.use_tma == 2 ? al16((size_t)RING_SLOTS * p.stencil_bytes + 128)
+                                           : al16((size_t)16 * p.n_pad * es);
   // tensor-core flush staging: shares the stencil buffer (unused during a flush) when that
-  // is large enough, else the move's phi', partial sums and column (dead during a flush,
-  // see accept_update) when those are, else a buffer of its own
+  // is large enough, else the move's phi', partial sums (or ring) and column (dead during
+  // a flush, see accept_update) when those are, else a buffer of its own
   L.tcs = L.stc;
-  const size_t move_bufs =
-      al16((size_t)5 * p.n_pad * es) + al16((size_t)16 * p.n_pad * es) + al16((size_t)p.n_pad * es);
-  const bool need_stage = p.tc_flush && !(p.use_tma && p.stencil_bytes >= TC_STAGE_BYTES);
+  const size_t move_bufs = al16((size_t)5 * p.n_pad * es) + part_bytes + al16((size_t)p.n_pad * es);
+  const bool need_stage = p.tc_flush && !(p.use_tma == 1 && p.stencil_bytes >= TC_STAGE_BYTES);
   const bool over_move = need_stage && es == 4 && move_bufs >= (size_t)TC_STAGE_BYTES + 128;
   if (need_stage && !over_move) {
     L.tcs = o;
@@ -140,7 +144,7 @@ __host__ __device__ inline Lay make_lay(const Params& p) {
   L.jc = o; o += al16((size_t)3 * (MAX_KNOTS + 3) * es);  // any Jastrow the crowd loads later
   L.jgl = o; o += p.inc_jastrow ? al16((size_t)p.N * 4 * es) : 0;
   L.phi = o; o += al16((size_t)5 * p.n_pad * es);
-  L.part = o; o += al16((size_t)16 * p.n_pad * es);
+  L.part = o; o += part_bytes;
   L.col = o; o += al16((size_t)p.n_pad * es);
   L.col2 = o; o += p.inc_jastrow ? al16((size_t)p.n_pad * es) : 0;  // the next move's column
   if (over_move) L.tcs = L.phi;
@@ -1033,6 +1037,24 @@ __device__ __forceinline__ void make_proposal(const Ctx<T>& c, int i, const T* F
   pr.logGf = -gf / (T(2) * tau);
 }
 
+// Ring-staged stencil (n_pad > 256): box s of a move holds orbitals
+// [RING_ORB (s / 4), RING_ORB (s / 4 + 1)) of the stencil's x-plane s % 4, as [y][z][orbital]
+// (4 x 4 x RING_ORB); it lands in slot s % RING_SLOTS on that slot's mbarrier.
+template <typename T>
+__device__ __forceinline__ uint64_t* ring_bar(const Ctx<T>& c, int slot) {
+  return slot == 0 ? c.bar : c.bar + 1 + slot;  // c.bar[1] belongs to the tensor cores
+}
+
+template <typename T>
+__device__ __forceinline__ void ring_issue(const Ctx<T>& c, const Prop<T>& pr, int s) {
+  const int slot = s % RING_SLOTS;
+  uint64_t* bar = ring_bar(c, slot);
+  fence_proxy_async_smem();  // the slot's previous box was read through the generic proxy
+  mbar_arrive_expect_tx(bar, (uint32_t)c.p.stencil_bytes);
+  tma_load_4d(c.stc + (size_t)slot * RING_ORB * 16, c.tmap, (s >> 2) * RING_ORB, pr.cell[2],
+              pr.cell[1], pr.cell[0] + (s & 3), bar);
+}
+
 // Ratio Psi(R')/Psi(R) and grad_i log Psi(R') (Alg. 1 lines 7-8): Jastrow difference over
 // all partners, tricubic orbital VGL at r', determinant ratio phi'.col.  Every thread
 // gets rhoD and dU; rho and Fp = grad log Psi(R') on every thread in the mixed path and
@@ -1044,13 +1066,19 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   const int n = p.n, n_pad = p.n_pad, GP = p.GP;
   const T* table = (const T*)p.table;
   T cf[16];
-  const bool tma = p.use_tma;
+  const bool tma = p.use_tma == 1;
+  // the ring serves the mixed path with 128 or 256 threads (the host enables it only there)
+  const bool ring = IsMixed<T>::value && (NT == 128 || NT == 256) && p.use_tma == 2;
+  const int nslab = 4 * ((n + RING_ORB - 1) / RING_ORB);
   if (tma) {
     if (c.tid == 0 && !p.test_no_copy) {  // the whole 4x4x4 x n_pad stencil in one copy
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(c.bar, (uint32_t)p.stencil_bytes);
       tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
     }
+  } else if (ring) {
+    if (c.tid == 0 && !p.test_no_copy)  // the first boxes fly during the Jastrow terms
+      for (int s = 0; s < RING_SLOTS && s < nslab; ++s) ring_issue(c, pr, s);
   } else if (c.nit > 0) {
     stencil_load(table, GP, n_pad, pr.cell[0], pr.cell[1], pr.cell[2], c.itj[0], c.ita[0], cf);
   }
@@ -1099,6 +1127,95 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     __syncthreads();  // weights in shared memory
     wts = c.sc->wts;
   }
+  if constexpr (IsMixed<T>::value && (NT == 128 || NT == 256)) {
+    if (ring) {
+      // each box as it lands: every thread reduces its RING_ORB / NT orbitals' 4 x 4 (y, z)
+      // values and adds the x-plane's share of value, gradient and Laplacian (the
+      // x-weights of stencil_combine, in the same order); after plane 3 of a chunk its
+      // orbitals' rows are final.  Then every thread is past the slot and thread 0
+      // refills it with the box RING_SLOTS ahead.
+      constexpr int NJ = RING_ORB / NT;
+      T wx[12];
+      basis12(pr.t[0], wx);
+      const T dinv = c.k.dgrid;
+      T acc[NJ][5];
+#pragma unroll
+      for (int u = 0; u < NJ; ++u)
+#pragma unroll
+        for (int r = 0; r < 5; ++r) acc[u][r] = T(0);
+      const uint32_t ph0 = c.tma_phase;
+      bool ok = true;
+      int s = 0;
+      for (; s < nslab; ++s) {
+        const int slot = s % RING_SLOTS, a = s & 3;
+        ok = mbar_wait_bounded(ring_bar(c, slot), ((ph0 >> slot) ^ (uint32_t)(s / RING_SLOTS)) & 1u);
+        if (ok) {
+          const T* sl = c.stc + (size_t)slot * RING_ORB * 16 + c.tid;
+          // plane a's x-weights (value, first, second derivative) by selects: a register
+          // array indexed at run time would live in local memory
+          T xa = wx[0], xd = wx[4], xl = wx[8];
+#pragma unroll
+          for (int q = 1; q < 4; ++q)
+            if (a == q) {
+              xa = wx[q];
+              xd = wx[4 + q];
+              xl = wx[8 + q];
+            }
+#pragma unroll
+          for (int u = 0; u < NJ; ++u) {
+#pragma unroll
+            for (int bc = 0; bc < 16; ++bc) cf[bc] = sl[bc * RING_ORB + u * NT];
+            T o4[4];
+            stencil_reduce(cf, wts, o4);
+            acc[u][0] += xa * o4[0];
+            acc[u][1] += xd * o4[0];
+            acc[u][2] += xa * o4[1];
+            acc[u][3] += xa * o4[2];
+            acc[u][4] += xl * o4[0] + xa * o4[3];
+          }
+          if (a == 3) {
+#pragma unroll
+            for (int u = 0; u < NJ; ++u) {
+              const int j = (s >> 2) * RING_ORB + c.tid + u * NT;
+              if (j < n) {
+                const T o5[5] = {acc[u][0], acc[u][1] * dinv, acc[u][2] * dinv, acc[u][3] * dinv,
+                                 acc[u][4] * dinv * dinv};
+#pragma unroll
+                for (int q = 0; q < 5; ++q) c.phi[q * n_pad + j] = o5[q];
+                const T cj = c.col[j];
+                v[0] += o5[0] * cj;
+                v[1] += o5[1] * cj;
+                v[2] += o5[2] * cj;
+                v[3] += o5[3] * cj;
+              }
+#pragma unroll
+              for (int r = 0; r < 5; ++r) acc[u][r] = T(0);
+            }
+          }
+        }
+        if (__syncthreads_or(!ok)) break;  // uniform: every thread leaves together
+        if (c.tid == 0 && s + RING_SLOTS < nslab && !p.test_no_copy) ring_issue(c, pr, s + RING_SLOTS);
+      }
+      if (s < nslab) {
+        // a box that never landed: record it, give every box still in flight one more
+        // bounded wait, and leave the kernel
+        if (c.tid == 0) atomicOr(p.status, ST_TIMEOUT);
+        for (int t = s; t < nslab && t < s + RING_SLOTS; ++t) {
+          const int slot = t % RING_SLOTS;
+          mbar_wait_bounded(ring_bar(c, slot), ((ph0 >> slot) ^ (uint32_t)(t / RING_SLOTS)) & 1u);
+        }
+        return false;
+      }
+      // each slot's phase after this move's boxes
+      uint32_t ph = ph0;
+      for (int slot = 0; slot < RING_SLOTS; ++slot) {
+        const int uses = nslab / RING_SLOTS + (slot < nslab % RING_SLOTS ? 1 : 0);
+        if (uses & 1) ph ^= 1u << slot;
+      }
+      c.tma_phase = ph;
+    }
+  }
+  if (!ring) {
   bool ok = true;
   if (tma) {
     ok = mbar_wait_bounded(c.bar, c.tma_phase);
@@ -1208,6 +1325,7 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     v[2] += o5[2] * cj;
     v[3] += o5[3] * cj;
   }
+  }  // !ring
   block_allreduce8<NWARP>(v, c.red1);
   rs.rhoD = v[0];
   rs.dU = v[4];
@@ -1639,7 +1757,7 @@ struct IncOut {
 // after this move (`pf`: that electron's dA entries for orbital j = tid).
 template <typename T>
 __device__ __forceinline__ void stencil_issue(Ctx<T>& c, const Prop<T>& pr) {
-  if (c.p.use_tma && c.tid == 0 && !c.p.test_no_copy) {  // the whole stencil in one copy
+  if (c.p.use_tma == 1 && c.tid == 0 && !c.p.test_no_copy) {  // the whole stencil in one copy
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(c.bar, (uint32_t)c.p.stencil_bytes);
     tma_load_4d(c.stc, c.tmap, 0, pr.cell[2], pr.cell[1], pr.cell[0], c.bar);
@@ -1703,7 +1821,7 @@ __device__ bool spo_inc(Ctx<T>& c, int i, int pp, const Prop<T>& pr, Res<T>& rs,
   const Params& p = c.p;
   const int n = p.n, n_pad = p.n_pad, GP = p.GP;
   const T* table = (const T*)p.table;
-  const bool tma = p.use_tma;
+  const bool tma = p.use_tma == 1;  // the ring (n_pad > 256) never meets this path
   T cf[16];
   T wreg[36];
   basis12(pr.t[1], wreg + 12);
@@ -2213,12 +2331,18 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     // uniform per CTA: the whole walker is skipped
     if (!QMC_CHECKP(p, w >= 0 && w < p.W, CK_WALKER, w)) return;
     if (!QMC_CHECKP(p, lay.total <= dyn, CK_SMEM, lay.total)) return;
-    if (p.use_tma &&
-        !QMC_CHECKP(p, p.stencil_bytes == 64 * n_pad * (int)sizeof(T) &&
-                           ((lay.stc + 127) & ~(size_t)127) + (size_t)p.stencil_bytes <=
-                               lay.stc + al16((size_t)p.stencil_bytes + 128),
-                    CK_STENCIL, p.stencil_bytes))
-      return;
+    if (p.use_tma) {
+      // the copy's size, and its 128-byte aligned buffer (all ring slots) inside the room
+      // the layout gave it
+      const bool ring = p.use_tma == 2;
+      const size_t sb = (ring ? (size_t)RING_SLOTS : 1) * (size_t)p.stencil_bytes;
+      const uintptr_t base = reinterpret_cast<uintptr_t>(smem + (ring ? lay.part : lay.stc));
+      const uintptr_t a = (base + 127) & ~(uintptr_t)127;
+      const int want = (ring ? RING_ORB * 16 : 64 * n_pad) * (int)sizeof(T);
+      if (!QMC_CHECKP(p, p.stencil_bytes == want && a + sb <= base + al16(sb + 128), CK_STENCIL,
+                      p.stencil_bytes))
+        return;
+    }
   }
 #endif
   Ctx<T> c{p};
@@ -2260,7 +2384,8 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
   c.yb = (T*)(smem + lay.yb);
   c.rows = (T*)p.rows + (size_t)w * N * 5 * n_pad;
   c.bar = (uint64_t*)(smem + lay.bar);
-  c.stc = (T*)((reinterpret_cast<uintptr_t>(smem + lay.stc) + 127) & ~(uintptr_t)127);
+  c.stc = (T*)((reinterpret_cast<uintptr_t>(smem + (p.use_tma == 2 ? lay.part : lay.stc)) + 127) &
+               ~(uintptr_t)127);
   c.tmap = tmap;
   c.tma_phase = 0;
   c.mma_phase = 0;
@@ -2304,6 +2429,10 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
     if (p.use_tma || p.tc_flush) {
       mbar_init(c.bar, 1);
       mbar_init(c.bar + 1, 1);
+      if (p.use_tma == 2) {
+        mbar_init(c.bar + 2, 1);
+        mbar_init(c.bar + 3, 1);
+      }
       mbar_fence_init();
     }
     sc->accept = 0;

@@ -407,6 +407,58 @@ def _pw1024():
                                 n_gen=1, tau=0.5, n_recompute=0, j2_knots=10)
 
 
+def _ring300():
+    # n = 300 per spin (n_pad 304): two ring boxes per x-plane, the second reaching past
+    # the table's orbitals (the copy fills zeros there)
+    return wl_mod.make_workload("ring300", n_el=600, n_orb=300, grid=24, n_walkers=3, n_gen=1,
+                                n_ions=6, tau=0.5, n_recompute=0, j1_knots=6, j2_knots=10)
+
+
+@pytest.mark.parametrize("make,nt,update,k", [(_pw1024, 128, "delayed", 16),
+                                              (_pw1024, 256, "sm", 1),
+                                              (_ring300, 128, "delayed", 8)])
+def test_tma_ring_matches_plain_loads(Q, oracle_lib, make, nt, update, k):
+    """n > 256: the stencil arrives as a ring of TMA boxes (256 orbitals x one x-plane,
+    three in flight) and each box is reduced as it lands.  Against per-thread loads of the
+    same coefficients: the proposals' log-ratios and drifts agree to FP32 rounding, a
+    generation follows the same trajectory, and E_L matches the oracle."""
+    wl = make()
+    W = wl.n_walkers
+    R = np.ascontiguousarray(wl.positions(n_walkers=W))
+    rng = np.random.default_rng(7)
+    iels = (0, wl.n_up - 1, wl.n_up, wl.n_el - 1)
+    rnews = [np.ascontiguousarray(np.mod(R[:, iel] + rng.normal(0, 0.3, (W, 3)), wl.L))
+             for iel in iels]
+    out = {}
+    for staging in ("auto", "ldg"):
+        c = Q.Crowd.from_workload(wl, precision="mixed", n_walkers=W, staging=staging,
+                                  update=update, delay_rank=k, cta_threads=nt)
+        assert c.kernel_config["stencil_tma"] == (2 if staging == "auto" else 0), c.kernel_config
+        c.qmc_load_positions(R)
+        c.qmc_recompute()
+        lrs = []
+        for iel, rnew in zip(iels, rnews):
+            lr = np.zeros(W)
+            grad = np.zeros((W, 3))
+            c.qmc_propose_move_batch(iel, rnew, None, grad, lr)
+            c.qmc_accept_reject_batch(iel, np.zeros(W, dtype=np.uint8))
+            lrs.append((lr, grad))
+        e = np.zeros((1, W))
+        st = c.qmc_sweep(1, e)
+        out[staging] = (lrs, c.qmc_get_positions(), e, st.n_accept)
+        c.close()
+    a, b = out["auto"], out["ldg"]
+    for (la, ga), (lb, gb) in zip(a[0], b[0]):
+        assert np.allclose(la, lb, rtol=1e-5, atol=1e-5), (la, lb)
+        assert np.allclose(ga, gb, rtol=1e-4, atol=1e-4), (ga, gb)
+    same = np.all(a[1] == b[1], axis=(1, 2))
+    assert same.sum() >= W - 1, same
+    osys = oracle_lib.OracleSystem(wl)
+    for w in range(W):
+        e_ref = osys.local_energy(a[1][w])[0]
+        assert abs(a[2][0, w] - e_ref) < 1e-3 * max(1.0, abs(e_ref)), (w, a[2][0, w], e_ref)
+
+
 @pytest.mark.parametrize("make,nt", [(wl_mod.pw512, 256), (wl_mod.pw512, 128), (_pw1024, 128)])
 def test_tensor_core_flush_matches_simt_flush(Q, oracle_lib, make, nt):
     """Inverse in global memory, delayed rank 16: windows flushed by tcgen05 3xTF32 MMAs
