@@ -230,8 +230,9 @@ STAGING = "auto"  # how each move's orbital stencil reaches shared memory (--sta
 def make_crowd(wl, precision, update, k, stream, crowd_id, nt=0, nlpp=None, coulomb=None):
     from paper_2209_14487_gb300 import qmcgb
     c = qmcgb.Crowd.from_workload(wl, precision=precision, update=update, delay_rank=k,
-                                  stream=stream, cta_threads=nt, layout=LAYOUT,
-                                  staging=STAGING)
+                                  stream=stream, cta_threads=nt,
+                                  layout=LAYOUT if precision == "mixed" else "auto",
+                                  staging=STAGING if precision == "mixed" else "auto")
     if nlpp is not None:
         c.qmc_load_nlpp(*nlpp)
     if coulomb is not None:
@@ -296,11 +297,18 @@ def time_path(wl, precision, update, k, steps, warmup, crowd_id, flush_buf, nt=0
         c.generation = g_next
     chain = None
     if energy is not None:
-        n_eq, n_e = energy
+        n_eq, n_e, snap = energy
         c.qmc_sweep(n_eq, None, stats=False)
         ech = torch.zeros((n_e, wl.n_walkers), dtype=torch.float64, device="cuda")
-        st = c.qmc_sweep(n_e, ech, stats=True)
-        chain = {"eloc": ech.cpu().numpy(), "repairs": getattr(st, "n_repair", 0)}
+        snaps, repairs_chain = [], 0
+        step = snap if snap else n_e
+        for g0 in range(0, n_e, step):
+            g1 = min(n_e, g0 + step)
+            st = c.qmc_sweep(g1 - g0, ech[g0:g1], stats=True)
+            repairs_chain += getattr(st, "n_repair", 0)
+            if snap:  # the chain's configuration and its E_L after generation g1 - 1
+                snaps.append((c.qmc_get_positions(), ech[g1 - 1].cpu().numpy()))
+        chain = {"eloc": ech.cpu().numpy(), "repairs": repairs_chain, "snaps": snaps}
     c.close()
     torch.cuda.set_stream(torch.cuda.default_stream())
     return {"ms": ms, "plain_ms": plain, "eloc": e, "p_acc": p_acc, "launches": launches,
@@ -668,6 +676,28 @@ def dmc_main(args, wl, ws, rank, cfg):
         print(json.dumps(out))
 
 
+def eloc_error(wl, snaps):
+    """The mixed path's E_L error where the sampling plays no part: at configurations of
+    its own chain (one per energy block), E_L(mixed) - E_L(FP64 path: FP64 recompute of
+    the same positions, then E_L)."""
+    from paper_2209_14487_gb300 import qmcgb
+    c = qmcgb.Crowd.from_workload(wl, precision="fp64")
+    d = []
+    for R, el in snaps:
+        c.qmc_load_positions(np.ascontiguousarray(R))
+        c.qmc_recompute()
+        e64 = np.zeros(wl.n_walkers)
+        c.qmc_local_energy_batch(e64)
+        d.append(el - e64)
+    c.close()
+    d = np.concatenate(d)
+    return {"samples": int(d.size), "mean": float(d.mean()),
+            "sem": float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else None,
+            "rms": float(np.sqrt((d * d).mean())), "max_abs": float(np.abs(d).max()),
+            "note": "E_L(mixed) - E_L(fp64) at the mixed chain's own configurations, one "
+                    "per block: the mixed path's energy error without the sampling noise"}
+
+
 def energy_stats(e: np.ndarray, block: int = 10):
     """Mean of E_L [generations][walkers] and its error from blocks of `block` generations
     (crowd averages per generation, then block means)."""
@@ -903,21 +933,27 @@ def main():
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
 
     tune_table = None
+    plan_table = None
     if update == "auto":
         from paper_2209_14487_gb300 import autotune
         update, k, tuned_nt, tune_table = autotune.tune(wl, "mixed")
         if not args.cta_threads:
             args.cta_threads = tuned_nt
+        if args.staging == "auto" and args.layout == "auto":
+            STAGING, LAYOUT, plan_table = autotune.tune_plan(wl, "mixed", update, k,
+                                                             args.cta_threads)
     barrier(ws)
     torch.cuda.synchronize()
-    energy = (args.equilibrate, args.energy_gens) if args.energy_gens > 0 else None
+    energy = ((args.equilibrate, args.energy_gens, args.energy_block)
+              if args.energy_gens > 0 else None)
     with ClockSampler(uuid) as clk:
         mixed = time_path(wl, "mixed", update, k, args.steps, args.warmup, rank, flush,
                           args.cta_threads, energy=energy)
         fp64 = None
         if not args.no_fp64:
             fp64 = time_path(wl, "fp64", "sm", 1, args.steps, args.warmup, rank, flush,
-                             args.cta_threads, energy=energy)
+                             args.cta_threads,
+                             energy=None if energy is None else energy[:2] + (0,))
     torch.cuda.synchronize()
     barrier(ws)
 
@@ -936,6 +972,9 @@ def main():
     if tune_table is not None:
         out["autotune"] = {"ms_per_generation": tune_table,
                            "chosen": f"{update}:{k}:{args.cta_threads}"}
+        if plan_table is not None:
+            out["autotune"]["plan_ms_per_generation"] = plan_table
+            out["autotune"]["plan"] = f"staging={STAGING} layout={LAYOUT}"
     out["recompute"] = {
         "every": wl.n_recompute,
         "recompute_ms": extra_mixed,
@@ -954,6 +993,8 @@ def main():
                          "generations": args.energy_gens, "block_generations": blk,
                          "mixed": {"mean": e_m, "sigma": s_m,
                                    "guard_repairs": mixed["chain"]["repairs"]}}
+        if not args.no_fp64 and mixed["chain"]["snaps"]:
+            out["energy"]["eloc_error_same_configs"] = eloc_error(wl, mixed["chain"]["snaps"])
     if fp64 is not None:
         ms64, _ = amortised(fp64, wl.n_recompute)
         v64 = aggregate_value(moves_step * args.steps, sum(ms64) / 1000.0, ws)

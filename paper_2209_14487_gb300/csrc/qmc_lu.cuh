@@ -81,10 +81,13 @@ __device__ bool lu_invert_cta(double* __restrict__ LU, double* __restrict__ X, i
     }
     for (int i = k + 1 + tid; i < n; i += NTH) LU[(size_t)i * n + k] /= akk;
     __syncthreads();
-    const int m = n - k - 1;
-    for (int e = tid; e < m * m; e += NTH) {
-      const int i = k + 1 + e / m, j = k + 1 + (e - (e / m) * m);
-      LU[(size_t)i * n + j] -= LU[(size_t)i * n + k] * LU[(size_t)k * n + j];
+    // rank-1 update of the trailing block: rows over warps, columns over lanes (row k of
+    // U is read by every warp, from L1)
+    for (int i = k + 1 + warp; i < n; i += NTH / 32) {
+      const double lik = LU[(size_t)i * n + k];
+      double* ri = LU + (size_t)i * n;
+      const double* rk = LU + (size_t)k * n;
+      for (int j = k + 1 + lane; j < n; j += 32) ri[j] -= lik * rk[j];
     }
     __syncthreads();
   }
@@ -101,16 +104,35 @@ __device__ bool lu_invert_cta(double* __restrict__ LU, double* __restrict__ X, i
       if (pos == k) pos = pk;
       else if (pos == pk) pos = k;
     }
-    for (int i = 0; i < n; ++i) X[(size_t)i * n + col] = (i == pos) ? 1.0 : 0.0;
-    for (int i = pos + 1; i < n; ++i) {
-      double acc = 0.0;
-      for (int j = pos; j < i; ++j) acc -= LU[(size_t)i * n + j] * X[(size_t)j * n + col];
-      X[(size_t)i * n + col] = acc;
+    // forward substitution L y = P e_col: y is 0 above pos and 1 at pos; every lane of a
+    // warp runs the same rows (over the zeros above its own pos, which add nothing), with
+    // four partial sums so that the FP64 products do not wait on one another
+    for (int i = 0; i < n; ++i) {
+      const double* li = LU + (size_t)i * n;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = 0;
+      for (; j + 4 <= i; j += 4) {
+        a0 += li[j] * X[(size_t)j * n + col];
+        a1 += li[j + 1] * X[(size_t)(j + 1) * n + col];
+        a2 += li[j + 2] * X[(size_t)(j + 2) * n + col];
+        a3 += li[j + 3] * X[(size_t)(j + 3) * n + col];
+      }
+      for (; j < i; ++j) a0 += li[j] * X[(size_t)j * n + col];
+      X[(size_t)i * n + col] = i < pos ? 0.0 : (i == pos ? 1.0 : -((a0 + a1) + (a2 + a3)));
     }
+    // back substitution U x = y
     for (int i = n - 1; i >= 0; --i) {
-      double acc = X[(size_t)i * n + col];
-      for (int j = i + 1; j < n; ++j) acc -= LU[(size_t)i * n + j] * X[(size_t)j * n + col];
-      X[(size_t)i * n + col] = acc / LU[(size_t)i * n + i];
+      const double* ui = LU + (size_t)i * n;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = i + 1;
+      for (; j + 4 <= n; j += 4) {
+        a0 += ui[j] * X[(size_t)j * n + col];
+        a1 += ui[j + 1] * X[(size_t)(j + 1) * n + col];
+        a2 += ui[j + 2] * X[(size_t)(j + 2) * n + col];
+        a3 += ui[j + 3] * X[(size_t)(j + 3) * n + col];
+      }
+      for (; j < n; ++j) a0 += ui[j] * X[(size_t)j * n + col];
+      X[(size_t)i * n + col] = (X[(size_t)i * n + col] - ((a0 + a1) + (a2 + a3))) / ui[i];
     }
   }
   __syncthreads();
