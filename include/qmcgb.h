@@ -92,7 +92,9 @@ typedef struct qmc_run_desc {
                      * 2: D = F (unlimited); 0: no drift (plain Metropolis)             */
   int potential;    /* 1: add the model potential to E_L                              */
   int staging;      /* QMC_STAGING_AUTO (0): each move's 4x4x4 x n orbital stencil is  *
-                     * copied to shared memory with one TMA tensor copy when it fits;  *
+                     * copied to shared memory with one TMA tensor copy when it fits   *
+                     * (n_pad <= 256), else in the mixed path with 128 threads by a    *
+                     * ring of TMA boxes (256 orbitals x one x-plane, three in flight);*
                      * QMC_STAGING_LDG: the stencil is read with per-thread loads      */
   double tau;       /* time step                                                      */
   uint64_t seed;    /* Philox key: (low 32 bits, walker ^ high 32 bits)               */
@@ -209,7 +211,8 @@ int qmc_set_generation(qmc_crowd* crowd, uint32_t gen);
 int qmc_get_launch_count(qmc_crowd* crowd, unsigned long long* count);
 /* The move kernel's configuration, chosen at creation from the shared memory a CTA may
  * use: 1 in *b_in_smem when the moving spin's inverse is staged in shared memory, 1 in
- * *stencil_tma when each move's orbital stencil arrives by TMA, the kernel's dynamic
+ * *stencil_tma when each move's orbital stencil arrives by one TMA copy (2: by the ring of
+ * TMA boxes, 0: by per-thread loads), the kernel's dynamic
  * shared memory in bytes, its threads per CTA, 1 in *tc_flush when delayed windows
  * are flushed on the tensor cores, and the layout taken (QMC_LAYOUT_SHARED or
  * QMC_LAYOUT_COMPACT).  Any output pointer may be NULL.  Errors: INVALID_ARG. */

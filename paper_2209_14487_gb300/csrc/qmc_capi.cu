@@ -485,9 +485,10 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   // stencil, the inverse alone, the stencil alone, neither.  A TMA box is at most 256
   // elements wide, so the staged stencil needs n_pad <= 256.
   const int optin = qmcgb::max_smem_optin();
-  // n_pad > 256: the mixed path's ring of smaller boxes (128 or 256 threads, so that the
-  // threads split a box's 256 orbitals evenly)
-  const bool ring_ok = run->precision == QMC_PREC_MIXED && (p.nt == 128 || p.nt == 256);
+  // n_pad > 256: the mixed path's ring of smaller boxes (128 threads: two orbitals of each
+  // box per thread; the wider kernels are built without the ring's code, which cost them
+  // registers)
+  const bool ring_ok = run->precision == QMC_PREC_MIXED && p.nt == 128;
   const bool tma_ok = run->staging == QMC_STAGING_AUTO && (p.n_pad <= 256 || ring_ok);
   // The tensor-core flush (mixed delayed path, inverse in global memory, n % 4 == 0) adds
   // a 64 KB operand stage unless it can share the stencil buffer.
@@ -560,6 +561,12 @@ int qmc_crowd_create(const qmc_system_desc* sys, const qmc_run_desc* run, void* 
   if (!placed) {
     delete c;
     return QMC_ERR_UNSUPPORTED;
+  }
+  // the incremental sweep pipelines proposals and reads the draw table the compact layout
+  // leaves out: a compact crowd takes the plain sweep (and its smaller layout)
+  if (p.compact && p.inc_jastrow) {
+    p.inc_jastrow = 0;
+    smem = qmcgb::move_smem_bytes(p, es);
   }
   // TMEM: a flush holds 128 of the SM's 512 columns while it runs; a CTA whose
   // allocation finds them taken waits for another CTA's flush to end

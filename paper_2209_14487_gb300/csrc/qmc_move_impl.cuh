@@ -70,6 +70,7 @@ struct Scal {
   int accept, m;
   uint32_t tmem;  // TMEM base address of the tensor-core flush
   T wts[48];
+  T chi[4];       // compact layout: the current move's Gaussian draws
 };
 
 // Constants of the crowd in the path's precision, converted once per kernel (a double to
@@ -1067,8 +1068,9 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
   const T* table = (const T*)p.table;
   T cf[16];
   const bool tma = p.use_tma == 1;
-  // the ring serves the mixed path with 128 or 256 threads (the host enables it only there)
-  const bool ring = IsMixed<T>::value && (NT == 128 || NT == 256) && p.use_tma == 2;
+  // the ring serves the mixed path with 128 threads (the host enables it only there; the
+  // other widths' kernels are compiled without it)
+  const bool ring = IsMixed<T>::value && NT == 128 && p.use_tma == 2;
   const int nslab = 4 * ((n + RING_ORB - 1) / RING_ORB);
   if (tma) {
     if (c.tid == 0 && !p.test_no_copy) {  // the whole 4x4x4 x n_pad stencil in one copy
@@ -1127,7 +1129,7 @@ __device__ bool ratio_grad(Ctx<T>& c, int i, const Prop<T>& pr, const T* uo, boo
     __syncthreads();  // weights in shared memory
     wts = c.sc->wts;
   }
-  if constexpr (IsMixed<T>::value && (NT == 128 || NT == 256)) {
+  if constexpr (IsMixed<T>::value && NT == 128) {
     if (ring) {
       // each box as it lands: every thread reduces its RING_ORB / NT orbitals' 4 x 4 (y, z)
       // values and adds the x-plane's share of value, gradient and Laplacian (the
@@ -2259,27 +2261,20 @@ __device__ __forceinline__ void prefetch_grad_rows(const Ctx<T>& c, int i, T* pf
   }
 }
 
-// The Gaussian draws chi of move i and its acceptance uniform: read from the sweep's
-// table in shared memory, or (compact layout) computed from the same Philox words here.
+// The Gaussian draws chi of move i (in shared memory: the proposal indexes them by lane)
+// and its acceptance uniform: from the sweep's table, or (compact layout) computed from the
+// same Philox words here, every thread writing the same values to one shared slot (all
+// threads are at the same move: barriers separate consecutive proposals on this path).
+// The incremental sweep, which pipelines proposals, never runs in the compact layout.
 template <typename T>
-struct Chi3 {
-  T v[3];
-};
-template <typename T>
-__device__ __forceinline__ Chi3<T> chi_of(const Ctx<T>& c, int i) {
-  Chi3<T> r;
-  if (c.p.compact) {
-    T d4[4];
-    draws_t<T>(c.p.seed, (uint32_t)c.w, c.p.gen, (uint32_t)i, d4);
-    r.v[0] = d4[0];
-    r.v[1] = d4[1];
-    r.v[2] = d4[2];
-  } else {
-    r.v[0] = c.dchi[3 * i];
-    r.v[1] = c.dchi[3 * i + 1];
-    r.v[2] = c.dchi[3 * i + 2];
-  }
-  return r;
+__device__ __forceinline__ const T* chi_of(const Ctx<T>& c, int i) {
+  if (!c.p.compact) return c.dchi + 3 * i;
+  T d4[4];
+  draws_t<T>(c.p.seed, (uint32_t)c.w, c.p.gen, (uint32_t)i, d4);
+  c.sc->chi[0] = d4[0];
+  c.sc->chi[1] = d4[1];
+  c.sc->chi[2] = d4[2];
+  return c.sc->chi;
 }
 template <typename T>
 __device__ __forceinline__ T u_of(const Ctx<T>& c, int i) {
@@ -2499,7 +2494,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
           }
           bool nxt = p.drift && n > 1;
           if (nxt) prefetch_grad_rows(c, i + 1, pf);
-          shared_proposal(c, i, F, chi_of(c, i).v, nullptr, pr);
+          shared_proposal(c, i, F, c.dchi + 3 * i, nullptr, pr);
           stencil_issue(c, pr);
           jas_inc(c, i, pr, jv, io);
           for (int pp = 0; pp < n; ++pp) {
@@ -2509,7 +2504,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
               c.failed = true;
               break;
             }
-            const int acc = metropolis(p, c.k, pr, rs, u_of(c, i), w, i);
+            const int acc = metropolis(p, c.k, pr, rs, c.du[i], w, i);
             nacc += acc;
             if (p.accept_trace && c.tid == 0) p.accept_trace[(size_t)w * N + i] = (uint8_t)acc;
             if (acc) {
@@ -2530,7 +2525,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
                 for (int k = 0; k < 3; ++k) F[k] = det[k] - c.jgl[4 * i1 + k];
               nxt = p.drift && pp + 2 < n;
               if (nxt) prefetch_grad_rows(c, i1 + 1, pf);
-              shared_proposal(c, i1, F, chi_of(c, i1).v, nullptr, pr);
+              shared_proposal(c, i1, F, c.dchi + 3 * i1, nullptr, pr);
               stencil_issue(c, pr);
               jas_inc(c, i1, pr, jv, io);
             }
@@ -2562,7 +2557,7 @@ __device__ __forceinline__ void move_body(const Params& p, const int w, const CU
         compute_column(c, pp);
         if (p.drift) eval_grad(c, i, pf, pf_ok, uo, F);
         if (pf_ok) prefetch_grad_rows(c, i + 1, pf);  // row i+1 is not touched by move i
-        shared_proposal(c, i, F, chi_of(c, i).v, nullptr, pr);
+        shared_proposal(c, i, F, chi_of(c, i), nullptr, pr);
         // false only when a stencil copy timed out (status set; uniform over the CTA)
         if (!ratio_grad(c, i, pr, uo, cache_ok, rs)) {
           c.failed = true;

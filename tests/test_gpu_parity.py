@@ -415,11 +415,11 @@ def _ring300():
 
 
 @pytest.mark.parametrize("make,nt,update,k", [(_pw1024, 128, "delayed", 16),
-                                              (_pw1024, 256, "sm", 1),
+                                              (_pw1024, 128, "sm", 1),
                                               (_ring300, 128, "delayed", 8)])
 def test_tma_ring_matches_plain_loads(Q, oracle_lib, make, nt, update, k):
-    """n > 256: the stencil arrives as a ring of TMA boxes (256 orbitals x one x-plane,
-    three in flight) and each box is reduced as it lands.  Against per-thread loads of the
+    """n > 256 with 128 threads: the stencil arrives as a ring of TMA boxes (256 orbitals x
+    one x-plane, three in flight) and each box is reduced as it lands.  Against per-thread loads of the
     same coefficients: the proposals' log-ratios and drifts agree to FP32 rounding, a
     generation follows the same trajectory, and E_L matches the oracle."""
     wl = make()
