@@ -149,9 +149,11 @@ int qmc_crowd_destroy(qmc_crowd* crowd);
 
 /* Electron positions, double [W][N][3] (mem).  Values are wrapped into [0, L).  Marks
  * the orbital rows and inverses stale: the next move, energy or explicit
- * qmc_recompute() rebuilds them (Alg. 1 line 3). */
+ * qmc_recompute() rebuilds them (Alg. 1 line 3).  Errors: INVALID_ARG (also for a
+ * non-finite coordinate in host memory: nothing is loaded); a non-finite coordinate in
+ * device memory is replaced by 0 and the next synchronising call returns QMC_ERR_NAN. */
 int qmc_load_positions(qmc_crowd* crowd, const double* R, int mem);
-/* Ion positions, double [n_ions][3] (host). */
+/* Ion positions, double [n_ions][3] (host).  Errors: INVALID_ARG (also non-finite). */
 int qmc_load_ions(qmc_crowd* crowd, const double* RI);
 /* Orbital coefficient table [G][G][G][n_orb] (mem), x slowest, orbital fastest, periodic
  * (node g at x = g L / G), dtype QMC_DTYPE_F64 or F32.  The library adds three ghost
@@ -345,7 +347,8 @@ int qmc_load_coulomb(qmc_crowd* crowd, int on, double Z, double alpha, int mmax)
  * qmc_dmc_append: m walkers join at slots W..W+m-1 with positions R: double [m][N][3]
  * (mem), wrapped into the cell; their orbital rows and inverses are built (FP64
  * recompute) and nothing of the other walkers changes.  W + m <= capacity.  Synchronous.
- * Errors: INVALID_ARG; SINGULAR (a joining walker's Slater matrix is singular).
+ * Errors: INVALID_ARG (also a non-finite coordinate in host memory); NAN (one in device
+ * memory: replaced by 0); SINGULAR (a joining walker's Slater matrix is singular).
  * --------------------------------------------------------------------------------------- */
 int qmc_dmc_select(qmc_crowd* crowd, const int* src, int n_new, int mem);
 int qmc_dmc_append(qmc_crowd* crowd, const double* R, int m, int mem);

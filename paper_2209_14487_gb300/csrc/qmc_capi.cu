@@ -158,6 +158,12 @@ struct NvtxRange {
 
 bool is_mixed(const qmc_crowd* c) { return c->run.precision == QMC_PREC_MIXED; }
 
+bool all_finite(const double* x, size_t n) {
+  for (size_t e = 0; e < n; ++e)
+    if (!std::isfinite(x[e])) return false;
+  return true;
+}
+
 int dmalloc(void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (cudaMalloc(ptr, bytes) != cudaSuccess) {
@@ -677,10 +683,12 @@ int qmc_load_positions(qmc_crowd* c, const double* R, int mem) {
   QMC_RANGE();
   if (!c || !R) return QMC_ERR_INVALID_ARG;
   const size_t n3 = (size_t)c->p.W * c->p.N * 3;
+  if (mem == QMC_MEM_HOST && !all_finite(R, n3)) return QMC_ERR_INVALID_ARG;
   CK(cudaMemcpyAsync(c->d_R, R, n3 * sizeof(double),
                      mem == QMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      c->stream));
-  int st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R, n3, c->p.L, c->stream));
+  int st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R, n3, c->p.L, c->d_status,
+                                                         c->stream));
   if (st) return st;
   if (mem == QMC_MEM_HOST) CK(cudaStreamSynchronize(c->stream));
   c->has_positions = true;
@@ -692,7 +700,7 @@ int qmc_load_ions(qmc_crowd* c, const double* RI) {
   QMC_RANGE();
   if (!c) return QMC_ERR_INVALID_ARG;
   if (c->sys.n_ions == 0) return QMC_OK;
-  if (!RI) return QMC_ERR_INVALID_ARG;
+  if (!RI || !all_finite(RI, 3 * (size_t)c->sys.n_ions)) return QMC_ERR_INVALID_ARG;
   std::vector<double> h(RI, RI + 3 * c->sys.n_ions);
   for (double& x : h) x = x - c->p.L * std::floor(x / c->p.L);
   CK(cudaMemcpyAsync(c->d_ions, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
@@ -1249,13 +1257,15 @@ int qmc_dmc_append(qmc_crowd* c, const double* R, int m, int mem) {
   if (mem != QMC_MEM_HOST && mem != QMC_MEM_DEVICE) return QMC_ERR_INVALID_ARG;
   const int W = c->p.W, N = c->p.N;
   if (W + m > c->run.n_walkers) return QMC_ERR_INVALID_ARG;
+  if (mem == QMC_MEM_HOST && !all_finite(R, (size_t)m * N * 3)) return QMC_ERR_INVALID_ARG;
   int st = ensure_ready(c);
   if (st) return st;
   const size_t off = (size_t)W * N * 3, n3 = (size_t)m * N * 3;
   CK(cudaMemcpyAsync(c->d_R + off, R, n3 * sizeof(double),
                      mem == QMC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      c->stream));
-  st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R + off, n3, c->p.L, c->stream));
+  st = launch_status(c, qmcgb::launch_wrap_positions(c->d_R + off, n3, c->p.L, c->d_status,
+                                                     c->stream));
   if (st) return st;
   // the new walkers' orbital rows and FP64 inverses, nobody else's (launched with the
   // grown population, of which walkers W .. W + m - 1 are the new ones)

@@ -207,7 +207,7 @@ cudaError_t launch_pad_table(const Params& p, const void* src, int src_f32, int 
                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s);
-cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s);
+cudaError_t launch_wrap_positions(double* R, size_t n3, double L, int* status, cudaStream_t s);
 // adds the nonlocal pseudopotential term to eloc[0..W) (nothing when p.nl_n == 0);
 // partial: scratch of W * nlpp_partials_per_walker() doubles
 template <typename T>

@@ -171,11 +171,20 @@ __global__ void __launch_bounds__(LA_NT) jastrow_U_kernel(const Params p, double
   }
 }
 
-__global__ void wrap_kernel(double* R, size_t n3, double L) {
+// Wraps positions into [0, L); a non-finite coordinate is replaced by 0 and reported
+// (ST_NAN), so that no later kernel indexes the table with it.
+__global__ void wrap_kernel(double* R, size_t n3, double L, int* status) {
   const double invL = 1.0 / L;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n3;
-       e += (size_t)gridDim.x * blockDim.x)
-    R[e] = wrap_coord(R[e], L, invL);
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double x = R[e];
+    if (isfinite(x)) {
+      R[e] = wrap_coord(x, L, invL);
+    } else {
+      R[e] = 0.0;
+      atomicOr(status, (int)ST_NAN);
+    }
+  }
 }
 
 template <typename T>
@@ -213,8 +222,8 @@ cudaError_t launch_jastrow_U(const Params& p, double* U, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_wrap_positions(double* R, size_t n3, double L, cudaStream_t s) {
-  wrap_kernel<<<256, 256, 0, s>>>(R, n3, L);
+cudaError_t launch_wrap_positions(double* R, size_t n3, double L, int* status, cudaStream_t s) {
+  wrap_kernel<<<256, 256, 0, s>>>(R, n3, L, status);
   return cudaGetLastError();
 }
 

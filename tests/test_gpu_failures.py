@@ -75,3 +75,44 @@ def test_bounded_wait_times_out_and_the_crowd_recovers(Q):
         Q.Crowd.from_workload(wl, precision="mixed", n_walkers=W,
                               staging="ldg").qmc_test_skip_stencil_copy(True)
     assert ei.value.status == 1
+
+
+def test_non_finite_positions_are_refused(Q):
+    """Corrupted inputs: a NaN or infinite coordinate in host memory is refused before
+    anything is loaded (INVALID_ARG, the crowd unchanged); one in device memory is
+    replaced by 0 and reported as QMC_ERR_NAN by the next synchronising call, and a clean
+    reload restores the crowd.  Non-finite ion positions are refused."""
+    torch = pytest.importorskip("torch")
+    wl = wl_mod.pw128()
+    W = 4
+    c = Q.Crowd.from_workload(wl, precision="mixed", n_walkers=W, n_recompute=0)
+    R0 = np.ascontiguousarray(wl.positions(n_walkers=W))
+    c.qmc_load_positions(R0)
+    c.qmc_recompute()
+    before = c.qmc_get_positions()
+    for bad_value in (np.nan, np.inf):
+        bad = R0.copy()
+        bad[1, 7, 2] = bad_value
+        with pytest.raises(Q.QmcError) as ei:
+            c.qmc_load_positions(bad)
+        assert ei.value.status == 1
+        assert np.array_equal(c.qmc_get_positions(), before)
+    ions = np.ascontiguousarray(wl.ions.copy())
+    ions[0, 0] = np.nan
+    with pytest.raises(Q.QmcError) as ei:
+        c.qmc_load_ions(ions)
+    assert ei.value.status == 1
+    bad = R0.copy()
+    bad[2, 3, 0] = np.nan
+    dev = torch.from_numpy(bad).cuda()
+    c.qmc_load_positions(dev)
+    with pytest.raises(Q.QmcError) as ei:
+        c.qmc_recompute()
+    assert ei.value.status == 6
+    got = c.qmc_get_positions()
+    assert got[2, 3, 0] == 0.0 and np.all(np.isfinite(got))
+    c.qmc_load_positions(R0)
+    c.qmc_recompute()
+    e = np.zeros((1, W))
+    st = c.qmc_sweep(1, e)
+    assert np.all(np.isfinite(e)) and 0.2 < st.n_accept / st.n_moves < 0.95
