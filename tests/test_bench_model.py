@@ -18,3 +18,28 @@ def test_bytes_per_move_examples(n, N, s, update, k, expect):
 def test_aggregate_value_single_rank():
     assert bench.aggregate_value(1000.0, 2.0, 1) == 500.0
     assert bench.reduce_sum(3.5, 1) == 3.5
+
+
+def test_amortised_recompute_share():
+    """A step without the recompute gets (recompute generation - plain generation) /
+    n_recompute added; a step that carried one keeps its own time."""
+    r = {"ms": [1.0, 1.0, 5.0, 1.0], "plain_ms": [1.0, 1.0, 1.0], "due": [False, False, True, False],
+         "recompute_step_ms": [9.0, 9.0]}
+    ms, extra = bench.amortised(r, 4)
+    assert extra == pytest.approx(8.0)
+    assert ms == pytest.approx([3.0, 3.0, 5.0, 3.0])
+    assert bench.amortised(dict(r, recompute_step_ms=[]), 4) == (r["ms"], 0.0)
+    assert bench.amortised(r, 0) == (r["ms"], 0.0)
+
+
+def test_energy_stats_blocks():
+    """Block means of the crowd average per generation: the mean of all generations and the
+    standard error of the block means; fewer than two blocks give no error."""
+    np = pytest.importorskip("numpy")
+    e = np.repeat(np.arange(8.0)[:, None], 3, axis=1)  # generation g: every walker g
+    m, s = bench.energy_stats(e, block=2)
+    b = np.array([0.5, 2.5, 4.5, 6.5])
+    assert m == pytest.approx(b.mean())
+    assert s == pytest.approx(b.std(ddof=1) / 2.0)
+    m1, s1 = bench.energy_stats(e, block=8)
+    assert m1 == pytest.approx(3.5) and s1 != s1  # NaN
