@@ -54,3 +54,30 @@ def test_invalid_arguments_rejected_before_device_use():
     assert Q.lib.qmc_crowd_create(ctypes.byref(sys_), ctypes.byref(run), None,
                                   ctypes.byref(h)) == 8
     assert Q.lib.qmc_crowd_destroy(None) == 1
+
+
+def _enum_values(prefix):
+    src = open(os.path.join(ROOT, "include", "qmcgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b(" + prefix + r"[A-Z0-9_]*)\s*=\s*(\d+)", src)}
+
+
+def test_binding_constants_match_the_header():
+    """Every status, layout and build-flag constant the binding uses has the header's
+    value, and every status code has its name and its text."""
+    from paper_2209_14487_gb300 import build, qmcgb
+    errs = _enum_values("QMC_ERR_")
+    errs["QMC_OK"] = _enum_values("QMC_OK")["QMC_OK"]
+    assert qmcgb.STATUS_NAMES == {v: k for k, v in errs.items()}
+    layouts = _enum_values("QMC_LAYOUT_")
+    assert (qmcgb.QMC_LAYOUT_AUTO, qmcgb.QMC_LAYOUT_SHARED, qmcgb.QMC_LAYOUT_COMPACT) == (
+        layouts["QMC_LAYOUT_AUTO"], layouts["QMC_LAYOUT_SHARED"], layouts["QMC_LAYOUT_COMPACT"])
+    assert qmcgb.QMC_BUILD_CHECKED == _enum_values("QMC_BUILD_")["QMC_BUILD_CHECKED"]
+    assert qmcgb.QMC_ERR_BOUNDS == errs["QMC_ERR_BOUNDS"]
+    lib = ctypes.CDLL(build.build())
+    lib.qmc_status_string.restype = ctypes.c_char_p
+    for code in errs.values():
+        assert lib.qmc_status_string(code) != b"unknown status", code
+    lib.qmc_build_flags.restype = ctypes.c_int
+    assert lib.qmc_build_flags() == 0  # the normal build
