@@ -408,11 +408,14 @@ def test_spline_free_electron_energy_converges_second_order(oracle_lib):
     assert emed[2] < 1e-3 * exact
 
 
-@pytest.mark.parametrize("drift,wave", [(0, 1), (1, 0)])
+@pytest.mark.parametrize("drift,wave", [(0, 1), (1, 0), (2, 0), (1, 1)])
 def test_metropolis_samples_psi_squared(oracle_lib, drift, wave):
-    """One electron, Psi = w(x) exp(-u1) with w = cos(2 pi x / L) (plain Metropolis) or
-    w = 1 (nodeless, drift-diffusion Metropolis-Hastings): the walk's histogram on 4^3
-    bins against |Psi|^2 integrated on a fine grid (chi^2, p > 0.001)."""
+    """One electron, Psi = w(x) exp(-u1) with w = cos(2 pi x / L) (with nodes) or w = 1
+    (nodeless), moved by plain Metropolis (drift 0) or drift-diffusion Metropolis-Hastings
+    with the limited drift (1) or the plain drift F (2): the walk's histogram on 4^3 bins
+    against |Psi|^2 integrated on a fine grid (chi^2, p > 0.001).  A proposal density that
+    the acceptance ratio does not match exactly (a wrong drift in either Green's function)
+    biases the histogram."""
     from scipy import stats
     L = 3.0
     ions = np.array([[0.7, 1.1, 2.0], [2.2, 2.3, 0.6]])
@@ -444,6 +447,52 @@ def test_metropolis_samples_psi_squared(oracle_lib, drift, wave):
     exp_counts = p * counts.sum()
     chi2 = ((counts - exp_counts) ** 2 / exp_counts).sum()
     pval = stats.chi2.sf(chi2, nb ** 3 - 1)
+    assert pval > 1e-3, (chi2, pval)
+
+
+@pytest.mark.parametrize("drift,mx", [(1, 3), (2, 0), (0, 3)])
+def test_drift_diffusion_samples_psi_squared_near_nodes(oracle_lib, drift, mx):
+    """Sharper than the 4^3 histogram above: one electron in a 6 bohr cell with
+    Psi = cos(2 pi mx x / L) exp(-u1) (mx = 3: six nodal planes; mx = 0: nodeless), moved
+    with the limited drift (1), the plain drift F (2, nodeless only: near a node tau F
+    outgrows the cell and the single-image Green's function no longer holds) or none
+    (0); tau = 0.3.  The walk's 16-bin marginal in x against |Psi|^2 integrated over y and
+    z (chi^2 with 15 degrees of freedom, p > 0.001; the RNG is counter-based, so the test
+    is deterministic).  Near the nodes the limited and plain drifts differ most: an oracle
+    whose reverse Green's function used F(r') instead of D(F(r')) gave chi^2 = 2049 here
+    (p ~ 0), against 18.4 for the correct one."""
+    from scipy import stats
+    L, tau, nb = 6.0, 0.3, 16
+    ions = np.array([[1.4, 2.2, 4.0], [4.4, 4.6, 1.2]])
+    j1 = wl_mod.jastrow_coefs(6, -0.6, 1.4, cusp=None)
+    m = np.array([[mx, 0, 0]], dtype=np.int32)
+    kind = np.array([1], dtype=np.int32)
+    osys = oracle_lib.OracleSystem(None, analytic_waves=(m, kind), n_up=1, n_dn=0, n_orb=1,
+                                   n_ions=2, ions=ions, j1_K=6, j1_rc=1.4, j1=j1.coefs, L=L,
+                                   tau=tau, drift=drift, seed=777)
+    W = 1024
+    R = np.random.default_rng(1).uniform(0, L, size=(W, 1, 3))
+    crowd = oracle_lib.OracleCrowd(osys, R)
+    crowd.sweep(30)
+    counts = np.zeros(nb)
+    for _ in range(40):
+        crowd.sweep(8)
+        idx = np.minimum((crowd.positions()[:, 0, 0] / L * nb).astype(int), nb - 1)
+        np.add.at(counts, idx, 1)
+    f, g = 8, 24
+    xs = (np.arange(nb * f) + 0.5) * L / (nb * f)
+    ys = (np.arange(g) + 0.5) * L / g
+    dens = np.zeros(nb * f)
+    for a, x in enumerate(xs):
+        for y in ys:
+            for z in ys:
+                la, _ = osys.logpsi(np.array([[x, y, z]]))
+                dens[a] += math.exp(2 * la)
+    p = dens.reshape(nb, f).sum(axis=1)
+    p /= p.sum()
+    exp_counts = p * counts.sum()
+    chi2 = ((counts - exp_counts) ** 2 / exp_counts).sum()
+    pval = stats.chi2.sf(chi2, nb - 1)
     assert pval > 1e-3, (chi2, pval)
 
 
